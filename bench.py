@@ -1,0 +1,462 @@
+#!/usr/bin/env python
+"""Benchmark of the JaxWildfire hot path on libjwf (GB300).
+
+One step = one full episode of the batched workload: 4096 grids of 128 x 128
+cells (30 m; 11-class fBm landcover, fBm DEM 0-2000 m, per-grid wind, 1-3
+fires), reset to the initial fires, the probability table built (Eqs. 1-4),
+then 200 discrete steps (Section 3 stochastic update) with one random 3 x 3
+tanker drop per grid per step and per-step burning/burned counts and done
+flags.  Metric: cell-updates/s (grids x cells x steps / time).
+
+The same JSON line also reports the relaxed path (Eqs. 5-10): a forward and
+backward pass (sqrt(T) checkpoints) of 256 grids of 128 x 128 over T = 100
+steps, as fwd+bwd cell-steps/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own batch (weak scaling, no collective in
+the data path); rank 0 prints one JSON line.  --impl reference times the CPU
+oracle (the plain single-threaded C simulator) on a sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ENVS, SIDE, EPISODE = 4096, 128, 200
+REL_ENVS, REL_T = 256, 100
+METRIC = "CA cell-updates/s at 4096x128^2 (200-step episode with tanker drops)"
+CPU_SAMPLE_ENVS = 48
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-relaxed", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU)
+# ---------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Dist:
+    def __init__(self, use_cuda: bool):
+        import torch
+        self.rank, self.world, self.local = dist_env()
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if use_cuda else "gloo"
+            if use_cuda:
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if self.pg is None:
+            return x
+        import torch
+        dev = torch.device("cuda", self.local) if torch.cuda.is_available() else torch.device("cpu")
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(name: str, source: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(name)
+    if not d:
+        return None
+    sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()[:16]
+    return d.get("dram_bytes_per_launch") if d.get("source_sha") == sha else None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2512_06102_gb300 import build, jwf, scenarios
+    from paper_2512_06102_gb300 import relaxed as rlx
+
+    D = Dist(use_cuda=True)
+    rank, world = D.rank, D.world
+    torch.cuda.set_device(D.local)
+    dev = torch.device("cuda", D.local)
+    if rank == 0 or not build.up_to_date():
+        build.build()
+    D.barrier()
+
+    scn = scenarios.make_scenario(SIDE, SIDE, N=N_ENVS, seed=rank)
+    drops = scenarios.drops(EPISODE, scn.H, scn.W, seed=rank)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    cls_d, dem_d, ws_d, wd_d, F0_d, drops_d = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir),
+                                               to(scn.F0), to(drops))
+    sim = jwf.Sim(SIDE, SIDE, n_envs=N_ENVS, n_classes=scenarios.N_CLASSES, seed=1000 + rank)
+    sim.set_params(scn.params)
+    burning = torch.empty((EPISODE, N_ENVS), dtype=torch.int32, device=dev)
+    burnt = torch.empty_like(burning)
+    done = torch.empty((EPISODE, N_ENVS), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    ev_k = []
+
+    def episode(record=False):
+        sim.load_state(F0_d)
+        sim.precompute_probs(cls_d, dem_d, ws_d, wd_d)
+        if record:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        sim.step(EPISODE, drops_d, burning, burnt, done)
+        if record:
+            b.record(stream)
+            ev_k.append((a, b))
+
+    # consumed table entries of one episode (deterministic, counted once)
+    pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+    sim.set_pair_counter(pairs)
+    episode()
+    sim.set_pair_counter(None)
+    torch.cuda.synchronize()
+    n_pairs = int(pairs.item())
+    active = burning.sum(dtype=torch.int64).item()
+
+    for _ in range(args.warmup):
+        episode()
+    torch.cuda.synchronize()
+    D.barrier()
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    torch.cuda.synchronize()
+    D.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        episode(record=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    D.barrier()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    t_kernel = statistics.mean(a.elapsed_time(b) for a, b in ev_k) / 1e3
+    clocks = clk.stop()
+    t_max = D.max(t_dev)
+    cells = N_ENVS * SIDE * SIDE
+    units = cells * EPISODE * args.steps
+    value = world * units / t_max
+
+    # end to end through the public API with host buffers: inputs copied in
+    # from pinned memory and the per-step counts read back, every step
+    host = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            for k, a in (("cls", scn.cls), ("dem", scn.dem), ("ws", scn.wind_speed), ("wd", scn.wind_dir),
+                         ("F0", scn.F0), ("drops", drops))}
+    out_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
+             for k, v in (("burning", burning), ("burnt", burnt), ("done", done))}
+    dev_in = {"cls": cls_d, "dem": dem_d, "ws": ws_d, "wd": wd_d, "F0": F0_d, "drops": drops_d}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in out_h.values())
+
+    def e2e_step():
+        for k, v in host.items():
+            dev_in[k].copy_(v, non_blocking=True)
+        episode()
+        out_h["burning"].copy_(burning, non_blocking=True)
+        out_h["burnt"].copy_(burnt, non_blocking=True)
+        out_h["done"].copy_(done, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    D.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = D.max(time.perf_counter() - t0)
+    e2e_value = world * units / t_e2e
+
+    # roofline of the dominant kernel (the resident step launch)
+    hbm, peak_kind = peaks()
+    b_alg = 2 * cells * EPISODE + 4 * n_pairs + 8 * N_ENVS * EPISODE
+    achieved = b_alg / t_kernel / 1e9
+    b_min = 2 * cells + 4 * n_pairs + 8 * N_ENVS * EPISODE
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
+            "traffic": kernel_traffic("k_step_resident", "paper_2512_06102_gb300/csrc/k_step.cu"),
+            "kernel": "k_step_resident", "kernel_ms": round(t_kernel * 1e3, 3),
+            "bytes_model": "2 B/cell-update state + 4 B/consumed q entry + 8 B/env-step drop",
+            "algorithmic_bytes_per_launch": b_alg,
+            "min_bytes_per_launch": b_min,
+            "min_bytes_frac": round(b_min / t_kernel / 1e9 / hbm, 4),
+            "consumed_q_entries": n_pairs, "burning_cell_steps": active}
+    sim.close()
+    del sim
+
+    rel = None
+    if not args.no_relaxed:
+        rel = bench_relaxed(args, D, dev, rank)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scn, drops)
+
+    line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded fBm landcover/DEM stand-ins for WorldCover/GLO-30)",
+            "config": {"workload": f"batched: {N_ENVS} grids x {SIDE}x{SIDE}, {EPISODE}-step episode, 3x3 drop/step",
+                       "global_batch": N_ENVS * world, "grid": [SIDE, SIDE], "steps_per_episode": EPISODE,
+                       "parallelism": f"replicas x{world} (independent grid shards)",
+                       "l2": "inputs larger than L2 (2.15 GB probability table rebuilt and read every step)"},
+            "env_steps_per_s": world * N_ENVS * EPISODE * args.steps / t_max,
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks}
+    if rel is not None:
+        line["relaxed"] = rel
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    D.close()
+
+
+def bench_relaxed(args, D, dev, rank):
+    """fwd+bwd of T relaxed steps on 256 x 128^2 with sqrt(T) checkpoints."""
+    import torch
+
+    from paper_2512_06102_gb300 import jwf, scenarios
+    from paper_2512_06102_gb300 import relaxed as rlx
+
+    scn = scenarios.make_scenario(SIDE, SIDE, N=REL_ENVS, seed=100 + rank)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    scene = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    sim = jwf.Sim(SIDE, SIDE, n_envs=REL_ENVS, n_classes=scenarios.N_CLASSES, keep_rates=True)
+    p = scn.params
+    theta0 = torch.tensor([p.p_base, p.alpha_w1, p.alpha_w2, p.alpha_s, p.alpha_gamma, p.p_continue]
+                          + list(p.mu_veg) + list(p.mu_den), dtype=torch.float64)
+    pb0 = (to(scn.F0) == 2).float()
+    pu0 = 1.0 - pb0
+    target = torch.rand(pu0.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+    stream = torch.cuda.current_stream()
+    ev_f = []
+
+    def fwd_bwd():
+        th = theta0.clone().requires_grad_(True)
+        pu = pu0.clone().requires_grad_(True)
+        pb = pb0.clone().requires_grad_(True)
+        ou, ob = rlx.rollout(th, pu, pb, sim, scene, REL_T)
+        loss = ((ou - target) ** 2).mean() + ob.mean()
+        loss.backward()
+        return th.grad
+
+    # dominant kernel timing: one forward step launch, measured in isolation
+    def time_fwd_kernel(n=20):
+        bufs = [(pu0.clone(), pb0.clone()), (torch.empty_like(pu0), torch.empty_like(pb0))]
+        sim.set_params(rlx.theta_to_params(theta0, sim.n_classes))
+        sim.precompute_probs(*scene)
+        sim.relaxed_fwd(bufs[0][0], bufs[0][1], None, bufs[1][0], bufs[1][1])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(n):
+            src, dst = bufs[i % 2], bufs[(i + 1) % 2]
+            sim.relaxed_fwd(src[0], src[1], None, dst[0], dst[1])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / n
+
+    for _ in range(max(1, args.warmup)):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    D.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        fwd_bwd()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    D.barrier()
+    t = D.max(e0.elapsed_time(e1) / 1e3)
+    t_fwd = time_fwd_kernel()
+    cells = REL_ENVS * SIDE * SIDE
+    hbm, peak_kind = peaks()
+    fwd_bytes = 48 * cells
+    ach = fwd_bytes / t_fwd / 1e9
+    sim.close()
+    return {"metric": "fwd+bwd cell-steps/s at 256x128^2, T=100 (sqrt(T) checkpoints)",
+            "value": D.world * cells * REL_T * args.steps / t, "unit": "fwd+bwd cell-steps/s",
+            "ms_per_step": t / args.steps * 1e3, "dtype": "f32",
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(ach / hbm, 4), "peak_source": peak_kind,
+                         "traffic": kernel_traffic("k_relaxed_fwd", "paper_2512_06102_gb300/csrc/k_relaxed.cu"),
+                         "kernel": "k_relaxed_fwd", "kernel_us": round(t_fwd * 1e6, 2),
+                         "bytes_model": "48 B/cell-step (8 B state in, 32 B rates, 8 B state out)"}}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (rank 0, N = 1)
+# ---------------------------------------------------------------------------
+def oracle_episode(scn, drops, envs):
+    """The oracle on grids `envs` of the batch: FP64 table + C rollout."""
+    import torch
+
+    from oracle import discrete, prob
+    p = scn.params.as_dict()
+    q = []
+    for e in envs:
+        q32, _, _, _ = prob.table_f32(scn.env(e, scn.cls)[None], scn.env(e, scn.dem)[None],
+                                      scn.wind_speed[e:e + 1], scn.wind_dir[e:e + 1], p, 30.0)
+        q.append(q32.reshape(-1, 8))
+    n = len(envs)
+    F0 = np.concatenate([scn.env(e, scn.F0).reshape(-1) for e in envs])
+    ro = discrete.Rollout(np.full(n, SIDE), np.full(n, SIDE), F0, np.concatenate(q), scn.params.p_continue,
+                          seed=1000, env_ids=np.asarray(envs, np.int32))
+    ro.step(EPISODE, np.ascontiguousarray(drops[:, envs]))
+
+
+def cpu_baseline(scn, drops, n_envs=CPU_SAMPLE_ENVS, reps=1):
+    import torch
+    torch.set_num_threads(1)
+    envs = list(range(n_envs))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle_episode(scn, drops, envs)
+    dt = time.perf_counter() - t0
+    return {"value": reps * n_envs * SIDE * SIDE * EPISODE / dt, "unit": "cell-updates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{n_envs} of the {N_ENVS} grids x {EPISODE} steps ({reps} rep), FP64 table + C step, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    torch.set_num_threads(1)
+    from paper_2512_06102_gb300 import scenarios
+    n = 16
+    scn = scenarios.make_scenario(SIDE, SIDE, N=n, seed=0)
+    drops = scenarios.drops(EPISODE, scn.H, scn.W, seed=0)
+    envs = list(range(n))
+    for _ in range(args.warmup):
+        oracle_episode(scn, drops, envs[:2])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_episode(scn, drops, envs)
+    dt = time.perf_counter() - t0
+    value = args.steps * n * SIDE * SIDE * EPISODE / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded fBm landcover/DEM stand-ins for WorldCover/GLO-30)",
+            "config": {"workload": f"batched: {N_ENVS} grids x {SIDE}x{SIDE}, {EPISODE}-step episode, 3x3 drop/step",
+                       "global_batch": N_ENVS * world, "grid": [SIDE, SIDE], "steps_per_episode": EPISODE,
+                       "parallelism": "single host core"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {n} of the {N_ENVS} grids x {EPISODE} steps"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * jwf.h -- C ABI of libjwf, a GB300 (sm_103a) engine for the stochastic
+ * cellular-automaton wildfire model of JaxWildfire (arXiv 2512.06102).
+ *
+ * One context (jwf_ctx) holds a batch of N independent grids ("envs"), each
+ * with its own height H[e] and width W[e] (ragged batches are allowed).  The
+ * context owns the device state, the per-(cell, direction) probability and
+ * rate tables and the per-env counters; callers own every pointer they pass.
+ *
+ * Conventions shared by every entry point
+ *  - Cells of env e occupy the contiguous index range [off[e], off[e] + H*W),
+ *    row-major (x fastest), off[e] = sum of the sizes of envs before e.
+ *    "cells" below is the total over all envs.
+ *  - Cell states (uint8): 0 no fuel (an unburned cell whose fuel density
+ *    mu_den is -1; it can never ignite), 1 can burn, 2 burning, 3 burned
+ *    (Section 3, "State representation": F in {unburned, burning, burned}).
+ *  - Directions d = 0..7 (east, north-east, north, north-west, west,
+ *    south-west, south, south-east): the angle of Delta_d is d*45 degrees,
+ *    east = 0, counter-clockwise (Section 3, below Eq. 2).  Rows grow
+ *    southward, so north is row - 1.  Tables are indexed [cell v][d] and
+ *    describe spread INTO target v FROM source u = v - Delta_d.
+ *  - Pointers named d_* are device pointers (cudaMalloc / torch tensors),
+ *    h_* are host pointers.  Every call is asynchronous on the given
+ *    cudaStream_t (passed as void*; NULL = the legacy default stream) and
+ *    returns once the work is enqueued.  Argument errors are reported
+ *    immediately and leave the context unchanged.  Errors raised inside a
+ *    kernel (a bounded wait that ran out, an index check in a checked build)
+ *    are written to a device status word and reported by jwf_sync().
+ *  - No call aborts, throws or traps; every failure is a jwf_status.
+ *  - One context must be used from one stream at a time (calls on one
+ *    context that overlap on the GPU race).
+ */
+#ifndef JWF_H
+#define JWF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define JWF_API __attribute__((visibility("default")))
+#else
+#define JWF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jwf_ctx jwf_ctx;
+
+typedef enum {
+    JWF_OK = 0,
+    JWF_EINVAL = 1,        /* bad argument (null pointer, size, range)        */
+    JWF_ENOMEM = 2,        /* device or host allocation failed                */
+    JWF_ECUDA = 3,         /* a CUDA runtime call failed (see jwf_last_error) */
+    JWF_ETIMEOUT = 4,      /* a bounded device-side wait gave up              */
+    JWF_ESTATE = 5,        /* call out of order (e.g. step before load_state) */
+    JWF_EUNSUPPORTED = 6   /* option not available for this configuration     */
+} jwf_status;
+
+/* Flags of jwf_config.flags */
+#define JWF_AUTO_RESET     0x1u  /* a done env restarts from its initial state  */
+#define JWF_WIND_PER_CELL  0x2u  /* wind arrays are [cells], not [n_envs]       */
+#define JWF_KEEP_RATES     0x4u  /* keep the rate table r (relaxed path)        */
+
+typedef struct {
+    int32_t n_envs;          /* N >= 1                                           */
+    const int32_t* h_H;      /* [N] grid heights, 1..65535 (copied)              */
+    const int32_t* h_W;      /* [N] grid widths, 1..65535 (copied)               */
+    int32_t n_classes;       /* landcover classes, 1..16                         */
+    uint64_t seed;           /* Philox key (low word, high word)                 */
+    int32_t t_max;           /* episode length limit; <= 0: none                 */
+    int32_t drop_radius;     /* tanker drop: (2R+1)^2 square, R >= 0 (1 = 3x3)   */
+    uint32_t flags;          /* JWF_* flags above                                */
+} jwf_config;
+
+/* Model parameters (Section 3, Eqs. 1-4 and the stochastic update). */
+typedef struct {
+    float p_base;            /* base propagation factor, Eq. 3                   */
+    float alpha_w1;          /* wind-speed coefficient, Eq. 1                    */
+    float alpha_w2;          /* wind-direction coefficient, Eq. 1                */
+    float alpha_s;           /* slope coefficient per degree, Eq. 2              */
+    float alpha_gamma;       /* susceptibility scale, gamma(v), Section 3        */
+    float p_continue;        /* probability that a burning cell keeps burning    */
+    float cell_size;         /* metres per cell (slope run length)               */
+    const float* h_mu_veg;   /* [n_classes] canopy modifiers in [-1, 1] (copied) */
+    const float* h_mu_den;   /* [n_classes] fuel density in [-1, 1]; -1 = none   */
+} jwf_params;
+
+/* Number of doubles in a parameter-gradient vector:
+ * [p_base, alpha_w1, alpha_w2, alpha_s, alpha_gamma, mu_veg[C], mu_den[C]] */
+#define JWF_GRAD_SIZE(n_classes) (5 + 2 * (n_classes))
+
+/* ---- lifetime ------------------------------------------------------------ */
+
+/* Create a context for cfg (host struct, read during the call).  Allocates the
+ * state, the probability table, the per-env counters and, with
+ * JWF_KEEP_RATES, the rate table on the current CUDA device.  *out is NULL on
+ * failure.  Errors: JWF_EINVAL (bad sizes or flags), JWF_ENOMEM, JWF_ECUDA. */
+JWF_API jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out);
+
+/* Release everything the context owns.  Waits for the device.  NULL is a no-op. */
+JWF_API jwf_status jwf_destroy(jwf_ctx* ctx);
+
+/* Store the parameters used by later calls (copied; mu tables are host arrays
+ * of n_classes floats).  Errors: JWF_EINVAL (NULL, p_continue outside [0,1],
+ * mu outside [-1,1], negative coefficients where the paper requires >= 0). */
+JWF_API jwf_status jwf_set_params(jwf_ctx* ctx, const jwf_params* p);
+
+/* Block until the stream's work is done, then report (and clear) any error a
+ * kernel recorded in the device status word. */
+JWF_API jwf_status jwf_sync(jwf_ctx* ctx, void* stream);
+
+JWF_API const char* jwf_status_string(jwf_status s);
+JWF_API const char* jwf_last_error(const jwf_ctx* ctx);   /* message of the last failure */
+
+/* Read-only facts about the context. */
+JWF_API int32_t jwf_n_envs(const jwf_ctx* ctx);
+JWF_API int64_t jwf_n_cells(const jwf_ctx* ctx);
+JWF_API int64_t jwf_env_offset(const jwf_ctx* ctx, int32_t e);     /* off[e]; e == N gives cells */
+
+/* ---- probability tables (Section 3, Eqs. 1-4) ---------------------------- */
+
+/* Build the per-(cell, direction) tables on the device from landcover class
+ * ids (uint8 [cells], < n_classes), elevation (float [cells], metres) and
+ * wind speed (m/s, >= 0) and direction (radians; the direction the wind
+ * blows toward) given per env ([N]) or, with JWF_WIND_PER_CELL, per cell.
+ * For target v, direction d, source u = v - Delta_d:
+ *   S(u,d)   = atan((z(v) - z(u)) / (cell_size * |Delta_d|)) in degrees (Eq. 2)
+ *   phi(u,d) = p_base (1 + mu_veg(u)) (1 + mu_den(u))
+ *              exp(alpha_w1 V(u)) exp(alpha_w2 V(u) (cos(d*pi/4 - Theta(u)) - 1))
+ *              exp(alpha_s S(u,d))                                   (Eqs. 1-3)
+ *   gamma(v) = alpha_gamma (1 + mu_veg(v)) (1 + mu_den(v))           (Section 3)
+ *   r[v][d]  = gamma(v) phi(u,d), 0 when u is outside the grid       (Eq. 4 rate)
+ *   q[v][d]  = 1 - exp(-r[v][d]), the probability that a burning u ignites v
+ *              in one step; over all burning neighbours this gives exactly
+ *              Eq. 4's 1 - exp(-gamma(v) * lambda).
+ * Uses the parameters of the last jwf_set_params().  Writes q (and r with
+ * JWF_KEEP_RATES).  Errors: JWF_ESTATE (no parameters), JWF_EINVAL (NULL). */
+JWF_API jwf_status jwf_precompute_probs(jwf_ctx* ctx, const uint8_t* d_class, const float* d_dem,
+                                const float* d_wind_speed, const float* d_wind_dir, void* stream);
+
+/* Replace the tables with caller data: d_q float [cells][8] (required),
+ * d_r float [cells][8] (may be NULL; requires JWF_KEEP_RATES otherwise).
+ * Device-to-device copies on the stream. */
+JWF_API jwf_status jwf_set_probs(jwf_ctx* ctx, const float* d_q, const float* d_r, void* stream);
+
+/* Borrowed device views of the tables (valid until jwf_destroy). */
+JWF_API jwf_status jwf_get_probs(jwf_ctx* ctx, float** d_q, float** d_r);
+
+/* ---- discrete (stochastic) simulation (Section 3, "Stochastic update") --- */
+
+/* Start a run: the initial states d_F0 (uint8 [cells], values 0..3) are
+ * copied into the context as both the current state and the restart state of
+ * every env; t = 0 and episode = 0 for all envs. */
+JWF_API jwf_status jwf_load_state(jwf_ctx* ctx, const uint8_t* d_F0, void* stream);
+
+/* Restart the envs selected by d_env_mask (uint8 [N], nonzero = restart; NULL
+ * = all): state := initial state, t := 0, episode += 1 (a fresh random
+ * stream).  Section 4: episodes restart from randomised initial fires. */
+JWF_API jwf_status jwf_reset(jwf_ctx* ctx, const uint8_t* d_env_mask, void* stream);
+
+/* Air-tanker action (Section 4: water turns a burning cell into a burned
+ * one): every burning cell with d_mask[cell] != 0 (uint8 [cells]) becomes
+ * burned.  Other cells are untouched. */
+JWF_API jwf_status jwf_apply_action(jwf_ctx* ctx, const uint8_t* d_mask, void* stream);
+
+/* Advance every env by k >= 1 synchronous steps.  Step s of env e:
+ *   1. action: if d_drops is not NULL, d_drops[(s*N + e)*2 + {0,1}] is the
+ *      (column, row) centre of a square drop of radius drop_radius (clipped
+ *      to the grid; a negative centre means no drop); burning cells under it
+ *      become burned;
+ *   2. spread: every can-burn cell v with a burning neighbour u = v - Delta_d
+ *      ignites if any such u succeeds its draw U(v,d) < q[v][d]; every burning
+ *      cell stays burning if U(v) < p_continue, otherwise becomes burned
+ *      (all draws from the post-action state, all cells at once);
+ *   3. counts of burning and burned cells after the step go to
+ *      d_burning[s*N + e], d_burnt[s*N + e] (int32 [k][N], may be NULL);
+ *      done = (no burning cell) or (t >= t_max) goes to d_done[s*N + e]
+ *      (uint8 [k][N], may be NULL); with JWF_AUTO_RESET a done env restarts
+ *      (its reported counts are the pre-restart ones).
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
+ * = (y*W + x, t, env, 4*episode + slot); slot 0 -> directions 0..3, slot 1
+ * -> directions 4..7, slot 2 word 0 -> the remain-burning draw; uniform =
+ * (word >> 8) * 2^-24.  Results do not depend on the kernel chosen.
+ * Errors: JWF_ESTATE (no table or no state loaded), JWF_EINVAL (k < 1). */
+JWF_API jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
+                    int32_t* d_burnt, uint8_t* d_done, void* stream);
+
+/* Kernel choice for jwf_step (default JWF_KERNEL_AUTO). */
+typedef enum {
+    JWF_KERNEL_AUTO = 0,      /* resident when every env fits shared memory  */
+    JWF_KERNEL_PLAIN = 1,     /* one launch per step, state in global memory */
+    JWF_KERNEL_RESIDENT = 2   /* whole env in shared memory, k steps/launch  */
+} jwf_kernel;
+JWF_API jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_env);
+
+/* Instrumentation: while d_pairs (one uint64 on the device, owned by the
+ * caller) is set, the resident step kernel adds to it the number of
+ * (target, burning source) probability entries it compared -- the table
+ * reads of the byte model.  NULL switches counting off (the default). */
+JWF_API jwf_status jwf_set_pair_counter(jwf_ctx* ctx, unsigned long long* d_pairs);
+
+/* Borrowed device views: current state uint8 [cells] and int32 [N] step
+ * counters t and episode numbers (valid until the next call on ctx). */
+JWF_API jwf_status jwf_get_state(jwf_ctx* ctx, uint8_t** d_state, int32_t** d_t, int32_t** d_episode);
+
+/* ---- relaxed (raw-probabilities) update, Eqs. 5-10 ----------------------- */
+
+/* One deterministic step on probability planes (float [cells] each; p_bd =
+ * 1 - p_un - p_burn is implicit).  With m = d_mask[cell] in [0,1] (float
+ * [cells], NULL = 0) the tanker acts first: pb = (1 - m) p_burn.  Then
+ *   lam(v)  = sum_d pb(v - Delta_d) r[v][d]        (gamma(v) lambda, Eq. 4
+ *                                                  with b(u) := p_burn(u))
+ *   p_ign   = 1 - exp(-lam)                        (Eq. 4)
+ *   newly   = p_un p_ign                           (Eq. 5)
+ *   p_un'   = p_un - newly                         (Eq. 9)
+ *   p_burn' = newly + p_continue pb                (Eqs. 6, 8)
+ * Requires JWF_KEEP_RATES and a rate table.  Outputs must not alias inputs. */
+JWF_API jwf_status jwf_step_relaxed_fwd(jwf_ctx* ctx, const float* d_pun, const float* d_pburn,
+                                const float* d_mask, float* d_pun_out, float* d_pburn_out,
+                                void* stream);
+
+/* Adjoint of jwf_step_relaxed_fwd for the same inputs (d_pun, d_pburn,
+ * d_mask) and the adjoints d_gun_out, d_gburn_out of its outputs.  Writes
+ * the adjoints of the inputs to d_gun, d_gburn (float [cells]); writes
+ * d_glam[cell] = dL/dlam(v) (float [cells], may be NULL) for
+ * jwf_rates_bwd(); adds dL/dp_continue of this step to *d_gpc (one double,
+ * may be NULL; deterministic, summed in a fixed order).  Outputs must not
+ * alias inputs. */
+JWF_API jwf_status jwf_step_relaxed_bwd(jwf_ctx* ctx, const float* d_pun, const float* d_pburn,
+                                const float* d_mask, const float* d_gun_out,
+                                const float* d_gburn_out, float* d_gun, float* d_gburn,
+                                float* d_glam, double* d_gpc, void* stream);
+
+/* Parameter gradient through the rate table over n_steps relaxed steps.
+ * With lam(v) = sum_d pb(v - Delta_d) r[v][d] at every step t,
+ *   dL/dtheta += sum_t sum_{v,d} glam_t(v) pb_t(v - Delta_d) dr[v][d]/dtheta
+ * for theta = [p_base, alpha_w1, alpha_w2, alpha_s, alpha_gamma, mu_veg[C],
+ * mu_den[C]] (JWF_GRAD_SIZE doubles at d_gparams, accumulated, fixed
+ * summation order).  d_glam, d_pburn: float [n_steps][cells]; d_mask: float
+ * [n_steps][cells] or NULL.  The landcover, elevation and wind inputs are
+ * those given to jwf_precompute_probs (Eqs. 1-4 are differentiated exactly;
+ * a no-fuel source must carry no burning probability). */
+JWF_API jwf_status jwf_rates_bwd(jwf_ctx* ctx, int32_t n_steps, const float* d_glam,
+                         const float* d_pburn, const float* d_mask, const uint8_t* d_class,
+                         const float* d_dem, const float* d_wind_speed,
+                         const float* d_wind_dir, double* d_gparams, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JWF_H */

@@ -56,7 +56,7 @@ def lib():
             L.orc_discrete_rollout.argtypes = [ctypes.c_int, i32p, i32p, i64p, u8p, u8p, f32p,
                                                ctypes.c_float, i32p, ctypes.c_int, ctypes.c_uint64,
                                                i32p, i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                               i32p, i32p, u8p]
+                                               i32p, i32p, u8p, i32p]
             L.orc_discrete_rollout.restype = None
             L.orc_mc_outcomes.argtypes = [ctypes.c_int, ctypes.c_int, u8p, f32p, ctypes.c_float, u8p,
                                           ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
@@ -128,10 +128,12 @@ class Rollout:
     """Batch of (possibly ragged) grids advanced by the C oracle.
 
     H, W: int sequences per env.  F0: concatenated uint8 initial states.
-    q: concatenated float32 [cells, 8] table."""
+    q: concatenated float32 [cells, 8] table.  drops passed to step() are
+    [k, N, 2] for these N grids.  env_ids: the env index of each grid in the
+    random-number counter (default 0..N-1)."""
 
     def __init__(self, H, W, F0: np.ndarray, q: np.ndarray, p_continue: float, seed: int = 0,
-                 t_max: int = 0, auto_reset: bool = False, radius: int = 1):
+                 t_max: int = 0, auto_reset: bool = False, radius: int = 1, env_ids=None):
         self.H = np.ascontiguousarray(H, dtype=np.int32)
         self.W = np.ascontiguousarray(W, dtype=np.int32)
         self.N = int(self.H.shape[0])
@@ -149,6 +151,7 @@ class Rollout:
         self.t_max = int(t_max)
         self.auto_reset = bool(auto_reset)
         self.radius = int(radius)
+        self.env_ids = None if env_ids is None else np.ascontiguousarray(env_ids, dtype=np.int32)
 
     def step(self, k: int, drops: np.ndarray | None = None):
         """Advance k steps; drops int32 [k, N, 2] (column, row) or None.
@@ -163,7 +166,8 @@ class Rollout:
             _ptr(self.q, ctypes.c_float), ctypes.c_float(self.p_continue), _ptr(dr, ctypes.c_int32),
             self.radius, ctypes.c_uint64(self.seed), _ptr(self.t, ctypes.c_int32),
             _ptr(self.episode, ctypes.c_int32), k, self.t_max, int(self.auto_reset),
-            _ptr(burning, ctypes.c_int32), _ptr(burnt, ctypes.c_int32), _ptr(done, ctypes.c_uint8))
+            _ptr(burning, ctypes.c_int32), _ptr(burnt, ctypes.c_int32), _ptr(done, ctypes.c_uint8),
+            _ptr(self.env_ids, ctypes.c_int32))
         return burning, burnt, done
 
     def env_state(self, e: int) -> np.ndarray:

@@ -192,13 +192,16 @@ void orc_discrete_step(int H, int W, const uint8_t* F_in, uint8_t* F_out,
  *   auto_reset : when an env is done after a step, F_e := F0_e, t := 0,
  *                episode += 1 (the reported counts are the pre-reset ones)
  *   burning, burnt : int32 [k][N] outputs (may be NULL); done : uint8 [k][N]
+ *   env_ids : int32 [N] env index used in the random-number counter of each
+ *             grid (NULL: its position e), so that a sample of a larger batch
+ *             draws the same numbers as in the full batch
  * Done also holds when the post-step grid has no burning cell.
  * ------------------------------------------------------------------------- */
 void orc_discrete_rollout(int N, const int32_t* H, const int32_t* W, const int64_t* off,
                           uint8_t* F, const uint8_t* F0, const float* q, float p_continue,
                           const int32_t* drops, int R, uint64_t seed,
                           int32_t* t, int32_t* episode, int k, int t_max, int auto_reset,
-                          int32_t* burning, int32_t* burnt, uint8_t* done)
+                          int32_t* burning, int32_t* burnt, uint8_t* done, const int32_t* env_ids)
 {
     for (int step = 0; step < k; ++step) {
         for (int e = 0; e < N; ++e) {
@@ -212,8 +215,9 @@ void orc_discrete_rollout(int N, const int32_t* H, const int32_t* W, const int64
                 orc_drop_mask(H[e], W[e], c[0], c[1], R, mask);
             }
             int32_t nb = 0, nd = 0;
+            uint32_t env = env_ids != NULL ? (uint32_t)env_ids[e] : (uint32_t)e;
             orc_discrete_step(H[e], W[e], Fe, tmp, q + 8 * off[e], p_continue, mask, seed,
-                              (uint32_t)e, (uint32_t)t[e], (uint32_t)episode[e], &nb, &nd);
+                              env, (uint32_t)t[e], (uint32_t)episode[e], &nb, &nd);
             memcpy(Fe, tmp, n);
             free(tmp);
             free(mask);

@@ -1,0 +1,394 @@
+// jwf_api.cu -- the C ABI of libjwf (declared in include/jwf.h): argument
+// validation, context memory and kernel dispatch.  Every entry point returns a
+// jwf_status; nothing here throws, aborts or synchronises unless documented.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "jwf_internal.cuh"
+
+namespace {
+
+jwf_status fail(jwf_ctx* c, jwf_status st, const char* msg) {
+    if (c != nullptr) c->last_error = msg;
+    return st;
+}
+
+jwf_status cuda_fail(jwf_ctx* c, cudaError_t err, const char* where) {
+    if (c != nullptr) {
+        c->last_error = std::string(where) + ": " + cudaGetErrorString(err);
+    }
+    return err == cudaErrorMemoryAllocation ? JWF_ENOMEM : JWF_ECUDA;
+}
+
+#define JWF_CUDA_TRY(ctx, expr, where)                           \
+    do {                                                         \
+        cudaError_t err_ = (expr);                               \
+        if (err_ != cudaSuccess) return cuda_fail(ctx, err_, where); \
+    } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void free_all(jwf_ctx* c) {
+    void* ptrs[] = {c->d_H, c->d_W, c->d_off, c->d_order, c->d_tiles, c->d_state[0], c->d_state[1],
+                    c->d_F0, c->d_q, c->d_r, c->d_t, c->d_episode, c->d_cnt, c->d_flag,
+                    c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_wexp};
+    for (void* p : ptrs)
+        if (p != nullptr) cudaFree(p);
+}
+
+inline cudaStream_t S(void* stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+bool use_resident(const jwf_ctx* c) {
+    if (c->kernel == JWF_KERNEL_PLAIN) return false;
+    const int threads = c->threads_per_env > 0 ? c->threads_per_env
+                                               : jwf_resident_threads(c->maxH, c->maxW);
+    const size_t need = jwf_resident_smem(c->maxH, c->maxW, threads);
+    int limit = 0;
+    cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    return need + 64 <= (size_t)limit;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* jwf_status_string(jwf_status s) {
+    switch (s) {
+        case JWF_OK: return "ok";
+        case JWF_EINVAL: return "invalid argument";
+        case JWF_ENOMEM: return "out of memory";
+        case JWF_ECUDA: return "CUDA error";
+        case JWF_ETIMEOUT: return "device wait timed out";
+        case JWF_ESTATE: return "call out of order";
+        case JWF_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* jwf_last_error(const jwf_ctx* ctx) {
+    return ctx == nullptr ? "" : ctx->last_error.c_str();
+}
+
+int32_t jwf_n_envs(const jwf_ctx* ctx) { return ctx == nullptr ? 0 : ctx->N; }
+int64_t jwf_n_cells(const jwf_ctx* ctx) { return ctx == nullptr ? 0 : ctx->cells; }
+int64_t jwf_env_offset(const jwf_ctx* ctx, int32_t e) {
+    if (ctx == nullptr || e < 0 || e > ctx->N) return -1;
+    return ctx->off[e];
+}
+
+jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
+    if (out == nullptr) return JWF_EINVAL;
+    *out = nullptr;
+    if (cfg == nullptr || cfg->n_envs < 1 || cfg->h_H == nullptr || cfg->h_W == nullptr)
+        return JWF_EINVAL;
+    if (cfg->n_classes < 1 || cfg->n_classes > 16 || cfg->drop_radius < 0)
+        return JWF_EINVAL;
+    if ((cfg->flags & ~(JWF_AUTO_RESET | JWF_WIND_PER_CELL | JWF_KEEP_RATES)) != 0u) return JWF_EINVAL;
+    const int32_t N = cfg->n_envs;
+    for (int32_t e = 0; e < N; ++e) {
+        if (cfg->h_H[e] < 1 || cfg->h_W[e] < 1 || cfg->h_H[e] > 65535 || cfg->h_W[e] > 65535)
+            return JWF_EINVAL;
+        // Philox's cell counter word is 32 bits
+        if ((int64_t)cfg->h_H[e] * cfg->h_W[e] > (int64_t)0x7fffffff) return JWF_EINVAL;
+    }
+    jwf_ctx* c = new (std::nothrow) jwf_ctx();
+    if (c == nullptr) return JWF_ENOMEM;
+    c->N = N;
+    c->n_classes = cfg->n_classes;
+    c->seed = cfg->seed;
+    c->t_max = cfg->t_max;
+    c->drop_radius = cfg->drop_radius;
+    c->flags = cfg->flags;
+    c->H.assign(cfg->h_H, cfg->h_H + N);
+    c->W.assign(cfg->h_W, cfg->h_W + N);
+    c->off.resize(N + 1);
+    c->off[0] = 0;
+    std::vector<int2> tiles;
+    for (int32_t e = 0; e < N; ++e) {
+        const int64_t n = (int64_t)c->H[e] * c->W[e];
+        c->off[e + 1] = c->off[e] + n;
+        c->maxH = std::max(c->maxH, c->H[e]);
+        c->maxW = std::max(c->maxW, c->W[e]);
+        c->max_env_cells = std::max(c->max_env_cells, n);
+        for (int64_t s = 0; s < n; s += JWF_TILE) tiles.push_back(make_int2(e, (int)s));
+    }
+    c->cells = c->off[N];
+    c->n_tiles = (int64_t)tiles.size();
+    std::vector<int32_t> order(N);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return (int64_t)c->H[a] * c->W[a] > (int64_t)c->H[b] * c->W[b];
+    });
+
+    cudaError_t err = cudaGetDevice(&c->device);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->partial_cap = (int64_t)std::max(c->num_sms, 1) * 8 * 40;
+    const bool rates = (c->flags & JWF_KEEP_RATES) != 0u;
+    if (err == cudaSuccess) err = dev_alloc(&c->d_H, N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_W, N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_off, N + 1);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_order, N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tiles, tiles.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_state[0], (size_t)c->cells);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_state[1], (size_t)c->cells);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_F0, (size_t)c->cells);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_q, (size_t)c->cells * 8);
+    if (err == cudaSuccess && rates) err = dev_alloc(&c->d_r, (size_t)c->cells * 8);
+    if (err == cudaSuccess && rates) err = dev_alloc(&c->d_glam, (size_t)c->cells);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_t, N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_episode, N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_cnt, 2 * (size_t)N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_flag, N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_status, 1);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_queue, 2);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_partials, (size_t)c->partial_cap);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_red_counter, 1);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_wexp, (size_t)N * 8);
+    if (err == cudaSuccess) err = cudaMemcpy(c->d_H, c->H.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(c->d_W, c->W.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(c->d_off, c->off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(c->d_order, order.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(c->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemset(c->d_t, 0, N * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMemset(c->d_episode, 0, N * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMemset(c->d_cnt, 0, 2 * N * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMemset(c->d_flag, 0, N);
+    if (err == cudaSuccess) err = cudaMemset(c->d_status, 0, sizeof(uint32_t));
+    if (err == cudaSuccess) err = cudaMemset(c->d_queue, 0, 2 * sizeof(uint32_t));
+    if (err == cudaSuccess) err = cudaMemset(c->d_red_counter, 0, sizeof(uint32_t));
+    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) {
+        const jwf_status st = (err == cudaErrorMemoryAllocation) ? JWF_ENOMEM : JWF_ECUDA;
+        free_all(c);
+        delete c;
+        cudaGetLastError();
+        return st;
+    }
+    *out = c;
+    return JWF_OK;
+}
+
+jwf_status jwf_destroy(jwf_ctx* ctx) {
+    if (ctx == nullptr) return JWF_OK;
+    const cudaError_t err = cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+    return err == cudaSuccess ? JWF_OK : JWF_ECUDA;
+}
+
+jwf_status jwf_set_params(jwf_ctx* ctx, const jwf_params* p) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (p == nullptr || p->h_mu_veg == nullptr || p->h_mu_den == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_set_params: null pointer");
+    const float sc[] = {p->p_base, p->alpha_w1, p->alpha_w2, p->alpha_s, p->alpha_gamma, p->p_continue,
+                        p->cell_size};
+    for (float v : sc)
+        if (!std::isfinite(v)) return fail(ctx, JWF_EINVAL, "jwf_set_params: non-finite parameter");
+    if (p->p_continue < 0.f || p->p_continue > 1.f)
+        return fail(ctx, JWF_EINVAL, "jwf_set_params: p_continue outside [0, 1]");
+    if (p->p_base < 0.f || p->alpha_gamma < 0.f || !(p->cell_size > 0.f))
+        return fail(ctx, JWF_EINVAL, "jwf_set_params: p_base, alpha_gamma must be >= 0, cell_size > 0");
+    for (int k = 0; k < ctx->n_classes; ++k) {
+        const float a = p->h_mu_veg[k], b = p->h_mu_den[k];
+        if (!(a >= -1.f && a <= 1.f && b >= -1.f && b <= 1.f))
+            return fail(ctx, JWF_EINVAL, "jwf_set_params: mu outside [-1, 1]");
+    }
+    JwfDevParams P{};
+    P.p_base = p->p_base;
+    P.alpha_w1 = p->alpha_w1;
+    P.alpha_w2 = p->alpha_w2;
+    P.alpha_s = p->alpha_s;
+    P.alpha_gamma = p->alpha_gamma;
+    P.p_continue = p->p_continue;
+    P.cell_size = p->cell_size;
+    P.n_classes = ctx->n_classes;
+    for (int k = 0; k < ctx->n_classes; ++k) {
+        P.mu_veg[k] = p->h_mu_veg[k];
+        P.mu_den[k] = p->h_mu_den[k];
+    }
+    ctx->P = P;
+    ctx->have_params = true;
+    return JWF_OK;
+}
+
+jwf_status jwf_sync(jwf_ctx* ctx, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    JWF_CUDA_TRY(ctx, cudaStreamSynchronize(S(stream)), "jwf_sync");
+    uint32_t st = 0;
+    JWF_CUDA_TRY(ctx, cudaMemcpy(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost), "jwf_sync");
+    if (st != 0u) {
+        JWF_CUDA_TRY(ctx, cudaMemset(ctx->d_status, 0, sizeof(uint32_t)), "jwf_sync");
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "device status word 0x%x", st);
+        ctx->last_error = buf;
+        return JWF_ETIMEOUT;
+    }
+    return JWF_OK;
+}
+
+jwf_status jwf_precompute_probs(jwf_ctx* ctx, const uint8_t* d_class, const float* d_dem,
+                                const float* d_wind_speed, const float* d_wind_dir, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_precompute_probs: no parameters set");
+    if (d_class == nullptr || d_dem == nullptr || d_wind_speed == nullptr || d_wind_dir == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_precompute_probs: null pointer");
+    JWF_CUDA_TRY(ctx, jwf_launch_prob_table(ctx, d_class, d_dem, d_wind_speed, d_wind_dir, S(stream)),
+                 "jwf_precompute_probs");
+    ctx->have_table = true;
+    ctx->have_rates = (ctx->flags & JWF_KEEP_RATES) != 0u;
+    return JWF_OK;
+}
+
+jwf_status jwf_set_probs(jwf_ctx* ctx, const float* d_q, const float* d_r, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_q == nullptr) return fail(ctx, JWF_EINVAL, "jwf_set_probs: d_q is null");
+    if (d_r != nullptr && !(ctx->flags & JWF_KEEP_RATES))
+        return fail(ctx, JWF_EUNSUPPORTED, "jwf_set_probs: context has no rate table (JWF_KEEP_RATES)");
+    const size_t bytes = (size_t)ctx->cells * 8 * sizeof(float);
+    JWF_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_q, d_q, bytes, cudaMemcpyDeviceToDevice, S(stream)), "jwf_set_probs");
+    if (d_r != nullptr) {
+        JWF_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_r, d_r, bytes, cudaMemcpyDeviceToDevice, S(stream)),
+                     "jwf_set_probs");
+        ctx->have_rates = true;
+    }
+    ctx->have_table = true;
+    return JWF_OK;
+}
+
+jwf_status jwf_get_probs(jwf_ctx* ctx, float** d_q, float** d_r) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_q) *d_q = ctx->d_q;
+    if (d_r) *d_r = ctx->d_r;
+    return JWF_OK;
+}
+
+jwf_status jwf_load_state(jwf_ctx* ctx, const uint8_t* d_F0, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_F0 == nullptr) return fail(ctx, JWF_EINVAL, "jwf_load_state: null pointer");
+    JWF_CUDA_TRY(ctx, jwf_launch_load(ctx, d_F0, S(stream)), "jwf_load_state");
+    ctx->have_state = true;
+    return JWF_OK;
+}
+
+jwf_status jwf_reset(jwf_ctx* ctx, const uint8_t* d_env_mask, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_reset: no state loaded");
+    JWF_CUDA_TRY(ctx, jwf_launch_reset(ctx, d_env_mask, S(stream)), "jwf_reset");
+    return JWF_OK;
+}
+
+jwf_status jwf_apply_action(jwf_ctx* ctx, const uint8_t* d_mask, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_mask == nullptr) return fail(ctx, JWF_EINVAL, "jwf_apply_action: null mask");
+    if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_apply_action: no state loaded");
+    JWF_CUDA_TRY(ctx, jwf_launch_action(ctx, d_mask, S(stream)), "jwf_apply_action");
+    return JWF_OK;
+}
+
+jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
+                    int32_t* d_burnt, uint8_t* d_done, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (k < 1) return fail(ctx, JWF_EINVAL, "jwf_step: k < 1");
+    if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_step: no parameters set");
+    if (!ctx->have_table) return fail(ctx, JWF_ESTATE, "jwf_step: no probability table");
+    if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_step: no state loaded");
+    if (ctx->kernel == JWF_KERNEL_RESIDENT && !use_resident(ctx))
+        return fail(ctx, JWF_EUNSUPPORTED, "jwf_step: largest env does not fit shared memory");
+    cudaError_t err;
+    if (use_resident(ctx))
+        err = jwf_launch_step_resident(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
+    else
+        err = jwf_launch_step_plain(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "jwf_step");
+    return JWF_OK;
+}
+
+jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_env) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (kernel != JWF_KERNEL_AUTO && kernel != JWF_KERNEL_PLAIN && kernel != JWF_KERNEL_RESIDENT)
+        return fail(ctx, JWF_EINVAL, "jwf_set_kernel: unknown kernel");
+    if (threads_per_env != 0 && (threads_per_env < 32 || threads_per_env > 256 || threads_per_env % 32 != 0))
+        return fail(ctx, JWF_EINVAL, "jwf_set_kernel: threads_per_env must be 0 or a multiple of 32 in [32, 256]");
+    ctx->kernel = kernel;
+    ctx->threads_per_env = threads_per_env;
+    return JWF_OK;
+}
+
+jwf_status jwf_set_pair_counter(jwf_ctx* ctx, unsigned long long* d_pairs) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    ctx->d_pairs = d_pairs;
+    return JWF_OK;
+}
+
+jwf_status jwf_get_state(jwf_ctx* ctx, uint8_t** d_state, int32_t** d_t, int32_t** d_episode) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_state) *d_state = ctx->d_state[ctx->cur];
+    if (d_t) *d_t = ctx->d_t;
+    if (d_episode) *d_episode = ctx->d_episode;
+    return JWF_OK;
+}
+
+jwf_status jwf_step_relaxed_fwd(jwf_ctx* ctx, const float* d_pun, const float* d_pburn,
+                                const float* d_mask, float* d_pun_out, float* d_pburn_out,
+                                void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_pun == nullptr || d_pburn == nullptr || d_pun_out == nullptr || d_pburn_out == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_step_relaxed_fwd: null pointer");
+    if (d_pun_out == d_pun || d_pun_out == d_pburn || d_pburn_out == d_pun || d_pburn_out == d_pburn)
+        return fail(ctx, JWF_EINVAL, "jwf_step_relaxed_fwd: outputs alias inputs");
+    if (!ctx->have_params || !ctx->have_rates)
+        return fail(ctx, JWF_ESTATE, "jwf_step_relaxed_fwd: needs parameters and a rate table");
+    JWF_CUDA_TRY(ctx, jwf_launch_relaxed_fwd(ctx, d_pun, d_pburn, d_mask, d_pun_out, d_pburn_out, S(stream)),
+                 "jwf_step_relaxed_fwd");
+    return JWF_OK;
+}
+
+jwf_status jwf_step_relaxed_bwd(jwf_ctx* ctx, const float* d_pun, const float* d_pburn,
+                                const float* d_mask, const float* d_gun_out,
+                                const float* d_gburn_out, float* d_gun, float* d_gburn,
+                                float* d_glam, double* d_gpc, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_pun == nullptr || d_pburn == nullptr || d_gun_out == nullptr || d_gburn_out == nullptr ||
+        d_gun == nullptr || d_gburn == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_step_relaxed_bwd: null pointer");
+    const void* ins[] = {d_pun, d_pburn, d_mask, d_gun_out, d_gburn_out};
+    const void* outs[] = {d_gun, d_gburn, d_glam};
+    for (const void* o : outs)
+        for (const void* i : ins)
+            if (o != nullptr && o == i) return fail(ctx, JWF_EINVAL, "jwf_step_relaxed_bwd: outputs alias inputs");
+    if (!ctx->have_params || !ctx->have_rates)
+        return fail(ctx, JWF_ESTATE, "jwf_step_relaxed_bwd: needs parameters and a rate table");
+    float* glam = d_glam != nullptr ? d_glam : ctx->d_glam;
+    JWF_CUDA_TRY(ctx, jwf_launch_relaxed_bwd(ctx, d_pun, d_pburn, d_mask, d_gun_out, d_gburn_out, d_gun, d_gburn,
+                                             glam, d_gpc, S(stream)),
+                 "jwf_step_relaxed_bwd");
+    return JWF_OK;
+}
+
+jwf_status jwf_rates_bwd(jwf_ctx* ctx, int32_t n_steps, const float* d_glam,
+                         const float* d_pburn, const float* d_mask, const uint8_t* d_class,
+                         const float* d_dem, const float* d_wind_speed,
+                         const float* d_wind_dir, double* d_gparams, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (n_steps < 0) return fail(ctx, JWF_EINVAL, "jwf_rates_bwd: n_steps < 0");
+    if (d_glam == nullptr || d_pburn == nullptr || d_class == nullptr || d_dem == nullptr ||
+        d_wind_speed == nullptr || d_wind_dir == nullptr || d_gparams == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_rates_bwd: null pointer");
+    if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_rates_bwd: no parameters set");
+    if (n_steps == 0) return JWF_OK;
+    JWF_CUDA_TRY(ctx, jwf_launch_rates_bwd(ctx, n_steps, d_glam, d_pburn, d_mask, d_class, d_dem, d_wind_speed,
+                                           d_wind_dir, d_gparams, S(stream)),
+                 "jwf_rates_bwd");
+    return JWF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// jwf_internal.cuh -- shared definitions of libjwf's translation units.
+//
+// Device-side building blocks (directions, Philox4x32-10, 24-bit uniforms),
+// the context struct and the host-side launchers that jwf_api.cu calls.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/jwf.h"
+
+#define JWF_MAX_CLASSES 64
+
+// ---------------------------------------------------------------------------
+// Directions: Delta_d has angle d*45 degrees, east = 0, counter-clockwise
+// (Section 3, below Eq. 2).  Rows grow southward.  The source of target
+// (row y, column x) in direction d is (y - DR[d], x - DX[d]).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int jwf_dx(int d) {
+    return (d == 0 || d == 1 || d == 7) ? 1 : (d == 3 || d == 4 || d == 5) ? -1 : 0;
+}
+__host__ __device__ constexpr int jwf_dr(int d) {
+    return (d == 1 || d == 2 || d == 3) ? -1 : (d == 5 || d == 6 || d == 7) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+//   (c0,c1,c2,c3) <- (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+// with the key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 jwf_philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c.y ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c.w ^ k1;
+        c = make_uint4(n0, (uint32_t)p1, n2, (uint32_t)p0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Uniform in [0,1) with 24 random bits; exact in float.
+__device__ __forceinline__ float jwf_u24(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
+
+// ---------------------------------------------------------------------------
+// Parameters as the kernels see them (by value).
+// ---------------------------------------------------------------------------
+struct JwfDevParams {
+    float p_base, alpha_w1, alpha_w2, alpha_s, alpha_gamma, p_continue, cell_size;
+    int32_t n_classes;
+    float mu_veg[JWF_MAX_CLASSES];
+    float mu_den[JWF_MAX_CLASSES];
+};
+
+// Per-cell kernels walk blocks of JWF_TILE consecutive cells of one env.
+#define JWF_TILE 256
+
+struct jwf_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int32_t N = 0;
+    int64_t cells = 0;
+    int32_t maxH = 0, maxW = 0;
+    int64_t max_env_cells = 0;
+    int32_t n_classes = 0;
+    uint64_t seed = 0;
+    int32_t t_max = 0;
+    int32_t drop_radius = 1;
+    uint32_t flags = 0;
+    std::vector<int32_t> H, W;
+    std::vector<int64_t> off;            // N + 1
+
+    // device memory owned by the context
+    int32_t* d_H = nullptr;
+    int32_t* d_W = nullptr;
+    int64_t* d_off = nullptr;
+    int32_t* d_order = nullptr;          // env processing order, largest first
+    int2* d_tiles = nullptr;             // (env, first local cell) per JWF_TILE block
+    int64_t n_tiles = 0;
+    uint8_t* d_state[2] = {nullptr, nullptr};
+    int cur = 0;                         // index of the current state buffer
+    uint8_t* d_F0 = nullptr;
+    float* d_q = nullptr;
+    float* d_r = nullptr;
+    int32_t* d_t = nullptr;
+    int32_t* d_episode = nullptr;
+    int32_t* d_cnt = nullptr;            // [2][N] per-step counts (plain path)
+    uint8_t* d_flag = nullptr;           // [N] per-env done/reset flags
+    uint32_t* d_status = nullptr;        // device error word
+    uint32_t* d_queue = nullptr;         // [2] work queue cursor, exit counter
+    double* d_partials = nullptr;        // deterministic reduction scratch
+    int64_t partial_cap = 0;             // doubles available in d_partials
+    uint32_t* d_red_counter = nullptr;   // blocks finished (last-block reduction)
+    float* d_glam = nullptr;             // [cells] adjoint scratch of the relaxed step
+    unsigned long long* d_pairs = nullptr;  // caller's instrumentation counter (not owned)
+    float2* d_wexp = nullptr;            // [N][8] wind exponent (hi, lo) scratch of the table build
+
+    JwfDevParams P{};
+    bool have_params = false, have_table = false, have_rates = false, have_state = false;
+    jwf_kernel kernel = JWF_KERNEL_AUTO;
+    int threads_per_env = 0;             // 0: chosen by size
+    std::string last_error;
+};
+
+// Device status word bits.
+#define JWF_DEVERR_INDEX 0x1u      // an index check failed (checked build)
+
+// ---------------------------------------------------------------------------
+// Launchers (host functions; each returns cudaGetLastError() of its launch).
+// ---------------------------------------------------------------------------
+cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
+                                  const float* ws, const float* wd, cudaStream_t s);
+cudaError_t jwf_launch_rates_bwd(jwf_ctx* c, int32_t n_steps, const float* glam,
+                                 const float* pburn, const float* mask, const uint8_t* cls,
+                                 const float* dem, const float* ws, const float* wd,
+                                 double* gparams, cudaStream_t s);
+
+cudaError_t jwf_launch_load(jwf_ctx* c, const uint8_t* F0, cudaStream_t s);
+cudaError_t jwf_launch_reset(jwf_ctx* c, const uint8_t* env_mask, cudaStream_t s);
+cudaError_t jwf_launch_action(jwf_ctx* c, const uint8_t* mask, cudaStream_t s);
+cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
+                                  int32_t* burnt, uint8_t* done, cudaStream_t s);
+cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops,
+                                     int32_t* burning, int32_t* burnt, uint8_t* done,
+                                     cudaStream_t s);
+// shared memory a resident launch needs for env shape (H, W) with `threads`
+size_t jwf_resident_smem(int32_t H, int32_t W, int threads);
+int jwf_resident_threads(int32_t H, int32_t W);
+
+cudaError_t jwf_launch_relaxed_fwd(const jwf_ctx* c, const float* pun, const float* pburn,
+                                   const float* mask, float* pun_out, float* pburn_out,
+                                   cudaStream_t s);
+cudaError_t jwf_launch_relaxed_bwd(jwf_ctx* c, const float* pun, const float* pburn,
+                                   const float* mask, const float* gun_out,
+                                   const float* gburn_out, float* gun, float* gburn,
+                                   float* glam, double* gpc, cudaStream_t s);

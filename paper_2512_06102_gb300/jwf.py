@@ -1,0 +1,298 @@
+"""ctypes binding of libjwf (include/jwf.h): argument marshalling only.
+
+Every computation runs in libjwf's CUDA kernels; this module turns torch
+tensors into device pointers and the current torch stream into the
+cudaStream_t argument.  There is no CPU fallback: loading fails loudly when
+libjwf has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libjwf.so")
+
+JWF_AUTO_RESET = 0x1
+JWF_WIND_PER_CELL = 0x2
+JWF_KEEP_RATES = 0x4
+
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_RESIDENT = 0, 1, 2
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
+          4: "device wait timed out", 5: "call out of order", 6: "unsupported"}
+
+
+class JwfError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_envs", ctypes.c_int32), ("h_H", ctypes.POINTER(ctypes.c_int32)),
+                ("h_W", ctypes.POINTER(ctypes.c_int32)), ("n_classes", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("t_max", ctypes.c_int32), ("drop_radius", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("p_base", ctypes.c_float), ("alpha_w1", ctypes.c_float), ("alpha_w2", ctypes.c_float),
+                ("alpha_s", ctypes.c_float), ("alpha_gamma", ctypes.c_float), ("p_continue", ctypes.c_float),
+                ("cell_size", ctypes.c_float), ("h_mu_veg", ctypes.POINTER(ctypes.c_float)),
+                ("h_mu_den", ctypes.POINTER(ctypes.c_float))]
+
+
+# exported symbol -> (restype, argtypes)
+_VP = ctypes.c_void_p
+_SIGS = {
+    "jwf_create": (ctypes.c_int, [ctypes.POINTER(_Config), ctypes.POINTER(_VP)]),
+    "jwf_destroy": (ctypes.c_int, [_VP]),
+    "jwf_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(_Params)]),
+    "jwf_sync": (ctypes.c_int, [_VP, _VP]),
+    "jwf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "jwf_last_error": (ctypes.c_char_p, [_VP]),
+    "jwf_n_envs": (ctypes.c_int32, [_VP]),
+    "jwf_n_cells": (ctypes.c_int64, [_VP]),
+    "jwf_env_offset": (ctypes.c_int64, [_VP, ctypes.c_int32]),
+    "jwf_precompute_probs": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "jwf_set_probs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "jwf_get_probs": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "jwf_load_state": (ctypes.c_int, [_VP, _VP, _VP]),
+    "jwf_reset": (ctypes.c_int, [_VP, _VP, _VP]),
+    "jwf_apply_action": (ctypes.c_int, [_VP, _VP, _VP]),
+    "jwf_step": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP]),
+    "jwf_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int32]),
+    "jwf_set_pair_counter": (ctypes.c_int, [_VP, _VP]),
+    "jwf_get_state": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "jwf_step_relaxed_fwd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "jwf_step_relaxed_bwd": (ctypes.c_int, [_VP] * 11),
+    "jwf_rates_bwd": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 9),
+}
+EXPORTS = tuple(_SIGS)
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libjwf (built by paper_2512_06102_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libjwf is not built ({LIB_PATH} missing): run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("libjwf takes device tensors")
+        if not t.is_contiguous():
+            raise ValueError("libjwf takes contiguous tensors")
+        return t.data_ptr()
+    return int(t)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class _DevView:
+    """Zero-copy torch view of a device pointer owned by libjwf."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                          "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _view(ptr: int, shape, dtype: torch.dtype) -> torch.Tensor:
+    typestr = {torch.uint8: "|u1", torch.int32: "<i4", torch.float32: "<f4"}[dtype]
+    return torch.as_tensor(_DevView(ptr, shape, typestr), device="cuda")
+
+
+@dataclass
+class ParamSet:
+    p_base: float = 0.58
+    alpha_w1: float = 0.045
+    alpha_w2: float = 0.131
+    alpha_s: float = 0.078
+    alpha_gamma: float = 1.0
+    p_continue: float = 0.5
+    cell_size: float = 30.0
+    mu_veg: np.ndarray | None = None
+    mu_den: np.ndarray | None = None
+
+    @staticmethod
+    def from_any(p) -> "ParamSet":
+        if isinstance(p, ParamSet):
+            return p
+        d = p if isinstance(p, dict) else p.__dict__
+        keys = ParamSet.__dataclass_fields__.keys()
+        return ParamSet(**{k: d[k] for k in keys if k in d})
+
+
+class Sim:
+    """A batch of wildfire grids on the current CUDA device (one jwf_ctx)."""
+
+    def __init__(self, H, W, n_envs: int | None = None, n_classes: int = 11, seed: int = 0,
+                 t_max: int = 0, drop_radius: int = 1, auto_reset: bool = False,
+                 wind_per_cell: bool = False, keep_rates: bool = False):
+        L = lib()
+        if np.isscalar(H):
+            assert n_envs is not None
+            Hs = np.full(n_envs, int(H), np.int32)
+            Ws = np.full(n_envs, int(W), np.int32)
+        else:
+            Hs = np.ascontiguousarray(H, np.int32)
+            Ws = np.ascontiguousarray(W, np.int32)
+        self.H, self.W = Hs, Ws
+        self.N = int(Hs.shape[0])
+        self.n_classes = int(n_classes)
+        flags = ((JWF_AUTO_RESET if auto_reset else 0) | (JWF_WIND_PER_CELL if wind_per_cell else 0)
+                 | (JWF_KEEP_RATES if keep_rates else 0))
+        cfg = _Config(self.N, Hs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                      Ws.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.n_classes,
+                      ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), int(t_max), int(drop_radius), flags)
+        torch.cuda.init()
+        h = _VP()
+        st = L.jwf_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != 0:
+            raise JwfError(st, "jwf_create")
+        self._h = h
+        self.cells = int(L.jwf_n_cells(h))
+        self.offsets = np.array([L.jwf_env_offset(h, e) for e in range(self.N + 1)], np.int64)
+        self.params: ParamSet | None = None
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, st: int, where: str):
+        if st != 0:
+            raise JwfError(st, where, lib().jwf_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().jwf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        self._check(lib().jwf_sync(self._h, _stream(stream)), "jwf_sync")
+
+    # -- parameters and tables ---------------------------------------------
+    def set_params(self, p):
+        p = ParamSet.from_any(p)
+        mv = np.ascontiguousarray(p.mu_veg, np.float32)
+        md = np.ascontiguousarray(p.mu_den, np.float32)
+        assert mv.shape == (self.n_classes,) and md.shape == (self.n_classes,)
+        cp = _Params(p.p_base, p.alpha_w1, p.alpha_w2, p.alpha_s, p.alpha_gamma, p.p_continue, p.cell_size,
+                     mv.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                     md.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        self._check(lib().jwf_set_params(self._h, ctypes.byref(cp)), "jwf_set_params")
+        self.params = p
+
+    def precompute_probs(self, cls, dem, wind_speed, wind_dir, stream=None):
+        self._check(lib().jwf_precompute_probs(self._h, _ptr(cls), _ptr(dem), _ptr(wind_speed), _ptr(wind_dir),
+                                               _stream(stream)), "jwf_precompute_probs")
+
+    def set_probs(self, q, r=None, stream=None):
+        self._check(lib().jwf_set_probs(self._h, _ptr(q), _ptr(r), _stream(stream)), "jwf_set_probs")
+
+    def probs(self):
+        """Borrowed views (q, r) of the context's tables, float32 [cells, 8]."""
+        q, r = _VP(), _VP()
+        self._check(lib().jwf_get_probs(self._h, ctypes.byref(q), ctypes.byref(r)), "jwf_get_probs")
+        qt = _view(q.value, (self.cells, 8), torch.float32)
+        rt = _view(r.value, (self.cells, 8), torch.float32) if r.value else None
+        return qt, rt
+
+    # -- discrete simulation -----------------------------------------------
+    def load_state(self, F0, stream=None):
+        self._check(lib().jwf_load_state(self._h, _ptr(F0), _stream(stream)), "jwf_load_state")
+
+    def reset(self, env_mask=None, stream=None):
+        self._check(lib().jwf_reset(self._h, _ptr(env_mask), _stream(stream)), "jwf_reset")
+
+    def apply_action(self, mask, stream=None):
+        self._check(lib().jwf_apply_action(self._h, _ptr(mask), _stream(stream)), "jwf_apply_action")
+
+    def set_kernel(self, kernel: int = KERNEL_AUTO, threads_per_env: int = 0):
+        self._check(lib().jwf_set_kernel(self._h, int(kernel), int(threads_per_env)), "jwf_set_kernel")
+
+    def set_pair_counter(self, counter):
+        """counter: int64 device tensor of one element, or None (off)."""
+        self._check(lib().jwf_set_pair_counter(self._h, _ptr(counter)), "jwf_set_pair_counter")
+
+    def step(self, k: int = 1, drops=None, burning=None, burnt=None, done=None, stream=None):
+        """Advance k steps; returns the (burning, burnt, done) tensors [k, N]."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if burning is None:
+            burning = torch.empty((k, self.N), dtype=torch.int32, device=dev)
+        if burnt is None:
+            burnt = torch.empty((k, self.N), dtype=torch.int32, device=dev)
+        if done is None:
+            done = torch.empty((k, self.N), dtype=torch.uint8, device=dev)
+        self._check(lib().jwf_step(self._h, int(k), _ptr(drops), _ptr(burning), _ptr(burnt), _ptr(done),
+                                   _stream(stream)), "jwf_step")
+        return burning, burnt, done
+
+    def state_views(self):
+        """Borrowed views (state uint8 [cells], t int32 [N], episode int32 [N])."""
+        s, t, e = _VP(), _VP(), _VP()
+        self._check(lib().jwf_get_state(self._h, ctypes.byref(s), ctypes.byref(t), ctypes.byref(e)),
+                    "jwf_get_state")
+        return (_view(s.value, (self.cells,), torch.uint8), _view(t.value, (self.N,), torch.int32),
+                _view(e.value, (self.N,), torch.int32))
+
+    def state(self) -> torch.Tensor:
+        return self.state_views()[0].clone()
+
+    # -- relaxed update ----------------------------------------------------
+    def relaxed_fwd(self, pun, pburn, mask=None, pun_out=None, pburn_out=None, stream=None):
+        if pun_out is None:
+            pun_out = torch.empty_like(pun)
+        if pburn_out is None:
+            pburn_out = torch.empty_like(pburn)
+        self._check(lib().jwf_step_relaxed_fwd(self._h, _ptr(pun), _ptr(pburn), _ptr(mask), _ptr(pun_out),
+                                               _ptr(pburn_out), _stream(stream)), "jwf_step_relaxed_fwd")
+        return pun_out, pburn_out
+
+    def relaxed_bwd(self, pun, pburn, gun_out, gburn_out, mask=None, gun=None, gburn=None, glam=None,
+                    gpc=None, stream=None):
+        if gun is None:
+            gun = torch.empty_like(pun)
+        if gburn is None:
+            gburn = torch.empty_like(pburn)
+        self._check(lib().jwf_step_relaxed_bwd(self._h, _ptr(pun), _ptr(pburn), _ptr(mask), _ptr(gun_out),
+                                               _ptr(gburn_out), _ptr(gun), _ptr(gburn), _ptr(glam), _ptr(gpc),
+                                               _stream(stream)), "jwf_step_relaxed_bwd")
+        return gun, gburn
+
+    def rates_bwd(self, glam, pburn, cls, dem, wind_speed, wind_dir, gparams, mask=None, stream=None):
+        n = glam.shape[0] if glam.dim() == 2 else 1
+        self._check(lib().jwf_rates_bwd(self._h, int(n), _ptr(glam), _ptr(pburn), _ptr(mask), _ptr(cls),
+                                        _ptr(dem), _ptr(wind_speed), _ptr(wind_dir), _ptr(gparams),
+                                        _stream(stream)), "jwf_rates_bwd")
+        return gparams
+
+    @property
+    def grad_size(self) -> int:
+        return 5 + 2 * self.n_classes

@@ -108,56 +108,117 @@ class Scenario:
         return a.reshape(self.N, int(self.H[0]), int(self.W[0]), *a.shape[1:])
 
 
-def _value_noise(rng: np.random.Generator, H: int, W: int, spacing: float) -> np.ndarray:
-    gh = int(math.ceil(H / spacing)) + 2
-    gw = int(math.ceil(W / spacing)) + 2
-    lat = rng.random((gh, gw))
-    ys = np.arange(H) / spacing
-    xs = np.arange(W) / spacing
-    y0 = np.floor(ys).astype(np.int64)
-    x0 = np.floor(xs).astype(np.int64)
-    fy = (ys - y0)[:, None]
-    fx = (xs - x0)[None, :]
-    a = lat[y0][:, x0]
-    b = lat[y0][:, x0 + 1]
-    c = lat[y0 + 1][:, x0]
-    d = lat[y0 + 1][:, x0 + 1]
-    return (a * (1 - fx) + b * fx) * (1 - fy) + (c * (1 - fx) + d * fx) * fy
-
-
-def fbm(rng: np.random.Generator, H: int, W: int, octaves: int = 6) -> np.ndarray:
-    spacing = max(1.0, min(H, W) / 4.0)
-    amp, total, norm = 1.0, np.zeros((H, W)), 0.0
+def _octave_spacings(H: int, W: int, octaves: int = 6):
+    sp, out = max(1.0, min(H, W) / 4.0), []
     for _ in range(octaves):
-        total += amp * _value_noise(rng, H, W, spacing)
+        out.append(sp)
+        sp = max(1.0, sp / 2.0)
+    return out
+
+
+def _lattice_shape(H: int, W: int, spacing: float):
+    return int(math.ceil(H / spacing)) + 2, int(math.ceil(W / spacing)) + 2
+
+
+def _device():
+    import torch
+    return torch.device("cuda") if torch.cuda.is_available() else torch.device("cpu")
+
+
+def _interp(lat, H: int, W: int, spacing: float):
+    """Bilinear value noise for a batch of lattices [n, gh, gw] -> [n, H, W]
+    (separable: along x on the lattice rows, then along y).  float64 torch."""
+    import torch
+    dev = lat.device
+    ys = torch.arange(H, dtype=torch.float64, device=dev) / spacing
+    xs = torch.arange(W, dtype=torch.float64, device=dev) / spacing
+    y0 = torch.floor(ys).long()
+    x0 = torch.floor(xs).long()
+    fy = (ys - y0)[None, :, None]
+    fx = (xs - x0)[None, None, :]
+    rows = lat.index_select(2, x0) * (1 - fx) + lat.index_select(2, x0 + 1) * fx     # [n, gh, W]
+    return rows.index_select(1, y0) * (1 - fy) + rows.index_select(1, y0 + 1) * fy
+
+
+def _fbm_batch(lats, H: int, W: int):
+    """fBm from per-octave lattices (list over octaves of [n, gh, gw] numpy)."""
+    import torch
+    dev = _device()
+    amp, norm = 1.0, 0.0
+    total = None
+    for lat, sp in zip(lats, _octave_spacings(H, W)):
+        v = amp * _interp(torch.as_tensor(lat, device=dev), H, W, sp)
+        total = v if total is None else total + v
         norm += amp
         amp *= 0.5
-        spacing = max(1.0, spacing / 2.0)
     return total / norm
 
 
-def _landcover(field_: np.ndarray) -> np.ndarray:
+def _landcover_batch(field_):
+    """Threshold each grid's field at its own cumulative class quantiles
+    (linear-interpolated order statistics, numpy's default definition)."""
+    import torch
+    n = field_.shape[0]
+    flat = field_.reshape(n, -1)
+    srt, _ = torch.sort(flat, dim=1)
+    m = flat.shape[1]
     fr = np.array([CLASSES[c][2] for c in _FIELD_ORDER])
-    cuts = np.quantile(field_, np.cumsum(fr)[:-1] / fr.sum())
-    idx = np.searchsorted(cuts, field_, side="right")
-    return np.asarray(_FIELD_ORDER, np.uint8)[idx]
+    qs = np.cumsum(fr)[:-1] / fr.sum()
+    idx = torch.zeros(flat.shape, dtype=torch.long, device=flat.device)
+    for q in qs:
+        pos = q * (m - 1)
+        lo = int(math.floor(pos))
+        hi = min(lo + 1, m - 1)
+        cut = srt[:, lo] + (srt[:, hi] - srt[:, lo]) * (pos - lo)
+        idx += (flat >= cut[:, None]).long()
+    order = torch.as_tensor(np.asarray(_FIELD_ORDER, np.uint8), device=flat.device)
+    return order[idx].reshape(field_.shape)
 
 
-def _one_env(seed: int, e: int, H: int, W: int, n_ign=(1, 3)):
+def _draw_env(seed: int, e: int, H: int, W: int, n_ign=(1, 3)):
+    """All random draws of grid e, in a fixed order, from its own stream."""
     rng = np.random.default_rng(seed * 1_000_003 + e)
-    cls = _landcover(fbm(rng, H, W))
-    z = fbm(rng, H, W)
-    z = (z - z.min()) / max(z.max() - z.min(), 1e-12) * 2000.0
+    sps = _octave_spacings(H, W)
+    lat_c = [rng.random(_lattice_shape(H, W, sp)) for sp in sps]
+    lat_z = [rng.random(_lattice_shape(H, W, sp)) for sp in sps]
     V = rng.uniform(0.0, 10.0)
     Th = rng.uniform(0.0, 2.0 * math.pi)
-    burn = burnable_classes(np.array([c[4] for c in CLASSES]))[cls]
-    F = np.where(burn, STATE_CANBURN, STATE_NOFUEL).astype(np.uint8)
-    cand = np.flatnonzero(burn.reshape(-1))
     k = int(rng.integers(n_ign[0], n_ign[1] + 1))
-    if cand.size:
-        pick = rng.choice(cand, size=min(k, cand.size), replace=False)
-        F.reshape(-1)[pick] = STATE_BURNING
-    return cls.reshape(-1), z.astype(np.float32).reshape(-1), np.float32(V), np.float32(Th), F.reshape(-1)
+    pick_u = rng.random(n_ign[1])          # positions among the burnable cells
+    return lat_c, lat_z, V, Th, k, pick_u
+
+
+def _make_group(seed: int, envs, H: int, W: int, chunk: int = 1024):
+    """Grids `envs` (all H x W): cls, dem, V, Th, F0 arrays in env order."""
+    burn_cls = burnable_classes(np.array([c[4] for c in CLASSES]))
+    out = []
+    for c0 in range(0, len(envs), chunk):
+        ids = envs[c0:c0 + chunk]
+        draws = [_draw_env(seed, e, H, W) for e in ids]
+        nO = len(draws[0][0])
+        cls = _landcover_batch(_fbm_batch([np.stack([d[0][o] for d in draws]) for o in range(nO)], H, W))
+        cls = cls.cpu().numpy()
+        z = _fbm_batch([np.stack([d[1][o] for d in draws]) for o in range(nO)], H, W)
+        zmin = z.reshape(len(ids), -1).amin(dim=1)[:, None, None]
+        zmax = z.reshape(len(ids), -1).amax(dim=1)[:, None, None]
+        z = ((z - zmin) / (zmax - zmin).clamp_min(1e-12) * 2000.0).cpu().numpy()
+        burn = burn_cls[cls]
+        F = np.where(burn, STATE_CANBURN, STATE_NOFUEL).astype(np.uint8)
+        for i, d in enumerate(draws):
+            cand = np.flatnonzero(burn[i].reshape(-1))
+            if cand.size:
+                # distinct cells: sample without replacement by successive picks
+                chosen = []
+                pool = cand.copy()
+                for j in range(min(d[4], cand.size)):
+                    t = int(d[5][j] * pool.size)
+                    chosen.append(pool[t])
+                    pool = np.delete(pool, t)
+                F[i].reshape(-1)[chosen] = STATE_BURNING
+        for i, d in enumerate(draws):
+            out.append((cls[i].reshape(-1), z[i].astype(np.float32).reshape(-1), np.float32(d[2]),
+                        np.float32(d[3]), F[i].reshape(-1)))
+    return out
 
 
 def make_scenario(H, W, N: int | None = None, seed: int = 0, params: Params | None = None) -> Scenario:
@@ -169,7 +230,14 @@ def make_scenario(H, W, N: int | None = None, seed: int = 0, params: Params | No
     else:
         Hs = np.asarray(H, np.int32)
         Ws = np.asarray(W, np.int32)
-    parts = [_one_env(seed, e, int(Hs[e]), int(Ws[e])) for e in range(len(Hs))]
+    n = len(Hs)
+    parts = [None] * n
+    shapes = {}
+    for e in range(n):
+        shapes.setdefault((int(Hs[e]), int(Ws[e])), []).append(e)
+    for (h, w), envs in shapes.items():
+        for e, part in zip(envs, _make_group(seed, envs, h, w)):
+            parts[e] = part
     return Scenario(H=Hs, W=Ws,
                     cls=np.concatenate([p[0] for p in parts]),
                     dem=np.concatenate([p[1] for p in parts]),

@@ -1,0 +1,54 @@
+"""The C-ABI library loads and exports every entry point include/jwf.h declares.
+
+No compute call is made here (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "jwf.h")).read()
+    return sorted(set(re.findall(r"^JWF_API\s+[\w\s\*]+?\b(jwf_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libjwf():
+    from paper_2512_06102_gb300 import build
+    build.build()
+    import torch  # noqa: F401  (loads the CUDA runtime libjwf links against)
+    from paper_2512_06102_gb300 import jwf
+    return jwf.lib()
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ["jwf_create", "jwf_destroy", "jwf_precompute_probs", "jwf_step", "jwf_apply_action",
+                 "jwf_reset", "jwf_step_relaxed_fwd", "jwf_step_relaxed_bwd"]:
+        assert name in syms
+
+
+def test_every_declared_symbol_is_exported(libjwf):
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    for name in syms:
+        assert hasattr(libjwf, name), name
+    from paper_2512_06102_gb300 import jwf
+    assert set(jwf.EXPORTS) == set(syms)
+
+
+def test_host_side_errors_without_gpu(libjwf):
+    # argument validation happens before any CUDA call
+    from paper_2512_06102_gb300 import jwf
+    assert libjwf.jwf_status_string(0) == b"ok"
+    assert libjwf.jwf_status_string(1) == b"invalid argument"
+    h = ctypes.c_void_p()
+    assert libjwf.jwf_create(None, ctypes.byref(h)) == 1
+    cfg = jwf._Config(0, None, None, 11, 0, 0, 1, 0)
+    assert libjwf.jwf_create(ctypes.byref(cfg), ctypes.byref(h)) == 1
+    assert h.value is None
+    assert libjwf.jwf_destroy(None) == 0
+    assert libjwf.jwf_step(None, 1, None, None, None, None, None) == 1

@@ -1,0 +1,241 @@
+"""Relaxed (raw-probabilities) step on the GPU against the FP64 oracle.
+
+  * forward: one step within 1e-6 absolute; T = 100 steps within 1e-5 absolute
+    (FP32 state against FP64);
+  * one adjoint step: every input adjoint and dL/dp_continue within 1e-4
+    relative of the oracle's autograd;
+  * rollout gradients with respect to every parameter (T = 40) and to the
+    initial maps (T = 12) within 1e-4 relative of the oracle's autograd (which
+    the CPU suite pins to central differences), with tanker masks, on several
+    tiles and a ragged tail;
+  * checkpointed and non-checkpointed gradients are bit-identical;
+  * T = 1000 on the 256 x 128^2 differentiation workload with sqrt(T)
+    checkpoints: the parameter gradient of a loss on a sample of envs equals
+    the oracle's for those envs, and every gradient entry is finite or an
+    overflow of a reference value beyond the float range.
+Parameter components are compared as |g - g_ref| <= 1e-4 |g_ref| + 1e-7 max|g_ref|
+(the floor covers components that cancel to near zero); map entries as
+|g - g_ref| <= 1e-4 |g_ref| + 1e-20.  The map gradient is tested at a short
+horizon on purpose: a spark ahead of the front grows about sum_d r per step,
+so d p_T / d p_burn_0 leaves the float range after ~20 steps and, by T ~ 100,
+its conditioning exceeds 1/eps_float with respect to the forward states
+themselves (an FP64 adjoint over float states misses the FP64 reference by
+orders of magnitude there), while the parameter gradient stays well
+conditioned.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import prob
+from oracle import relaxed as orelaxed
+from paper_2512_06102_gb300 import relaxed, scenarios
+from tests.gpu_util import make_sim, oracle_tables, require_gpu, to
+
+pytestmark = pytest.mark.gpu
+f64 = torch.float64
+
+
+def _planes(scn, rng, soft=True):
+    F0 = scn.F0
+    fuel = (F0 != 0).astype(np.float64)
+    if soft:
+        pb = np.where(F0 == 2, 1.0, 0.0) + fuel * (rng.random(F0.size) < 0.02) * rng.random(F0.size) * 0.5
+        pb = np.minimum(pb, 1.0) * fuel
+        pu = fuel * (1 - pb) * (0.7 + 0.3 * rng.random(F0.size)) + (1 - fuel)
+    else:
+        pb = (F0 == 2).astype(np.float64)
+        pu = 1.0 - pb
+    return pu, pb
+
+
+def _oracle_rates(scn):
+    return torch.as_tensor(oracle_tables(scn)[3]).reshape(scn.N, int(scn.H[0]), int(scn.W[0]), 8)
+
+
+def test_forward_one_step_and_T100():
+    require_gpu()
+    scn = scenarios.make_scenario(128, 128, N=6, seed=1)
+    rng = np.random.default_rng(0)
+    pu, pb = _planes(scn, rng)
+    sim = make_sim(scn, keep_rates=True)
+    sim.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    r64 = _oracle_rates(scn)
+    shp = (scn.N, 128, 128)
+    m = (rng.random(scn.F0.size) < 0.01).astype(np.float32) * 0.8
+    gu, gb = sim.relaxed_fwd(to(pu.astype(np.float32)), to(pb.astype(np.float32)), to(m))
+    ou, ob = orelaxed.relaxed_step(torch.as_tensor(pu.astype(np.float32).astype(np.float64)).reshape(shp),
+                                   torch.as_tensor(pb.astype(np.float32).astype(np.float64)).reshape(shp),
+                                   r64, float(np.float32(scn.params.p_continue)),
+                                   torch.as_tensor(m.astype(np.float64)).reshape(shp))
+    assert np.abs(gu.cpu().numpy() - ou.reshape(-1).numpy()).max() < 1e-6
+    assert np.abs(gb.cpu().numpy() - ob.reshape(-1).numpy()).max() < 1e-6
+    # 100 steps
+    pu_g, pb_g = to(pu.astype(np.float32)), to(pb.astype(np.float32))
+    for _ in range(100):
+        pu_g, pb_g = sim.relaxed_fwd(pu_g, pb_g)
+    ou, ob = orelaxed.relaxed_rollout(torch.as_tensor(pu.astype(np.float32).astype(np.float64)).reshape(shp),
+                                      torch.as_tensor(pb.astype(np.float32).astype(np.float64)).reshape(shp),
+                                      r64, float(np.float32(scn.params.p_continue)), 100)
+    err_u = np.abs(pu_g.cpu().numpy() - ou.reshape(-1).numpy()).max()
+    err_b = np.abs(pb_g.cpu().numpy() - ob.reshape(-1).numpy()).max()
+    assert err_u < 1e-5 and err_b < 1e-5, (err_u, err_b)
+    pbd = 1 - pu_g - pb_g
+    assert pbd.min().item() > -1e-5
+
+
+def _close(g, ref, rel=1e-4, floor=1e-7, atol=0.0):
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    tol = rel * np.abs(ref) + floor * np.abs(ref).max() + atol
+    bad = np.abs(g - ref) > tol
+    assert not bad.any(), f"{bad.sum()} off; worst {np.max(np.abs(g - ref) / np.maximum(np.abs(ref), 1e-300))}"
+
+
+def test_one_adjoint_step():
+    require_gpu()
+    scn = scenarios.make_scenario(96, 80, N=3, seed=2)
+    rng = np.random.default_rng(1)
+    pu, pb = _planes(scn, rng)
+    pu32, pb32 = pu.astype(np.float32), pb.astype(np.float32)
+    au = rng.standard_normal(pu.size).astype(np.float32)
+    ab = rng.standard_normal(pu.size).astype(np.float32)
+    m = (rng.random(pu.size) < 0.05).astype(np.float32) * rng.random(pu.size).astype(np.float32)
+    sim = make_sim(scn, keep_rates=True)
+    sim.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    gpc = torch.zeros(1, dtype=f64, device="cuda")
+    glam = torch.empty(pu.size, device="cuda")
+    gu, gb = sim.relaxed_bwd(to(pu32), to(pb32), to(au), to(ab), mask=to(m), glam=glam, gpc=gpc)
+    # oracle: autograd of one FP64 step
+    shp = (scn.N, 96, 80)
+    U = torch.as_tensor(pu32.astype(np.float64)).reshape(shp).requires_grad_(True)
+    B = torch.as_tensor(pb32.astype(np.float64)).reshape(shp).requires_grad_(True)
+    pc = torch.tensor(float(np.float32(scn.params.p_continue)), dtype=f64, requires_grad=True)
+    r64 = _oracle_rates(scn).requires_grad_(True)
+    ou, ob = orelaxed.relaxed_step(U, B, r64, pc, torch.as_tensor(m.astype(np.float64)).reshape(shp))
+    L = (torch.as_tensor(au.astype(np.float64)).reshape(shp) * ou).sum() + \
+        (torch.as_tensor(ab.astype(np.float64)).reshape(shp) * ob).sum()
+    rU, rB, rpc = torch.autograd.grad(L, [U, B, pc])
+    torch.cuda.synchronize()
+    _close(gu.cpu().numpy(), rU.reshape(-1).numpy())
+    _close(gb.cpu().numpy(), rB.reshape(-1).numpy())
+    assert gpc.item() == pytest.approx(rpc.item(), rel=1e-5)
+
+
+def _theta(params, C):
+    return torch.tensor([params.p_base, params.alpha_w1, params.alpha_w2, params.alpha_s, params.alpha_gamma,
+                         params.p_continue] + list(params.mu_veg[:C]) + list(params.mu_den[:C]), dtype=f64)
+
+
+def _oracle_grad(scn, theta, pu, pb, T, wu, wb, masks=None, envs=None):
+    """Gradient of sum(wu * p_un_T + wb * p_burn_T) by the FP64 oracle."""
+    C = len(scn.params.mu_veg)
+    idx = range(scn.N) if envs is None else envs
+    th = theta.clone().requires_grad_(True)
+    U = torch.as_tensor(np.stack([scn.env(e, pu) for e in idx])).requires_grad_(True)
+    B = torch.as_tensor(np.stack([scn.env(e, pb) for e in idx])).requires_grad_(True)
+    cls = torch.as_tensor(np.stack([scn.env(e, scn.cls) for e in idx])).long()
+    dem = torch.as_tensor(np.stack([scn.env(e, scn.dem) for e in idx]).astype(np.float64))
+    sel = list(idx)
+    r = prob.rates(cls, dem, torch.as_tensor(scn.wind_speed[sel].astype(np.float64)),
+                   torch.as_tensor(scn.wind_dir[sel].astype(np.float64)), th[0], th[1], th[2], th[3], th[4],
+                   th[6:6 + C], th[6 + C:6 + 2 * C], scn.params.cell_size)
+    mk = None if masks is None else [torch.as_tensor(np.stack([scn.env(e, masks[t]) for e in idx]).astype(np.float64))
+                                     for t in range(T)]
+    ou, ob = orelaxed.relaxed_rollout(U, B, r, th[5], T, mk)
+    WU = torch.as_tensor(np.stack([scn.env(e, wu) for e in idx]).astype(np.float64))
+    WB = torch.as_tensor(np.stack([scn.env(e, wb) for e in idx]).astype(np.float64))
+    L = (WU * ou).sum() + (WB * ob).sum()
+    return torch.autograd.grad(L, [th, U, B])
+
+
+@pytest.mark.parametrize("T,check_maps", [(40, False), (12, True)])
+def test_rollout_gradient_matches_oracle(T, check_maps):
+    require_gpu()
+    H, W, N = 70, 66, 3                 # several 256-cell tiles and a ragged tail
+    scn = scenarios.make_scenario(H, W, N=N, seed=3)
+    rng = np.random.default_rng(3)
+    pu, pb = _planes(scn, rng)
+    pu = pu.astype(np.float32).astype(np.float64)
+    pb = pb.astype(np.float32).astype(np.float64)
+    wu = rng.standard_normal(pu.size).astype(np.float32)
+    wb = rng.standard_normal(pu.size).astype(np.float32)
+    masks = (rng.random((T, pu.size)) < 0.01).astype(np.float32) * 0.9
+    C = scenarios.N_CLASSES
+    theta = _theta(scn.params, C)
+    theta32 = theta.float().double()       # the GPU sees float32 parameters
+    sim = make_sim(scn, keep_rates=True)
+    scene = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    th = theta32.clone().requires_grad_(True)
+    U = to(pu.astype(np.float32)).requires_grad_(True)
+    B = to(pb.astype(np.float32)).requires_grad_(True)
+    ou, ob = relaxed.rollout(th, U, B, sim, scene, T, masks=to(masks), ckpt_every=16)
+    L = (to(wu) * ou).sum() + (to(wb) * ob).sum()
+    gth, gU, gB = torch.autograd.grad(L, [th, U, B])
+    rth, rU, rB = _oracle_grad(scn, theta32, pu, pb, T, wu, wb, masks=masks)
+    _close(gth.cpu().numpy(), rth.numpy())
+    if check_maps:
+        _close(gU.cpu().numpy(), rU.reshape(-1).numpy(), floor=0.0, atol=1e-20)
+        _close(gB.cpu().numpy(), rB.reshape(-1).numpy(), floor=0.0, atol=1e-20)
+
+
+def test_checkpointing_is_bit_identical():
+    require_gpu()
+    scn = scenarios.make_scenario(64, 64, N=4, seed=4)
+    rng = np.random.default_rng(4)
+    pu, pb = _planes(scn, rng)
+    T = 67
+    wu = to(rng.standard_normal(pu.size).astype(np.float32))
+    sim = make_sim(scn, keep_rates=True)
+    scene = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    grads = []
+    for ck in (8, 16, 24, T):
+        th = _theta(scn.params, scenarios.N_CLASSES).float().double().requires_grad_(True)
+        U = to(pu.astype(np.float32)).requires_grad_(True)
+        B = to(pb.astype(np.float32)).requires_grad_(True)
+        ou, ob = relaxed.rollout(th, U, B, sim, scene, T, ckpt_every=ck)
+        L = (wu * ou).sum() + ob.sum()
+        grads.append(torch.autograd.grad(L, [th, U, B]))
+    for g in grads[1:]:
+        for a, b in zip(grads[0], g):
+            assert torch.equal(a, b)
+
+
+def test_full_size_T1000_sampled():
+    """256 x 128^2, T = 1000, sqrt(T) checkpoints; loss on 2 sampled envs."""
+    require_gpu()
+    N, H, W, T = 256, 128, 128, 1000
+    scn = scenarios.make_scenario(H, W, N=N, seed=0)
+    rng = np.random.default_rng(5)
+    pu, pb = _planes(scn, rng, soft=False)
+    sample = [17, 200]
+    wu = np.zeros(pu.size, np.float32)
+    wb = np.zeros(pu.size, np.float32)
+    for e in sample:
+        o0, o1 = scn.offsets[e], scn.offsets[e + 1]
+        wu[o0:o1] = rng.standard_normal(o1 - o0)
+        wb[o0:o1] = rng.standard_normal(o1 - o0)
+    theta = _theta(scn.params, scenarios.N_CLASSES).float().double()
+    sim = make_sim(scn, keep_rates=True)
+    scene = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    th = theta.clone().requires_grad_(True)
+    U = to(pu.astype(np.float32)).requires_grad_(True)
+    B = to(pb.astype(np.float32)).requires_grad_(True)
+    ou, ob = relaxed.rollout(th, U, B, sim, scene, T)
+    L = (to(wu) * ou).sum() + (to(wb) * ob).sum()
+    gth, gU, gB = torch.autograd.grad(L, [th, U, B])
+    rth, rU, rB = _oracle_grad(scn, theta, pu, pb, T, wu, wb, envs=sample)
+    _close(gth.cpu().numpy(), rth.numpy())
+    F32_MAX = float(np.finfo(np.float32).max)
+    for i, e in enumerate(sample):
+        o0, o1 = scn.offsets[e], scn.offsets[e + 1]
+        for g, ref in ((gU[o0:o1], rU[i]), (gB[o0:o1], rB[i])):
+            g = g.cpu().numpy().astype(np.float64)
+            ref = ref.reshape(-1).numpy()
+            assert not np.isnan(g).any()
+            assert np.isfinite(g[np.abs(ref) < 1e-3 * F32_MAX]).all()
+    # envs outside the loss get zero adjoint
+    other = np.ones(pu.size, bool)
+    for e in sample:
+        other[scn.offsets[e]:scn.offsets[e + 1]] = False
+    assert float(gB[to(other)].abs().max()) == 0.0
