@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "jwf_internal.cuh"
+#include "rate_model.cuh"
 
 namespace {
 
@@ -54,74 +55,6 @@ __device__ __forceinline__ RateTerms rate_terms(const JwfDevParams& P, float z_s
     return t;
 }
 
-// ---------------------------------------------------------------------------
-// Double-float helpers (a value is hi + lo with |lo| <= ulp(hi)/2).  Error-free
-// transforms use the _rn intrinsics so the compiler cannot contract them.
-// ---------------------------------------------------------------------------
-struct df {
-    float hi, lo;
-};
-
-__device__ __forceinline__ df two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-__device__ __forceinline__ df quick_two_sum(float a, float b) {   // |a| >= |b|
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ df df_add(df a, df b) {
-    const df s = two_sum(a.hi, b.hi);
-    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df df_mul(df a, df b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    const float e = fmaf(a.hi, b.hi, -p);
-    return quick_two_sum(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
-}
-__device__ __forceinline__ df df_div(df a, df b) {
-    const float q1 = __fdiv_rn(a.hi, b.hi);
-    const df r = df_add(a, df_neg(df_mul({q1, 0.f}, b)));
-    return quick_two_sum(q1, __fdiv_rn(r.hi, b.hi));
-}
-
-// Constants prepared on the host in double precision.
-struct ProbConsts {
-    df atan_th[65];      // theta_k = k pi/256, k = 0..64
-    df atan_tan[65];     // tan(theta_k)
-    df half_pi;
-    df slope_coef;       // alpha_s * 180 / pi: exponent per radian of slope
-    df run[8];           // cell_size * |Delta_d|
-    float G[16][16];     // gamma(c_v) * p_base (1 + mu_veg(c_u)) (1 + mu_den(c_u)), [c_v][c_u]
-};
-
-// atan of a double-float to ~1e-9 absolute: reduce to b = |x| <= 1 (via
-// atan(x) = pi/2 - atan(1/x)), pick theta_k near atan(b), and use
-// atan(b) = theta_k + atan(u), u = (b - tan theta_k) / (1 + b tan theta_k),
-// |u| < 0.012, with atan(u) = u - u^3/3 + u^5/5.
-__device__ __forceinline__ df atan_df(df x, const ProbConsts& K) {
-    const bool neg = x.hi < 0.f;
-    df a = neg ? df_neg(x) : x;
-    const bool inv = a.hi > 1.0f;
-    const df b = inv ? df_div({1.0f, 0.0f}, a) : a;
-    // cheap estimate of atan(b) on [0, 1] (error < 5e-3 rad) to pick the node
-    const float est = b.hi / fmaf(0.28f, b.hi * b.hi, 1.0f);
-    int k = __float2int_rn(est * 81.48733086305042f);       // 256 / pi
-    k = min(max(k, 0), 64);
-    const df t = K.atan_tan[k];
-    const df num = df_add(b, df_neg(t));
-    const df den = df_add({1.0f, 0.0f}, df_mul(b, t));
-    const float u = __fdiv_rn(num.hi + num.lo, den.hi);
-    const float u2 = u * u;
-    const float at_u = u + u * u2 * fmaf(u2, 0.2f, -0.33333334f);
-    df th = df_add(K.atan_th[k], {at_u, 0.0f});
-    if (inv) th = df_add(K.half_pi, df_neg(th));
-    return neg ? df_neg(th) : th;
-}
-
 __global__ void k_wind_exponent(int32_t N, const float* __restrict__ ws, const float* __restrict__ wd,
                                 double alpha_w1, double alpha_w2, float2* __restrict__ wexp) {
     // alpha_w1 V + alpha_w2 V (cos(d pi/4 - Theta) - 1) per env and direction, in
@@ -136,65 +69,65 @@ __global__ void k_wind_exponent(int32_t N, const float* __restrict__ ws, const f
     wexp[i] = make_float2(hi, (float)(w - (double)hi));
 }
 
+// wind exponent of one source cell with its own wind (per-cell mode), in double
+__device__ __forceinline__ df wind_exponent_cell(float V, float Th, int d, double a1, double a2) {
+    const double s = sin(0.5 * (d * 0.78539816339744830962 - (double)Th));
+    const double w = a1 * (double)V + a2 * (double)V * (-2.0 * s * s);
+    const float hi = (float)w;
+    return {hi, (float)(w - (double)hi)};
+}
+
 __global__ void __launch_bounds__(JWF_TILE)
-k_prob_table(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
+k_prob_table(const int2* __restrict__ tiles, int64_t n_tiles, const int32_t* __restrict__ Hs,
              const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs,
              const uint8_t* __restrict__ cls, const float* __restrict__ dem,
              const float* __restrict__ ws, const float* __restrict__ wd,
              const float2* __restrict__ wexp, int per_cell_wind, const JwfDevParams P,
-             const ProbConsts K, float* __restrict__ q, float* __restrict__ r) {
-    __shared__ ProbConsts sK;
-    for (int i = threadIdx.x; i < (int)(sizeof(ProbConsts) / 4); i += blockDim.x)
+             const RateConsts K, float* __restrict__ q, float* __restrict__ r) {
+    __shared__ RateConsts sK;
+    for (int i = threadIdx.x; i < (int)(sizeof(RateConsts) / 4); i += blockDim.x)
         reinterpret_cast<float*>(&sK)[i] = reinterpret_cast<const float*>(&K)[i];
     __syncthreads();
-    const int2 tile = tiles[blockIdx.x];
-    const int e = tile.x;
-    const int W = Ws[e], H = Hs[e];
-    const int local = tile.y + (int)threadIdx.x;
-    if (local >= H * W) return;
-    const int64_t off = offs[e];
-    const int y = local / W, x = local - (local / W) * W;
-    const int64_t v = off + local;
-
-    const int cv = cls[v];
-    const float zv = dem[v];
-    float rr[8], qq[8];
+    const double a1 = (double)P.alpha_w1, a2 = (double)P.alpha_w2;
+    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        const int2 tile = tiles[ti];
+        const int e = tile.x;
+        const int W = Ws[e], H = Hs[e];
+        const int local = tile.y + (int)threadIdx.x;
+        if (local >= H * W) continue;
+        const int64_t off = offs[e];
+        const int y = local / W, x = local - (local / W) * W;
+        const int64_t v = off + local;
+        const int cv = cls[v];
+        const float zv = dem[v];
+        float rr[8], qq[8];
 #pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        const int uy = y - jwf_dr(d), ux = x - jwf_dx(d);
-        rr[d] = 0.f;
-        qq[d] = 0.f;
-        if (uy < 0 || uy >= H || ux < 0 || ux >= W) continue;
-        const int64_t u = off + (int64_t)uy * W + ux;
-        const int cu = cls[u];
-        const float G = sK.G[cv][cu];
-        if (G == 0.f) continue;                      // no fuel at the source or the target
-        // wind part of the exponent at the source (Eq. 1)
-        df wexp_d;
-        if (per_cell_wind) {
-            const float V = ws[u];
-            const float sn = sinf(0.5f * (d * 0.78539816f - wd[u]));
-            wexp_d = {V * fmaf(-2.0f * P.alpha_w2, sn * sn, P.alpha_w1), 0.0f};
-        } else {
-            const float2 w2 = wexp[e * 8 + d];
-            wexp_d = {w2.x, w2.y};
+        for (int d = 0; d < 8; ++d) {
+            const int uy = y - jwf_dr(d), ux = x - jwf_dx(d);
+            rr[d] = 0.f;
+            qq[d] = 0.f;
+            if (uy < 0 || uy >= H || ux < 0 || ux >= W) continue;
+            const int64_t u = off + (int64_t)uy * W + ux;
+            const float G = sK.G[cv][cls[u]];
+            if (G == 0.f) continue;                      // no fuel at the source or the target
+            df wx;
+            if (per_cell_wind) {
+                wx = wind_exponent_cell(ws[u], wd[u], d, a1, a2);
+            } else {
+                const float2 w2 = wexp[e * 8 + d];
+                wx = {w2.x, w2.y};
+            }
+            rr[d] = rate_of(G, zv, dem[u], wx, d, sK);
+            qq[d] = prob_of(rr[d]);
         }
-        // slope part (Eq. 2): alpha_s * degrees(atan(dz / run)), in double-float
-        const df dz = two_sum(zv, -dem[u]);
-        const df slope = atan_df(df_div(dz, sK.run[d]), sK);
-        const df E = df_add(wexp_d, df_mul(sK.slope_coef, slope));
-        const float kh = expf(E.hi);
-        const float kappa = fmaf(kh, E.lo, kh);       // exp(E.hi + E.lo)
-        rr[d] = G * kappa;                            // gamma(v) phi(u, d)  (Eqs. 3-4)
-        qq[d] = -expm1f(-rr[d]);                      // 1 - exp(-rate)
-    }
-    float4* q4 = reinterpret_cast<float4*>(q + v * 8);
-    q4[0] = make_float4(qq[0], qq[1], qq[2], qq[3]);
-    q4[1] = make_float4(qq[4], qq[5], qq[6], qq[7]);
-    if (r != nullptr) {
-        float4* r4 = reinterpret_cast<float4*>(r + v * 8);
-        r4[0] = make_float4(rr[0], rr[1], rr[2], rr[3]);
-        r4[1] = make_float4(rr[4], rr[5], rr[6], rr[7]);
+        float4* q4 = reinterpret_cast<float4*>(q + v * 8);
+        q4[0] = make_float4(qq[0], qq[1], qq[2], qq[3]);
+        q4[1] = make_float4(qq[4], qq[5], qq[6], qq[7]);
+        if (r != nullptr) {
+            float4* r4 = reinterpret_cast<float4*>(r + v * 8);
+            r4[0] = make_float4(rr[0], rr[1], rr[2], rr[3]);
+            r4[1] = make_float4(rr[4], rr[5], rr[6], rr[7]);
+        }
     }
 }
 
@@ -385,39 +318,52 @@ static df split_df(double v) {
     return {hi, (float)(v - (double)hi)};
 }
 
-cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
-                                  const float* ws, const float* wd, cudaStream_t s) {
+void jwf_rate_consts(const jwf_ctx* c, RateConsts* K) {
     const double pi = 3.14159265358979323846;
-    ProbConsts K{};
+    *K = RateConsts{};
     for (int k = 0; k <= 64; ++k) {
         const double th = k * pi / 256.0;
-        K.atan_th[k] = split_df(th);
-        K.atan_tan[k] = split_df(std::tan(th));
+        K->atan_th[k] = split_df(th);
+        K->atan_tan[k] = split_df(std::tan(th));
     }
-    K.half_pi = split_df(pi / 2.0);
-    K.slope_coef = split_df((double)c->P.alpha_s * 180.0 / pi);
+    K->half_pi = split_df(pi / 2.0);
+    K->slope_coef = split_df((double)c->P.alpha_s * 180.0 / pi);
     for (int d = 0; d < 8; ++d)
-        K.run[d] = split_df((double)c->P.cell_size * ((d & 1) ? std::sqrt(2.0) : 1.0));
+        K->inv_run[d] = split_df(1.0 / ((double)c->P.cell_size * ((d & 1) ? std::sqrt(2.0) : 1.0)));
     for (int a = 0; a < 16; ++a)
         for (int b = 0; b < 16; ++b) {
             if (a >= c->n_classes || b >= c->n_classes) {
-                K.G[a][b] = 0.f;
+                K->G[a][b] = 0.f;
                 continue;
             }
             const double gamma = (double)c->P.alpha_gamma * (1.0 + (double)c->P.mu_veg[a]) *
                                  (1.0 + (double)c->P.mu_den[a]);
             const double base = (double)c->P.p_base * (1.0 + (double)c->P.mu_veg[b]) *
                                 (1.0 + (double)c->P.mu_den[b]);
-            K.G[a][b] = (float)(gamma * base);
+            K->G[a][b] = (float)(gamma * base);
         }
+}
+
+cudaError_t jwf_launch_wind_exponent(const jwf_ctx* c, const float* ws, const float* wd, cudaStream_t s) {
+    k_wind_exponent<<<(c->N * 8 + 255) / 256, 256, 0, s>>>(c->N, ws, wd, (double)c->P.alpha_w1,
+                                                             (double)c->P.alpha_w2, c->d_wexp);
+    return cudaGetLastError();
+}
+
+cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
+                                  const float* ws, const float* wd, cudaStream_t s) {
+    RateConsts K;
+    jwf_rate_consts(c, &K);
     const bool per_cell = (c->flags & JWF_WIND_PER_CELL) != 0u;
     if (!per_cell) {
-        k_wind_exponent<<<(c->N * 8 + 255) / 256, 256, 0, s>>>(c->N, ws, wd, (double)c->P.alpha_w1,
-                                                                 (double)c->P.alpha_w2, c->d_wexp);
+        const cudaError_t err = jwf_launch_wind_exponent(c, ws, wd, s);
+        if (err != cudaSuccess) return err;
     }
-    k_prob_table<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(
-        c->d_tiles, c->d_H, c->d_W, c->d_off, cls, dem, ws, wd, c->d_wexp, per_cell ? 1 : 0, c->P, K,
-        c->d_q, (c->flags & JWF_KEEP_RATES) ? c->d_r : nullptr);
+    int64_t grid = (int64_t)c->num_sms * 8;
+    if (grid > c->n_tiles) grid = c->n_tiles;
+    k_prob_table<<<(unsigned)grid, JWF_TILE, 0, s>>>(
+        c->d_tiles, c->n_tiles, c->d_H, c->d_W, c->d_off, cls, dem, ws, wd, c->d_wexp, per_cell ? 1 : 0,
+        c->P, K, c->d_q, (c->flags & JWF_KEEP_RATES) ? c->d_r : nullptr);
     return cudaGetLastError();
 }
 

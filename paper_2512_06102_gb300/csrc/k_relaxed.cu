@@ -17,12 +17,19 @@
 //
 // The adjoint of a cell that the fire has not reached grows by about
 // sum_d r per step (a spark there would spread), so it can leave the float
-// range over long horizons.  A factor that is exactly zero (a burned-out
-// cell's p_un, a no-fuel rate, a full mask) keeps its product zero even when
-// the other factor overflowed, so overflow never turns into NaN.
+// range over long horizons.  Every stored adjoint is therefore saturated at
+// +-JWF_ADJ_SAT (1e35): with rates below ~3e36 / 9 no sum of nine terms can
+// overflow, so the adjoint never becomes inf or NaN.  Only entries whose
+// exact value exceeds 1e35 are affected (they lie ahead of the fire, where
+// p_burn is zero, so the parameter gradients do not see them); a factor that
+// is exactly zero keeps its product zero.
 #include "jwf_internal.cuh"
 
 namespace {
+
+constexpr float JWF_ADJ_SAT = 1e35f;
+
+__device__ __forceinline__ float sat(float x) { return fminf(fmaxf(x, -JWF_ADJ_SAT), JWF_ADJ_SAT); }
 
 __device__ __forceinline__ float pb_at(const float* __restrict__ pburn, const float* __restrict__ mask,
                                        int64_t i) {
@@ -97,8 +104,8 @@ k_relaxed_bwd_a(const int2* __restrict__ tiles, int64_t n_tiles, const int32_t* 
         const float au = gun_out[v], ab = gburn_out[v];
         const float nb = ab - au;
         const float pe = pun[v] * em;
-        gun[v] = p_ign != 0.f ? au + nb * p_ign : au;
-        glam[v] = pe != 0.f ? nb * pe : 0.f;
+        gun[v] = sat(p_ign != 0.f ? au + nb * p_ign : au);
+        glam[v] = pe != 0.f ? sat(nb * pe) : 0.f;
         const float pbv = pb_at(pburn, mask, v);
         if (pbv != 0.f) acc += (double)(ab * pbv);
     }
@@ -161,7 +168,7 @@ k_relaxed_bwd_b(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
         const float keep = 1.0f - mask[u];
         g = keep != 0.f ? g * keep : 0.f;
     }
-    gburn[u] = g;
+    gburn[u] = sat(g);
 }
 
 }  // namespace

@@ -11,11 +11,14 @@
   * checkpointed and non-checkpointed gradients are bit-identical;
   * T = 1000 on the 256 x 128^2 differentiation workload with sqrt(T)
     checkpoints: the parameter gradient of a loss on a sample of envs equals
-    the oracle's for those envs, and every gradient entry is finite or an
-    overflow of a reference value beyond the float range.
+    the oracle's for those envs, and every map entry is finite (the adjoint
+    saturates at 1e35 instead of overflowing).
 Parameter components are compared as |g - g_ref| <= 1e-4 |g_ref| + 1e-7 max|g_ref|
-(the floor covers components that cancel to near zero); map entries as
-|g - g_ref| <= 1e-4 |g_ref| + 1e-20.  The map gradient is tested at a short
+(the floor covers components that cancel to near zero).  Map entries are
+compared as |g - g_ref| <= 1e-4 |g_ref| + 10 |g_ref32 - g_ref|, where g_ref32
+is the same oracle evaluated in float32: a few entries cancel to values far
+below their terms, and float32 arithmetic cannot resolve them any better
+(the float32 oracle misses them too).  The map gradient is tested at a short
 horizon on purpose: a spark ahead of the front grows about sum_d r per step,
 so d p_T / d p_burn_0 leaves the float range after ~20 steps and, by T ~ 100,
 its conditioning exceeds 1/eps_float with respect to the forward states
@@ -127,26 +130,28 @@ def _theta(params, C):
                          params.p_continue] + list(params.mu_veg[:C]) + list(params.mu_den[:C]), dtype=f64)
 
 
-def _oracle_grad(scn, theta, pu, pb, T, wu, wb, masks=None, envs=None):
-    """Gradient of sum(wu * p_un_T + wb * p_burn_T) by the FP64 oracle."""
+def _oracle_grad(scn, theta, pu, pb, T, wu, wb, masks=None, envs=None, dtype=f64):
+    """Gradient of sum(wu * p_un_T + wb * p_burn_T) by the oracle (FP64 by
+    default; float32 only to gauge each entry's float32 conditioning).  The
+    rates are always built in FP64."""
     C = len(scn.params.mu_veg)
     idx = range(scn.N) if envs is None else envs
     th = theta.clone().requires_grad_(True)
-    U = torch.as_tensor(np.stack([scn.env(e, pu) for e in idx])).requires_grad_(True)
-    B = torch.as_tensor(np.stack([scn.env(e, pb) for e in idx])).requires_grad_(True)
+    U = torch.as_tensor(np.stack([scn.env(e, pu) for e in idx])).to(dtype).requires_grad_(True)
+    B = torch.as_tensor(np.stack([scn.env(e, pb) for e in idx])).to(dtype).requires_grad_(True)
     cls = torch.as_tensor(np.stack([scn.env(e, scn.cls) for e in idx])).long()
     dem = torch.as_tensor(np.stack([scn.env(e, scn.dem) for e in idx]).astype(np.float64))
     sel = list(idx)
     r = prob.rates(cls, dem, torch.as_tensor(scn.wind_speed[sel].astype(np.float64)),
                    torch.as_tensor(scn.wind_dir[sel].astype(np.float64)), th[0], th[1], th[2], th[3], th[4],
-                   th[6:6 + C], th[6 + C:6 + 2 * C], scn.params.cell_size)
-    mk = None if masks is None else [torch.as_tensor(np.stack([scn.env(e, masks[t]) for e in idx]).astype(np.float64))
+                   th[6:6 + C], th[6 + C:6 + 2 * C], scn.params.cell_size).to(dtype)
+    mk = None if masks is None else [torch.as_tensor(np.stack([scn.env(e, masks[t]) for e in idx])).to(dtype)
                                      for t in range(T)]
-    ou, ob = orelaxed.relaxed_rollout(U, B, r, th[5], T, mk)
-    WU = torch.as_tensor(np.stack([scn.env(e, wu) for e in idx]).astype(np.float64))
-    WB = torch.as_tensor(np.stack([scn.env(e, wb) for e in idx]).astype(np.float64))
+    ou, ob = orelaxed.relaxed_rollout(U, B, r, th[5].to(dtype), T, mk)
+    WU = torch.as_tensor(np.stack([scn.env(e, wu) for e in idx])).to(dtype)
+    WB = torch.as_tensor(np.stack([scn.env(e, wb) for e in idx])).to(dtype)
     L = (WU * ou).sum() + (WB * ob).sum()
-    return torch.autograd.grad(L, [th, U, B])
+    return [g.double() for g in torch.autograd.grad(L, [th, U, B])]
 
 
 @pytest.mark.parametrize("T,check_maps", [(40, False), (12, True)])
@@ -175,8 +180,11 @@ def test_rollout_gradient_matches_oracle(T, check_maps):
     rth, rU, rB = _oracle_grad(scn, theta32, pu, pb, T, wu, wb, masks=masks)
     _close(gth.cpu().numpy(), rth.numpy())
     if check_maps:
-        _close(gU.cpu().numpy(), rU.reshape(-1).numpy(), floor=0.0, atol=1e-20)
-        _close(gB.cpu().numpy(), rB.reshape(-1).numpy(), floor=0.0, atol=1e-20)
+        _, sU, sB = _oracle_grad(scn, theta32, pu, pb, T, wu, wb, masks=masks, dtype=torch.float32)
+        for g, ref, ref32 in ((gU, rU, sU), (gB, rB, sB)):
+            ref = ref.reshape(-1).numpy()
+            noise = np.abs(ref32.reshape(-1).numpy() - ref)
+            _close(g.cpu().numpy(), ref, floor=0.0, atol=10.0 * noise + 1e-20)
 
 
 def test_checkpointing_is_bit_identical():
@@ -226,14 +234,13 @@ def test_full_size_T1000_sampled():
     gth, gU, gB = torch.autograd.grad(L, [th, U, B])
     rth, rU, rB = _oracle_grad(scn, theta, pu, pb, T, wu, wb, envs=sample)
     _close(gth.cpu().numpy(), rth.numpy())
-    F32_MAX = float(np.finfo(np.float32).max)
     for i, e in enumerate(sample):
         o0, o1 = scn.offsets[e], scn.offsets[e + 1]
         for g, ref in ((gU[o0:o1], rU[i]), (gB[o0:o1], rB[i])):
             g = g.cpu().numpy().astype(np.float64)
             ref = ref.reshape(-1).numpy()
-            assert not np.isnan(g).any()
-            assert np.isfinite(g[np.abs(ref) < 1e-3 * F32_MAX]).all()
+            assert np.isfinite(g).all()                  # saturated, never inf or NaN
+            assert np.abs(g).max() <= float(np.float32(1e35))
     # envs outside the loss get zero adjoint
     other = np.ones(pu.size, bool)
     for e in sample:
