@@ -247,6 +247,44 @@ JWF_API jwf_status jwf_rates_bwd(jwf_ctx* ctx, int32_t n_steps, const float* d_g
                          const float* d_dem, const float* d_wind_speed,
                          const float* d_wind_dir, double* d_gparams, void* stream);
 
+/* ---- no-allocation variant ------------------------------------------------ */
+
+/* Largest batch, in cells (n_envs * H * W), that
+ * jwf_step_relaxed_bwd_noalloc accepts. */
+#define JWF_NOALLOC_MAX_CELLS (1 << 22)
+
+/* The adjoint step of jwf_step_relaxed_bwd for a uniform batch of n_envs
+ * grids of H x W cells, without a context and without allocating device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc -- code running inside another framework's
+ * custom operator, which hands over its buffers and forbids allocation while
+ * the operator runs, and real-time loops that must not allocate once they
+ * have started.
+ *
+ * Buffers are the caller's, laid out as on the context path: d_r float
+ * [cells][8] rate table (e.g. the one jwf_get_probs returns); d_pun, d_pburn,
+ * d_gun_out, d_gburn_out float [cells]; d_mask float [cells] or NULL;
+ * outputs d_gun, d_gburn float [cells]; *d_gpc (one double, or NULL)
+ * accumulates dL/dp_continue.  The results are those of jwf_step_relaxed_bwd
+ * on the same inputs.
+ *
+ * Scratch: one file-scope device array of about 16 MiB (one float per cell
+ * for JWF_NOALLOC_MAX_CELLS cells, plus reduction partial sums) that every
+ * GPU loading the library holds until the process exits.  Errors: JWF_EINVAL
+ * when n_envs * H * W exceeds JWF_NOALLOC_MAX_CELLS, for null pointers,
+ * p_continue outside [0, 1] or outputs that alias inputs; JWF_ECUDA when the
+ * device or a launch fails.  The first call on each device looks up the
+ * array's device address with that device current: make that first call
+ * before any stream capture.  All calls share the array, which keeps the
+ * last call's contents: calls that overlap on the GPU (on different streams
+ * or from different host threads) race, so the caller must serialise them. */
+JWF_API jwf_status jwf_step_relaxed_bwd_noalloc(int32_t n_envs, int32_t H, int32_t W,
+                                                const float* d_r, float p_continue,
+                                                const float* d_pun, const float* d_pburn,
+                                                const float* d_mask, const float* d_gun_out,
+                                                const float* d_gburn_out, float* d_gun,
+                                                float* d_gburn, double* d_gpc, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

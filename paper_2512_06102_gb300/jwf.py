@@ -72,7 +72,10 @@ _SIGS = {
     "jwf_step_relaxed_fwd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_step_relaxed_bwd": (ctypes.c_int, [_VP] * 11),
     "jwf_rates_bwd": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 9),
+    "jwf_step_relaxed_bwd_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP,
+                                                    ctypes.c_float] + [_VP] * 9),
 }
+NOALLOC_MAX_CELLS = 1 << 22
 EXPORTS = tuple(_SIGS)
 
 _lib = None
@@ -144,6 +147,24 @@ class ParamSet:
         d = p if isinstance(p, dict) else p.__dict__
         keys = ParamSet.__dataclass_fields__.keys()
         return ParamSet(**{k: d[k] for k in keys if k in d})
+
+
+def relaxed_bwd_noalloc(n_envs: int, H: int, W: int, r, p_continue: float, pun, pburn, gun_out, gburn_out,
+                        mask=None, gun=None, gburn=None, gpc=None, stream=None):
+    """jwf_step_relaxed_bwd_noalloc: the relaxed adjoint step for a uniform
+    batch without a context, for callers that cannot allocate device memory
+    (the library allocates nothing; output tensors the caller does not pass
+    are created here, by torch).  Returns (gun, gburn)."""
+    if gun is None:
+        gun = torch.empty_like(pun)
+    if gburn is None:
+        gburn = torch.empty_like(pburn)
+    st = lib().jwf_step_relaxed_bwd_noalloc(int(n_envs), int(H), int(W), _ptr(r), ctypes.c_float(p_continue),
+                                            _ptr(pun), _ptr(pburn), _ptr(mask), _ptr(gun_out), _ptr(gburn_out),
+                                            _ptr(gun), _ptr(gburn), _ptr(gpc), _stream(stream))
+    if st != 0:
+        raise JwfError(st, "jwf_step_relaxed_bwd_noalloc")
+    return gun, gburn
 
 
 class Sim:
