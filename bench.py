@@ -191,9 +191,14 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ev_k = []
 
+    sim.set_kernel(jwf.KERNEL_FUSED)
+
     def episode(record=False):
+        # reset to the initial fires, (re)build the wind part of Eqs. 1-4, and
+        # run the episode; the fused kernel evaluates the ignition probability
+        # of every compared (target, source) pair from the terrain
         sim.load_state(F0_d)
-        sim.precompute_probs(cls_d, dem_d, ws_d, wd_d)
+        sim.set_terrain(cls_d, dem_d, ws_d, wd_d)
         if record:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -271,13 +276,38 @@ def run_ours(args):
     b_min = 2 * cells + 4 * n_pairs + 8 * N_ENVS * EPISODE
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "peak_source": peak_kind,
-            "traffic": kernel_traffic("k_step_resident", "paper_2512_06102_gb300/csrc/k_step.cu"),
+            "traffic": kernel_traffic("k_step_resident", "paper_2512_06102_gb300/csrc/k_resident.cu"),
             "kernel": "k_step_resident", "kernel_ms": round(t_kernel * 1e3, 3),
             "bytes_model": "2 B/cell-update state + 4 B/consumed q entry + 8 B/env-step drop",
             "algorithmic_bytes_per_launch": b_alg,
             "min_bytes_per_launch": b_min,
             "min_bytes_frac": round(b_min / t_kernel / 1e9 / hbm, 4),
             "consumed_q_entries": n_pairs, "burning_cell_steps": active}
+    # comparators on the same workload: the table path (table kernel + resident
+    # step reading q) and the plain one-launch-per-step path
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    def table_episode():
+        sim.load_state(F0_d)
+        sim.precompute_probs(cls_d, dem_d, ws_d, wd_d)
+        sim.step(EPISODE, drops_d, burning, burnt, done)
+
+    sim.set_kernel(jwf.KERNEL_RESIDENT)
+    table_episode()
+    t_table = timed(table_episode)
+    sim.set_kernel(jwf.KERNEL_PLAIN)
+    t_plain = timed(table_episode)
+    comparators = {"table_resident_ms_per_step": round(t_table * 1e3, 3),
+                   "plain_one_launch_per_step_ms_per_step": round(t_plain * 1e3, 3),
+                   "speedup_vs_plain": round(t_plain / (t_max / args.steps), 2),
+                   "speedup_vs_table_resident": round(t_table / (t_max / args.steps), 2)}
     sim.close()
     del sim
 
@@ -299,6 +329,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2.15 GB probability table rebuilt and read every step)"},
             "env_steps_per_s": world * N_ENVS * EPISODE * args.steps / t_max,
             "roofline": roof,
+            "comparators": comparators,
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": 3 * args.steps,

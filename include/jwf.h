@@ -140,6 +140,17 @@ JWF_API int64_t jwf_env_offset(const jwf_ctx* ctx, int32_t e);     /* off[e]; e 
 JWF_API jwf_status jwf_precompute_probs(jwf_ctx* ctx, const uint8_t* d_class, const float* d_dem,
                                 const float* d_wind_speed, const float* d_wind_dir, void* stream);
 
+/* Register the terrain the fused step kernel (JWF_KERNEL_FUSED) evaluates
+ * Eqs. 1-4 from, without building the table: landcover class ids (uint8
+ * [cells]), elevation (float [cells]) and per-env wind speed and direction
+ * (float [N]; per-cell wind is JWF_EUNSUPPORTED here).  The pointers are
+ * borrowed: the caller keeps the buffers alive and unchanged while it steps.
+ * jwf_precompute_probs registers its inputs the same way.  Uses the
+ * parameters of the last jwf_set_params (later parameter changes are picked
+ * up by the next jwf_step). */
+JWF_API jwf_status jwf_set_terrain(jwf_ctx* ctx, const uint8_t* d_class, const float* d_dem,
+                                   const float* d_wind_speed, const float* d_wind_dir, void* stream);
+
 /* Replace the tables with caller data: d_q float [cells][8] (required),
  * d_r float [cells][8] (may be NULL; requires JWF_KEEP_RATES otherwise).
  * Device-to-device copies on the stream. */
@@ -187,12 +198,20 @@ JWF_API jwf_status jwf_apply_action(jwf_ctx* ctx, const uint8_t* d_mask, void* s
 JWF_API jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
                     int32_t* d_burnt, uint8_t* d_done, void* stream);
 
-/* Kernel choice for jwf_step (default JWF_KERNEL_AUTO). */
+/* Kernel choice for jwf_step (default JWF_KERNEL_AUTO).  All kernels give
+ * identical results for the same probabilities. */
 typedef enum {
     JWF_KERNEL_AUTO = 0,      /* resident when every env fits shared memory  */
     JWF_KERNEL_PLAIN = 1,     /* one launch per step, state in global memory */
-    JWF_KERNEL_RESIDENT = 2   /* whole env in shared memory, k steps/launch  */
+    JWF_KERNEL_RESIDENT = 2,  /* whole env in shared memory, k steps/launch  */
+    JWF_KERNEL_FUSED = 3      /* resident, evaluating the probability of each
+                                 compared (target, source) pair from the
+                                 terrain of jwf_set_terrain instead of reading
+                                 the table; bit-identical to the table built
+                                 by jwf_precompute_probs from that terrain   */
 } jwf_kernel;
+/* Choose the step kernel; threads_per_env = 0 picks a block size by env size,
+ * else 32, 64, 128 or 256 threads per env (resident kernels). */
 JWF_API jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_env);
 
 /* Instrumentation: while d_pairs (one uint64 on the device, owned by the

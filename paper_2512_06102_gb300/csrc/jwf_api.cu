@@ -217,6 +217,7 @@ jwf_status jwf_set_params(jwf_ctx* ctx, const jwf_params* p) {
     }
     ctx->P = P;
     ctx->have_params = true;
+    ctx->wexp_stale = true;
     return JWF_OK;
 }
 
@@ -244,7 +245,34 @@ jwf_status jwf_precompute_probs(jwf_ctx* ctx, const uint8_t* d_class, const floa
     JWF_CUDA_TRY(ctx, jwf_launch_prob_table(ctx, d_class, d_dem, d_wind_speed, d_wind_dir, S(stream)),
                  "jwf_precompute_probs");
     ctx->have_table = true;
+    if (!(ctx->flags & JWF_WIND_PER_CELL)) {
+        // the table build also left the per-env wind exponent in d_wexp
+        ctx->t_cls = d_class;
+        ctx->t_dem = d_dem;
+        ctx->t_ws = d_wind_speed;
+        ctx->t_wd = d_wind_dir;
+        ctx->have_terrain = true;
+        ctx->wexp_stale = false;
+    }
     ctx->have_rates = (ctx->flags & JWF_KEEP_RATES) != 0u;
+    return JWF_OK;
+}
+
+jwf_status jwf_set_terrain(jwf_ctx* ctx, const uint8_t* d_class, const float* d_dem,
+                           const float* d_wind_speed, const float* d_wind_dir, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_set_terrain: no parameters set");
+    if (d_class == nullptr || d_dem == nullptr || d_wind_speed == nullptr || d_wind_dir == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_set_terrain: null pointer");
+    if (ctx->flags & JWF_WIND_PER_CELL)
+        return fail(ctx, JWF_EUNSUPPORTED, "jwf_set_terrain: the fused step takes per-env wind only");
+    JWF_CUDA_TRY(ctx, jwf_launch_wind_exponent(ctx, d_wind_speed, d_wind_dir, S(stream)), "jwf_set_terrain");
+    ctx->t_cls = d_class;
+    ctx->t_dem = d_dem;
+    ctx->t_ws = d_wind_speed;
+    ctx->t_wd = d_wind_dir;
+    ctx->have_terrain = true;
+    ctx->wexp_stale = false;
     return JWF_OK;
 }
 
@@ -299,11 +327,17 @@ jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_
     if (ctx == nullptr) return JWF_EINVAL;
     if (k < 1) return fail(ctx, JWF_EINVAL, "jwf_step: k < 1");
     if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_step: no parameters set");
-    if (!ctx->have_table) return fail(ctx, JWF_ESTATE, "jwf_step: no probability table");
     if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_step: no state loaded");
-    if (ctx->kernel == JWF_KERNEL_RESIDENT && !use_resident(ctx))
+    const bool fused = ctx->kernel == JWF_KERNEL_FUSED;
+    if (fused && !ctx->have_terrain) return fail(ctx, JWF_ESTATE, "jwf_step: fused step needs jwf_set_terrain");
+    if (!fused && !ctx->have_table) return fail(ctx, JWF_ESTATE, "jwf_step: no probability table");
+    if ((ctx->kernel == JWF_KERNEL_RESIDENT || fused) && !use_resident(ctx))
         return fail(ctx, JWF_EUNSUPPORTED, "jwf_step: largest env does not fit shared memory");
     cudaError_t err;
+    if (fused && ctx->wexp_stale) {
+        JWF_CUDA_TRY(ctx, jwf_launch_wind_exponent(ctx, ctx->t_ws, ctx->t_wd, S(stream)), "jwf_step");
+        ctx->wexp_stale = false;
+    }
     if (use_resident(ctx))
         err = jwf_launch_step_resident(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
     else
@@ -314,7 +348,8 @@ jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_
 
 jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_env) {
     if (ctx == nullptr) return JWF_EINVAL;
-    if (kernel != JWF_KERNEL_AUTO && kernel != JWF_KERNEL_PLAIN && kernel != JWF_KERNEL_RESIDENT)
+    if (kernel != JWF_KERNEL_AUTO && kernel != JWF_KERNEL_PLAIN && kernel != JWF_KERNEL_RESIDENT &&
+        kernel != JWF_KERNEL_FUSED)
         return fail(ctx, JWF_EINVAL, "jwf_set_kernel: unknown kernel");
     if (threads_per_env != 0 && (threads_per_env < 32 || threads_per_env > 256 || threads_per_env % 32 != 0))
         return fail(ctx, JWF_EINVAL, "jwf_set_kernel: threads_per_env must be 0 or a multiple of 32 in [32, 256]");

@@ -100,6 +100,13 @@ struct jwf_ctx {
     float* d_glam = nullptr;             // [cells] adjoint scratch of the relaxed step
     unsigned long long* d_pairs = nullptr;  // caller's instrumentation counter (not owned)
     float2* d_wexp = nullptr;            // [N][8] wind exponent (hi, lo) scratch of the table build
+    // terrain borrowed from the caller for the fused step (jwf_set_terrain)
+    const uint8_t* t_cls = nullptr;
+    const float* t_dem = nullptr;
+    const float* t_ws = nullptr;
+    const float* t_wd = nullptr;
+    bool have_terrain = false;
+    bool wexp_stale = true;              // parameters changed since d_wexp was built
 
     JwfDevParams P{};
     bool have_params = false, have_table = false, have_rates = false, have_state = false;
@@ -114,6 +121,7 @@ struct jwf_ctx {
 // ---------------------------------------------------------------------------
 // Launchers (host functions; each returns cudaGetLastError() of its launch).
 // ---------------------------------------------------------------------------
+cudaError_t jwf_launch_wind_exponent(const jwf_ctx* c, const float* ws, const float* wd, cudaStream_t s);
 cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
                                   const float* ws, const float* wd, cudaStream_t s);
 cudaError_t jwf_launch_rates_bwd(jwf_ctx* c, int32_t n_steps, const float* glam,

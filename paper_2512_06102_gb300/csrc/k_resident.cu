@@ -1,0 +1,591 @@
+// k_resident.cu -- the shared-memory-resident discrete step (Section 3
+// "Stochastic update", tanker action of Section 4) running k steps per launch.
+//
+// Persistent CTAs pull whole envs from a work queue (largest first) and keep
+// each env in shared memory as bit planes, 32 cells per word: burning B
+// (double-buffered, one zero row above and below), can-burn C and burned D.
+// One step:
+//   * warps claim 32-word chunks from a per-step counter (dynamic, so the warp
+//     holding the fire front does not set the pace of the others); each lane
+//     owns one word and finds its can-burn cells with a burning neighbour and
+//     its burning cells from eight shifted ORs of the burning plane;
+//   * the warp shares its active cells out across its lanes (ballot + prefix
+//     sum), so every lane draws Philox numbers and evaluates ignition
+//     probabilities for the same number of cells;
+//   * the owner lane writes the next burning word, applies the next step's
+//     tanker drop to it, and counts; one __syncthreads ends the step.
+// The ignition probability of a compared (target, source) pair is read from
+// the q table or, in the fused variant, evaluated on the spot with the same
+// rate code as the table kernel (rate_model.cuh), so both variants draw the
+// same numbers against the same probabilities.  An env whose fire is out
+// stops early; with auto-reset it restarts from its initial state instead.
+#include <type_traits>
+
+#include "jwf_internal.cuh"
+#include "rate_model.cuh"
+
+namespace {
+
+constexpr int kListCap = 256;      // active cells shared out per warp pass
+// per warp: item list, ign and out words, pair list (fused variant)
+constexpr int kWarpScratch = kListCap + 64 + 256;
+
+struct ResArgs {
+    const int32_t* H;
+    const int32_t* W;
+    const int64_t* off;
+    const int32_t* order;
+    int32_t N;
+    uint8_t* F;                 // in/out (in place: one CTA per env)
+    const uint8_t* F0;
+    const float* q;             // table variant
+    const uint8_t* cls;         // fused variant: landcover, elevation, wind exponent
+    const float* dem;
+    const float2* wexp;         // [N][8] (hi, lo)
+    const int32_t* drops;       // [k][N][2] or null
+    int32_t* t;
+    int32_t* episode;
+    int32_t* out_burning;       // [k][N] or null
+    int32_t* out_burnt;
+    uint8_t* out_done;
+    uint32_t* queue;            // [0] cursor, [1] CTAs finished
+    unsigned long long* pairs;  // optional: count of (target, source) pairs compared
+    int32_t k;
+    int32_t t_max;
+    int32_t R;
+    int32_t auto_reset;
+    uint32_t key0, key1;
+    float p_continue;
+};
+
+// words of dynamic shared memory for the planes of an H x W env
+__host__ __device__ __forceinline__ int res_plane_words(int H, int W) {
+    const int WW = (W + 31) >> 5;
+    return 2 * (H + 2) * WW + 2 * H * WW;
+}
+
+// 4 states (one uint32) -> 4-bit mask of the bytes equal to `pattern`
+__device__ __forceinline__ uint32_t nib_eq(uint32_t w, uint32_t pattern) {
+    const uint32_t m = __vcmpeq4(w, pattern);
+    return (((m & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
+}
+// 4-bit mask -> 4 bytes of 0 / 1
+__device__ __forceinline__ uint32_t nib_spread(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
+
+// Load env into planes: one word (32 cells) per thread iteration.
+__device__ void res_load(const uint8_t* __restrict__ Fe, int H, int W, int WW, bool vec,
+                         uint32_t* Bp, uint32_t* C, uint32_t* D) {
+    const int words = H * WW;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) {
+        const int y = i / WW, w = i - (i / WW) * WW;
+        const int x0 = w << 5;
+        const uint8_t* src = Fe + (int64_t)y * W + x0;
+        uint32_t b = 0, c = 0, dd = 0;
+        if (vec) {
+            const uint4 lo = __ldg(reinterpret_cast<const uint4*>(src));
+            const uint4 hi = __ldg(reinterpret_cast<const uint4*>(src) + 1);
+            const uint32_t v8[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                c |= nib_eq(v8[k], 0x01010101u) << (4 * k);
+                b |= nib_eq(v8[k], 0x02020202u) << (4 * k);
+                dd |= nib_eq(v8[k], 0x03030303u) << (4 * k);
+            }
+        } else {
+            const int n = min(32, W - x0);
+            for (int j = 0; j < n; ++j) {
+                const uint32_t s = src[j];
+                b |= (uint32_t)(s == 2) << j;
+                c |= (uint32_t)(s == 1) << j;
+                dd |= (uint32_t)(s == 3) << j;
+            }
+        }
+        Bp[(y + 1) * WW + w] = b;
+        C[i] = c;
+        D[i] = dd;
+    }
+}
+
+__device__ void res_store(uint8_t* __restrict__ Fe, int H, int W, int WW, bool vec,
+                          const uint32_t* Bp, const uint32_t* C, const uint32_t* D) {
+    const int words = H * WW;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) {
+        const int y = i / WW, w = i - (i / WW) * WW;
+        const int x0 = w << 5;
+        uint8_t* dst = Fe + (int64_t)y * W + x0;
+        const uint32_t b = Bp[(y + 1) * WW + w], c = C[i], dd = D[i];
+        if (vec) {
+            uint32_t v8[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int sh = 4 * k;
+                v8[k] = nib_spread((c >> sh) & 0xFu) + 2u * nib_spread((b >> sh) & 0xFu) +
+                        3u * nib_spread((dd >> sh) & 0xFu);
+            }
+            reinterpret_cast<uint4*>(dst)[0] = make_uint4(v8[0], v8[1], v8[2], v8[3]);
+            reinterpret_cast<uint4*>(dst)[1] = make_uint4(v8[4], v8[5], v8[6], v8[7]);
+        } else {
+            const int n = min(32, W - x0);
+            for (int j = 0; j < n; ++j)
+                dst[j] = (uint8_t)(((c >> j) & 1u) + ((b >> j) & 1u) * 2u + ((dd >> j) & 1u) * 3u);
+        }
+    }
+}
+
+// Bits of word w (cells 32w .. 32w+31) of row y covered by a drop of radius R
+// at (cx, cy), clipped to the grid; 0 for no drop.
+__device__ __forceinline__ uint32_t drop_bits(int y, int w, int W, int cx, int cy, int R) {
+    if (cx < 0 || cy < 0 || abs(y - cy) > R) return 0u;
+    const int lo = max(max(cx - R, 0) - (w << 5), 0);
+    const int hi = min(min(cx + R, W - 1) - (w << 5), 31);
+    if (lo > hi) return 0u;
+    const uint32_t span = (hi - lo == 31) ? 0xffffffffu : ((1u << (hi - lo + 1)) - 1u);
+    return span << lo;
+}
+
+// Apply a drop to the planes (burning under it -> burned), all threads.
+__device__ void res_action(int H, int W, int WW, uint32_t* Bp, uint32_t* D, int cx, int cy, int R) {
+    if (cx < 0 || cy < 0) return;
+    const int y0 = max(cy - R, 0), y1 = min(cy + R, H - 1);
+    if (y0 > y1) return;
+    const int w0 = max(cx - R, 0) >> 5, w1 = min(cx + R, W - 1) >> 5;
+    const int nw = w1 - w0 + 1;
+    const int total = (y1 - y0 + 1) * nw;
+    for (int j = threadIdx.x; j < total; j += blockDim.x) {
+        const int y = y0 + j / nw, w = w0 + j % nw;
+        const uint32_t m = drop_bits(y, w, W, cx, cy, R);
+        uint32_t* bp = &Bp[(y + 1) * WW + w];
+        const uint32_t doused = *bp & m;
+        *bp &= ~m;
+        D[y * WW + w] |= doused;
+    }
+}
+
+// Table variant: does can-burn cell `cell` ignite this step?  dm: bit d set
+// when its source in direction d burns.  Draws: slot 0 words -> d 0..3, slot 1
+// words -> d 4..7; success iff u < q.  Any success ignites, so the second half
+// is skipped once the first has succeeded.
+__device__ __forceinline__ bool ignites(const ResArgs& a, int e, int64_t off, uint32_t cell, uint32_t dm,
+                                        uint32_t tt, uint32_t ep4) {
+    const float4* q4 = reinterpret_cast<const float4*>(a.q + (off + cell) * 8);
+    bool ign = false;
+    if (dm & 0x0Fu) {
+        const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4), a.key0, a.key1);
+        const float4 qa = __ldg(q4);
+        ign |= ((dm & 1u) && jwf_u24(u.x) < qa.x) || ((dm & 2u) && jwf_u24(u.y) < qa.y) ||
+               ((dm & 4u) && jwf_u24(u.z) < qa.z) || ((dm & 8u) && jwf_u24(u.w) < qa.w);
+    }
+    if (!ign && (dm & 0xF0u)) {
+        const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 1u), a.key0, a.key1);
+        const float4 qb = __ldg(q4 + 1);
+        ign |= ((dm & 16u) && jwf_u24(u.x) < qb.x) || ((dm & 32u) && jwf_u24(u.y) < qb.y) ||
+               ((dm & 64u) && jwf_u24(u.z) < qb.z) || ((dm & 128u) && jwf_u24(u.w) < qb.w);
+    }
+    return ign;
+}
+
+// Fused variant: the candidate cells of list[it0 .. it0+32) are flattened
+// into (cell, direction) pairs, one pair per lane per round, so the rate code
+// of Eqs. 1-4 runs once per pair rather than once per direction present in
+// any lane.  A success sets the cell's bit in ignw.
+__device__ __forceinline__ void fused_pairs(const ResArgs& a, const RateConsts& K, const uint32_t* list,
+                                            uint32_t* plist, uint32_t* ignw, int it0, int n_pass, int base,
+                                            int e, int64_t off, int W, int WW, uint32_t tt, uint32_t ep4,
+                                            int lane) {
+    const int it = it0 + lane;
+    const uint32_t item = it < n_pass ? list[it] : 0u;
+    const uint32_t dm = (item & (1u << 18)) ? (item >> 10) & 0xFFu : 0u;
+    const int np = __popc(dm);
+    int incl = np;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int ptotal = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = incl - np;
+    for (uint32_t rem = dm; rem != 0u; rem &= rem - 1u) plist[pos++] = ((uint32_t)lane << 3) | (__ffs(rem) - 1);
+    __syncwarp();
+    for (int p = lane; p < ptotal; p += 32) {
+        const uint32_t pe = plist[p];
+        const int d = (int)(pe & 7u);
+        const uint32_t itm = list[it0 + (int)(pe >> 3)];
+        const int ol = (int)(itm >> 5) & 31;
+        const int j = (int)itm & 31;
+        const int ii = base + ol;
+        const int yy = ii / WW;
+        const int xx = ((ii - yy * WW) << 5) + j;
+        const uint32_t cell = (uint32_t)(yy * W + xx);
+        const int64_t v = off + cell;
+        const int64_t u = off + (int64_t)(yy - jwf_dr(d)) * W + (xx - jwf_dx(d));
+        const int cv = a.cls[v], cu = a.cls[u];
+        const float zv = a.dem[v], zu = a.dem[u];
+        const float2 w2 = a.wexp[e * 8 + d];
+        const uint4 u4 = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + (uint32_t)(d >> 2)), a.key0, a.key1);
+        const uint32_t uw = (d & 3) == 0 ? u4.x : (d & 3) == 1 ? u4.y : (d & 3) == 2 ? u4.z : u4.w;
+        const float r = rate_of(K.G[cv][cu], zv, zu, {w2.x, w2.y}, d, K);
+        if (jwf_u24(uw) < prob_of(r)) atomicOr(&ignw[ol], 1u << j);
+    }
+    __syncwarp();
+}
+
+template <int NT, bool FUSED>
+__global__ void __launch_bounds__(NT)
+k_step_resident(const ResArgs a, const RateConsts Kc) {
+    extern __shared__ uint32_t sm[];
+    __shared__ int32_t s_env;
+    __shared__ int32_t s_cnt[3][2];
+    __shared__ int32_t s_chunk[3];
+    // the rate constants live in shared memory only in the fused variant
+    __shared__ typename std::conditional<FUSED, RateConsts, int>::type sK_store;
+    const RateConsts& sK = *reinterpret_cast<const RateConsts*>(&sK_store);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (FUSED) {
+        for (int i = threadIdx.x; i < (int)(sizeof(RateConsts) / 4); i += NT)
+            reinterpret_cast<float*>(&sK_store)[i] = reinterpret_cast<const float*>(&Kc)[i];
+    }
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t slot = atomicAdd(&a.queue[0], 1u);
+            s_env = (slot < (uint32_t)a.N) ? a.order[slot] : -1;
+        }
+        __syncthreads();
+        const int e = s_env;
+        __syncthreads();
+        if (e < 0) break;
+
+        const int H = a.H[e], W = a.W[e];
+        const int WW = (W + 31) >> 5;
+        const int pw = (H + 2) * WW;
+        const int words = H * WW;
+        const int nchunks = (words + 31) >> 5;
+        uint32_t* B0 = sm;
+        uint32_t* B1 = B0 + pw;
+        uint32_t* C = B1 + pw;
+        uint32_t* D = C + words;
+        uint32_t* list = D + words + warp * kWarpScratch;      // per-warp scratch
+        uint32_t* ignw = list + kListCap;
+        uint32_t* outw = ignw + 32;
+        uint32_t* plist = outw + 32;
+        const int64_t off = a.off[e];
+        uint8_t* Fe = a.F + off;
+        const bool vec = ((W & 31) == 0) && ((off & 15) == 0);
+
+        // zero both burning planes (the padding rows must read as 0), then load
+        for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
+        if (threadIdx.x < 6) s_cnt[threadIdx.x / 2][threadIdx.x & 1] = 0;
+        if (threadIdx.x < 3) s_chunk[threadIdx.x] = 0;
+        ignw[lane] = 0u;
+        outw[lane] = 0u;
+        __syncthreads();
+        res_load(Fe, H, W, WW, vec, B0, C, D);
+        __syncthreads();
+        if (a.drops != nullptr && a.k > 0) {
+            res_action(H, W, WW, B0, D, a.drops[(int64_t)e * 2], a.drops[(int64_t)e * 2 + 1], a.R);
+            __syncthreads();
+        }
+
+        int32_t t = a.t[e];
+        int32_t ep = a.episode[e];
+        uint32_t* Bc = B0;
+        uint32_t* Bn = B1;
+        int32_t last_burnt = 0;
+        for (int s = 0; s < a.k; ++s) {
+            const uint32_t tt = (uint32_t)t;
+            const uint32_t ep4 = 4u * (uint32_t)ep;
+            if (threadIdx.x == 0) {
+                s_cnt[(s + 1) % 3][0] = 0;
+                s_cnt[(s + 1) % 3][1] = 0;
+                s_chunk[(s + 1) % 3] = 0;
+            }
+            // the next step's drop is applied while the new planes are written
+            int cxn = -1, cyn = -1;
+            if (a.drops != nullptr && s + 1 < a.k) {
+                cxn = a.drops[((int64_t)(s + 1) * a.N + e) * 2];
+                cyn = a.drops[((int64_t)(s + 1) * a.N + e) * 2 + 1];
+            }
+            int my_b = 0, my_d = 0;
+            uint32_t my_pairs = 0;
+            for (;;) {
+                int c = 0;
+                if (lane == 0) c = atomicAdd(&s_chunk[s % 3], 1);
+                c = __shfl_sync(0xffffffffu, c, 0);
+                if (c >= nchunks) break;
+                const int base = c << 5;
+                const int i = base + lane;
+                uint32_t burn = 0, cand = 0;
+                uint32_t sd[8];
+                int y = 0, w = 0;
+                if (i < words) {
+                    y = i / WW;
+                    w = i - y * WW;
+                    const uint32_t* bp = &Bc[WW + i];             // row y + 1 of the padded plane
+                    const bool hl = w > 0, hr = w + 1 < WW;
+                    const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
+                    const uint32_t uc = bp[-WW], ul = hl ? bp[-WW - 1] : 0u, ur = hr ? bp[-WW + 1] : 0u;
+                    const uint32_t dc = bp[WW], dl = hl ? bp[WW - 1] : 0u, dr = hr ? bp[WW + 1] : 0u;
+                    // source of direction d for target (y, x) sits at (y - DR[d], x - DX[d])
+                    sd[0] = (bc << 1) | (bl >> 31);   // E : (y,   x-1)
+                    sd[1] = (dc << 1) | (dl >> 31);   // NE: (y+1, x-1)
+                    sd[2] = dc;                       // N : (y+1, x)
+                    sd[3] = (dc >> 1) | (dr << 31);   // NW: (y+1, x+1)
+                    sd[4] = (bc >> 1) | (br << 31);   // W : (y,   x+1)
+                    sd[5] = (uc >> 1) | (ur << 31);   // SW: (y-1, x+1)
+                    sd[6] = uc;                       // S : (y-1, x)
+                    sd[7] = (uc << 1) | (ul >> 31);   // SE: (y-1, x-1)
+                    const uint32_t any = sd[0] | sd[1] | sd[2] | sd[3] | sd[4] | sd[5] | sd[6] | sd[7];
+                    cand = C[i] & any;
+                    burn = bc;
+                } else {
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) sd[d] = 0u;
+                }
+                const uint32_t act = cand | burn;
+                if (__ballot_sync(0xffffffffu, act != 0u) != 0u) {
+                    // share out the active cells of these 32 words across the warp
+                    const int n_act = __popc(act);
+                    int incl = n_act;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, incl, 31);
+                    const int excl = incl - n_act;
+                    for (int pass = 0; pass < total; pass += kListCap) {
+                        uint32_t rem = act;
+                        int idx = excl;
+                        while (rem != 0u) {
+                            const int j = __ffs(rem) - 1;
+                            rem &= rem - 1u;
+                            if (idx >= pass && idx < pass + kListCap) {
+                                uint32_t item = ((uint32_t)lane << 5) | (uint32_t)j;
+                                if ((cand >> j) & 1u) {
+                                    uint32_t dm = 0;
+#pragma unroll
+                                    for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
+                                    item |= (dm << 10) | (1u << 18);
+                                }
+                                list[idx - pass] = item;
+                            }
+                            ++idx;
+                        }
+                        __syncwarp();
+                        const int n_pass = min(kListCap, total - pass);
+                        for (int it = lane; it < n_pass; it += 32) {
+                            const uint32_t item = list[it];
+                            const int ol = (int)(item >> 5) & 31;    // owner lane
+                            const int j = (int)item & 31;
+                            const int ii = base + ol;
+                            const int yy = ii / WW;
+                            const int xx = ((ii - yy * WW) << 5) + j;
+                            const uint32_t cell = (uint32_t)(yy * W + xx);
+                            if (item & (1u << 18)) {
+                                const uint32_t dm = (item >> 10) & 0xFFu;
+                                my_pairs += __popc(dm);
+                                if (!FUSED && ignites(a, e, off, cell, dm, tt, ep4))
+                                    atomicOr(&ignw[ol], 1u << j);
+                            } else {
+                                const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
+                                if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&outw[ol], 1u << j);
+                            }
+                        }
+                        if (FUSED) {
+                            for (int it0 = 0; it0 < n_pass; it0 += 32)
+                                fused_pairs(a, sK, list, plist, ignw, it0, n_pass, base, e, off, W, WW, tt, ep4,
+                                            lane);
+                        }
+                        __syncwarp();
+                    }
+                }
+                if (i < words) {
+                    const uint32_t ig = ignw[lane], ou = outw[lane];
+                    uint32_t nb = (burn & ~ou) | ig;
+                    uint32_t nd = D[i] | ou;
+                    my_b += __popc(nb);
+                    my_d += __popc(nd);
+                    const uint32_t m = drop_bits(y, w, W, cxn, cyn, a.R);
+                    nd |= nb & m;
+                    nb &= ~m;
+                    Bn[WW + i] = nb;
+                    D[i] = nd;
+                    C[i] &= ~ig;
+                    ignw[lane] = 0u;
+                    outw[lane] = 0u;
+                }
+                __syncwarp();
+            }
+            // counts of this step (before the next drop), one barrier
+            if (a.pairs != nullptr) {
+                my_pairs = __reduce_add_sync(0xffffffffu, my_pairs);
+                if (lane == 0 && my_pairs) atomicAdd(a.pairs, (unsigned long long)my_pairs);
+            }
+            my_b = __reduce_add_sync(0xffffffffu, my_b);
+            my_d = __reduce_add_sync(0xffffffffu, my_d);
+            if (lane == 0) {
+                atomicAdd(&s_cnt[s % 3][0], my_b);
+                atomicAdd(&s_cnt[s % 3][1], my_d);
+            }
+            __syncthreads();
+            const int32_t nb = s_cnt[s % 3][0];
+            const int32_t nd = s_cnt[s % 3][1];
+            uint32_t* tmp = Bc;
+            Bc = Bn;
+            Bn = tmp;
+            t += 1;
+            const bool done = (nb == 0) || (a.t_max > 0 && t >= a.t_max);
+            if (threadIdx.x == 0) {
+                const int64_t o = (int64_t)s * a.N + e;
+                if (a.out_burning) a.out_burning[o] = nb;
+                if (a.out_burnt) a.out_burnt[o] = nd;
+                if (a.out_done) a.out_done[o] = done ? 1 : 0;
+            }
+            last_burnt = nd;
+            if (done && a.auto_reset) {
+                // restart from the initial state with a fresh random stream
+                t = 0;
+                ep += 1;
+                for (int i2 = threadIdx.x; i2 < pw; i2 += NT) Bc[i2] = 0u;
+                __syncthreads();
+                res_load(a.F0 + off, H, W, WW, vec, Bc, C, D);
+                __syncthreads();
+                if (cxn >= 0) {
+                    res_action(H, W, WW, Bc, D, cxn, cyn, a.R);
+                    __syncthreads();
+                }
+                continue;
+            }
+            if (nb == 0) {
+                // fire out: nothing can change any more; fill the remaining steps
+                for (int s2 = s + 1 + (int)threadIdx.x; s2 < a.k; s2 += NT) {
+                    const int64_t o = (int64_t)s2 * a.N + e;
+                    if (a.out_burning) a.out_burning[o] = 0;
+                    if (a.out_burnt) a.out_burnt[o] = last_burnt;
+                    if (a.out_done) a.out_done[o] = 1;
+                }
+                t += a.k - (s + 1);
+                break;
+            }
+        }
+        __syncthreads();
+        res_store(Fe, H, W, WW, vec, Bc, C, D);
+        if (threadIdx.x == 0) {
+            a.t[e] = t;
+            a.episode[e] = ep;
+        }
+        __syncthreads();
+    }
+    // the last CTA to leave resets the queue for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t fin = atomicAdd(&a.queue[1], 1u);
+        if (fin == gridDim.x - 1) {
+            a.queue[0] = 0u;
+            a.queue[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+constexpr int kMaxDev = 64;
+
+// Per-instantiation launch facts, cached per device so that a launch after
+// the first one makes no attribute or occupancy query.
+template <int NT, bool FUSED>
+cudaError_t launch_t(const jwf_ctx* c, const ResArgs& a, const RateConsts& K, size_t smem, cudaStream_t s) {
+    static size_t set_smem[kMaxDev] = {};
+    static size_t occ_smem[kMaxDev] = {};
+    static int occ_blocks[kMaxDev] = {};
+    const int dev = c->device;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    cudaError_t err;
+    if (smem > set_smem[dev]) {
+        err = cudaFuncSetAttribute(k_step_resident<NT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        set_smem[dev] = smem;
+    }
+    if (occ_smem[dev] != smem || occ_blocks[dev] == 0) {
+        int per_sm = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_resident<NT, FUSED>, NT, smem);
+        if (err != cudaSuccess) return err;
+        occ_blocks[dev] = per_sm;
+        occ_smem[dev] = smem;
+    }
+    if (occ_blocks[dev] < 1) return cudaErrorInvalidConfiguration;
+    int64_t grid = (int64_t)occ_blocks[dev] * c->num_sms;
+    if (grid > c->N) grid = c->N;
+    k_step_resident<NT, FUSED><<<(unsigned)grid, NT, smem, s>>>(a, K);
+    return cudaGetLastError();
+}
+
+template <bool FUSED>
+cudaError_t launch_v(const jwf_ctx* c, int threads, const ResArgs& a, const RateConsts& K, size_t smem,
+                     cudaStream_t s) {
+    switch (threads) {
+        case 32: return launch_t<32, FUSED>(c, a, K, smem, s);
+        case 64: return launch_t<64, FUSED>(c, a, K, smem, s);
+        case 128: return launch_t<128, FUSED>(c, a, K, smem, s);
+        case 256: return launch_t<256, FUSED>(c, a, K, smem, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+void jwf_rate_consts(const jwf_ctx* c, RateConsts* K);
+
+size_t jwf_resident_smem(int32_t H, int32_t W, int threads) {
+    const int nwarps = threads / 32;
+    return (size_t)(res_plane_words(H, W) + nwarps * kWarpScratch) * sizeof(uint32_t);
+}
+
+int jwf_resident_threads(int32_t H, int32_t W) {
+    const int64_t words = (int64_t)H * ((W + 31) / 32);
+    if (words <= 64) return 32;
+    if (words <= 256) return 64;
+    if (words <= 2048) return 128;
+    return 256;
+}
+
+cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
+                                     int32_t* burnt, uint8_t* done, cudaStream_t s) {
+    int threads = c->threads_per_env > 0 ? c->threads_per_env : jwf_resident_threads(c->maxH, c->maxW);
+    if (threads != 32 && threads != 64 && threads != 128) threads = 256;
+    const size_t smem = jwf_resident_smem(c->maxH, c->maxW, threads);
+    const bool fused = c->kernel == JWF_KERNEL_FUSED;
+    ResArgs a;
+    a.H = c->d_H;
+    a.W = c->d_W;
+    a.off = c->d_off;
+    a.order = c->d_order;
+    a.N = c->N;
+    a.F = c->d_state[c->cur];
+    a.F0 = c->d_F0;
+    a.q = c->d_q;
+    a.cls = c->t_cls;
+    a.dem = c->t_dem;
+    a.wexp = c->d_wexp;
+    a.drops = drops;
+    a.t = c->d_t;
+    a.episode = c->d_episode;
+    a.out_burning = burning;
+    a.out_burnt = burnt;
+    a.out_done = done;
+    a.queue = c->d_queue;
+    a.pairs = c->d_pairs;
+    a.k = k;
+    a.t_max = c->t_max;
+    a.R = c->drop_radius;
+    a.auto_reset = (c->flags & JWF_AUTO_RESET) ? 1 : 0;
+    a.key0 = (uint32_t)(c->seed & 0xffffffffu);
+    a.key1 = (uint32_t)(c->seed >> 32);
+    a.p_continue = c->P.p_continue;
+    RateConsts K;
+    if (fused) {
+        jwf_rate_consts(c, &K);
+        return launch_v<true>(c, threads, a, K, smem, s);
+    }
+    K = RateConsts{};
+    return launch_v<false>(c, threads, a, K, smem, s);
+}

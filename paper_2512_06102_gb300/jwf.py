@@ -21,7 +21,7 @@ JWF_AUTO_RESET = 0x1
 JWF_WIND_PER_CELL = 0x2
 JWF_KEEP_RATES = 0x4
 
-KERNEL_AUTO, KERNEL_PLAIN, KERNEL_RESIDENT = 0, 1, 2
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_RESIDENT, KERNEL_FUSED = 0, 1, 2, 3
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
           4: "device wait timed out", 5: "call out of order", 6: "unsupported"}
@@ -61,6 +61,7 @@ _SIGS = {
     "jwf_env_offset": (ctypes.c_int64, [_VP, ctypes.c_int32]),
     "jwf_precompute_probs": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_set_probs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "jwf_set_terrain": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_get_probs": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "jwf_load_state": (ctypes.c_int, [_VP, _VP, _VP]),
     "jwf_reset": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -231,8 +232,15 @@ class Sim:
         self.params = p
 
     def precompute_probs(self, cls, dem, wind_speed, wind_dir, stream=None):
+        self._terrain = (cls, dem, wind_speed, wind_dir)
         self._check(lib().jwf_precompute_probs(self._h, _ptr(cls), _ptr(dem), _ptr(wind_speed), _ptr(wind_dir),
                                                _stream(stream)), "jwf_precompute_probs")
+
+    def set_terrain(self, cls, dem, wind_speed, wind_dir, stream=None):
+        """Register (borrow) the terrain the fused step evaluates probabilities from."""
+        self._terrain = (cls, dem, wind_speed, wind_dir)     # keep the buffers alive
+        self._check(lib().jwf_set_terrain(self._h, _ptr(cls), _ptr(dem), _ptr(wind_speed), _ptr(wind_dir),
+                                          _stream(stream)), "jwf_set_terrain")
 
     def set_probs(self, q, r=None, stream=None):
         self._check(lib().jwf_set_probs(self._h, _ptr(q), _ptr(r), _stream(stream)), "jwf_set_probs")

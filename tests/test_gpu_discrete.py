@@ -236,3 +236,71 @@ def test_plain_and_resident_agree_full_size():
     np.testing.assert_array_equal(res[0][0], res[1][0])
     for a, b in zip(res[0][1], res[1][1]):
         np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# fused step: probabilities evaluated on the spot from the terrain, with the
+# same rate code as the table kernel, so its trajectories equal the table
+# path's bit for bit (the table path equals the oracle given the same table,
+# and the table kernel is within 1e-6 of the FP64 oracle)
+# ---------------------------------------------------------------------------
+def _gpu_run(scn, k, drops, kernel, seed, threads=0, t_max=0, auto_reset=False):
+    sim = make_sim(scn, seed=seed, t_max=t_max, auto_reset=auto_reset)
+    sim.set_kernel(kernel, threads)
+    terrain = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    if kernel == jwf.KERNEL_FUSED:
+        sim.set_terrain(*terrain)
+    else:
+        sim.precompute_probs(*terrain)
+    sim.load_state(to(scn.F0))
+    out = sim.step(k, drops=None if drops is None else to(drops))
+    torch.cuda.synchronize()
+    sim.sync()
+    s, t, ep = (x.cpu().numpy().copy() for x in sim.state_views())
+    res = (s, [x.cpu().numpy() for x in out], t, ep)
+    sim.close()
+    return res
+
+
+def _same(a, b):
+    np.testing.assert_array_equal(a[0], b[0])
+    for x, y in zip(a[1], b[1]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(a[2], b[2])
+    np.testing.assert_array_equal(a[3], b[3])
+
+
+@pytest.mark.parametrize("threads", [0, 32, 256])
+@pytest.mark.parametrize("shape,N", [((128, 128), 16), ((37, 45), 5), ((1, 17), 3), ((300, 260), 2)])
+def test_fused_equals_table_path(shape, N, threads):
+    require_gpu()
+    H, W = shape
+    scn = scenarios.make_scenario(H, W, N=N, seed=21)
+    k = 80
+    drops = scenarios.drops(k, scn.H, scn.W, seed=21)
+    a = _gpu_run(scn, k, drops, jwf.KERNEL_RESIDENT, 5, threads)
+    b = _gpu_run(scn, k, drops, jwf.KERNEL_FUSED, 5, threads)
+    _same(a, b)
+    assert (a[0] == 3).sum() > 0 or H * W < 64
+
+
+def test_fused_ragged_auto_reset_equals_plain():
+    require_gpu()
+    sides = scenarios.ragged_sides(12, 32, 512, seed=6)
+    scn = scenarios.make_scenario(sides, sides[::-1], seed=6)
+    k = 70
+    drops = scenarios.drops(k, scn.H, scn.W, seed=6)
+    a = _gpu_run(scn, k, drops, jwf.KERNEL_PLAIN, 9, t_max=30, auto_reset=True)
+    b = _gpu_run(scn, k, drops, jwf.KERNEL_FUSED, 9, t_max=30, auto_reset=True)
+    _same(a, b)
+    assert (b[3] >= 2).all()
+
+
+def test_fused_equals_table_path_full_size():
+    """4096 x 128^2, one 200-step episode with drops (the benchmark workload)."""
+    require_gpu()
+    scn = scenarios.make_scenario(128, 128, N=4096, seed=0)
+    drops = scenarios.drops(200, scn.H, scn.W, seed=0)
+    a = _gpu_run(scn, 200, drops, jwf.KERNEL_RESIDENT, 1000)
+    b = _gpu_run(scn, 200, drops, jwf.KERNEL_FUSED, 1000)
+    _same(a, b)
