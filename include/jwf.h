@@ -198,27 +198,38 @@ JWF_API jwf_status jwf_apply_action(jwf_ctx* ctx, const uint8_t* d_mask, void* s
 JWF_API jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
                     int32_t* d_burnt, uint8_t* d_done, void* stream);
 
-/* Kernel choice for jwf_step (default JWF_KERNEL_AUTO).  All kernels give
- * identical results for the same probabilities. */
+/* Kernel choice for jwf_step (default JWF_KERNEL_AUTO: resident when every
+ * env fits shared memory, else tiled, else (auto-reset) plain).  All kernels
+ * give identical results for the same probabilities. */
 typedef enum {
     JWF_KERNEL_AUTO = 0,      /* resident when every env fits shared memory  */
     JWF_KERNEL_PLAIN = 1,     /* one launch per step, state in global memory */
     JWF_KERNEL_RESIDENT = 2,  /* whole env in shared memory, k steps/launch  */
-    JWF_KERNEL_FUSED = 3      /* resident, evaluating the probability of each
+    JWF_KERNEL_FUSED = 3,     /* resident, evaluating the probability of each
                                  compared (target, source) pair from the
                                  terrain of jwf_set_terrain instead of reading
                                  the table; bit-identical to the table built
-                                 by jwf_precompute_probs from that terrain   */
+                                 by jwf_precompute_probs from that terrain;
+                                 tiled (below) for envs too large for shared
+                                 memory                                      */
+    JWF_KERNEL_TILED = 4,     /* 128 x 256-cell tiles with a halo, up to 16
+                                 steps per launch (temporal blocking); tiles
+                                 with no fire within reach are skipped; for
+                                 grids larger than shared memory.  Without
+                                 JWF_AUTO_RESET only                          */
+    JWF_KERNEL_TILED_FUSED = 5 /* tiled, probabilities from the terrain      */
 } jwf_kernel;
 /* Choose the step kernel; threads_per_env = 0 picks a block size by env size,
  * else 32, 64, 128 or 256 threads per env (resident kernels). */
 JWF_API jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_env);
 
-/* Instrumentation: while d_pairs (one uint64 on the device, owned by the
- * caller) is set, the resident step kernel adds to it the number of
- * (target, burning source) probability entries it compared -- the table
- * reads of the byte model.  NULL switches counting off (the default). */
-JWF_API jwf_status jwf_set_pair_counter(jwf_ctx* ctx, unsigned long long* d_pairs);
+/* Instrumentation: while d_counts (four uint64 on the device, owned by the
+ * caller) is set, the resident step kernels add to them the work they did:
+ * [0] (target, burning source) pairs compared (the table reads of the byte
+ * model), [1] Philox blocks drawn for can-burn cells, [2] remain-burning
+ * draws, [3] 32-cell bit-plane words scanned (one per word per step).
+ * NULL switches counting off (the default). */
+JWF_API jwf_status jwf_set_pair_counter(jwf_ctx* ctx, unsigned long long* d_counts);
 
 /* Borrowed device views: current state uint8 [cells] and int32 [N] step
  * counters t and episode numbers (valid until the next call on ctx). */

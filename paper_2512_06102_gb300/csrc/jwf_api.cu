@@ -40,7 +40,9 @@ cudaError_t dev_alloc(T** p, size_t count) {
 void free_all(jwf_ctx* c) {
     void* ptrs[] = {c->d_H, c->d_W, c->d_off, c->d_order, c->d_tiles, c->d_state[0], c->d_state[1],
                     c->d_F0, c->d_q, c->d_r, c->d_t, c->d_episode, c->d_cnt, c->d_flag,
-                    c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_wexp};
+                    c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_wexp,
+                    c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
+                    c->d_tcnt};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -123,6 +125,16 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     }
     c->cells = c->off[N];
     c->n_tiles = (int64_t)tiles.size();
+    // tiles of the tiled path: (env, tile row, tile column) and per-env layout
+    std::vector<int4> tiles4, env_tiles(N);
+    for (int32_t e = 0; e < N; ++e) {
+        const int tr = (c->H[e] + jwf_tile_rows() - 1) / jwf_tile_rows();
+        const int tcn = (c->W[e] + jwf_tile_cols() - 1) / jwf_tile_cols();
+        env_tiles[e] = make_int4((int)tiles4.size(), tcn, tr, 0);
+        for (int r = 0; r < tr; ++r)
+            for (int q = 0; q < tcn; ++q) tiles4.push_back(make_int4(e, r, q, 0));
+    }
+    c->n_tiles4 = (int64_t)tiles4.size();
     std::vector<int32_t> order(N);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
@@ -153,6 +165,18 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = dev_alloc(&c->d_partials, (size_t)c->partial_cap);
     if (err == cudaSuccess) err = dev_alloc(&c->d_red_counter, 1);
     if (err == cudaSuccess) err = dev_alloc(&c->d_wexp, (size_t)N * 8);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tiles4, tiles4.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_env_tiles, (size_t)N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tact[0], tiles4.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tact[1], tiles4.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tsync, tiles4.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tburnt, tiles4.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tcnt, (size_t)16 * 2 * N);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(c->d_tiles4, tiles4.data(), tiles4.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(c->d_env_tiles, env_tiles.data(), (size_t)N * sizeof(int4), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemset(c->d_tburnt, 0, tiles4.size() * sizeof(int32_t));
     if (err == cudaSuccess) err = cudaMemcpy(c->d_H, c->H.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_W, c->W.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_off, c->off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -302,6 +326,7 @@ jwf_status jwf_get_probs(jwf_ctx* ctx, float** d_q, float** d_r) {
 jwf_status jwf_load_state(jwf_ctx* ctx, const uint8_t* d_F0, void* stream) {
     if (ctx == nullptr) return JWF_EINVAL;
     if (d_F0 == nullptr) return fail(ctx, JWF_EINVAL, "jwf_load_state: null pointer");
+    ctx->tiles_valid = false;
     JWF_CUDA_TRY(ctx, jwf_launch_load(ctx, d_F0, S(stream)), "jwf_load_state");
     ctx->have_state = true;
     return JWF_OK;
@@ -310,6 +335,7 @@ jwf_status jwf_load_state(jwf_ctx* ctx, const uint8_t* d_F0, void* stream) {
 jwf_status jwf_reset(jwf_ctx* ctx, const uint8_t* d_env_mask, void* stream) {
     if (ctx == nullptr) return JWF_EINVAL;
     if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_reset: no state loaded");
+    ctx->tiles_valid = false;
     JWF_CUDA_TRY(ctx, jwf_launch_reset(ctx, d_env_mask, S(stream)), "jwf_reset");
     return JWF_OK;
 }
@@ -318,6 +344,7 @@ jwf_status jwf_apply_action(jwf_ctx* ctx, const uint8_t* d_mask, void* stream) {
     if (ctx == nullptr) return JWF_EINVAL;
     if (d_mask == nullptr) return fail(ctx, JWF_EINVAL, "jwf_apply_action: null mask");
     if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_apply_action: no state loaded");
+    ctx->tiles_valid = false;
     JWF_CUDA_TRY(ctx, jwf_launch_action(ctx, d_mask, S(stream)), "jwf_apply_action");
     return JWF_OK;
 }
@@ -328,28 +355,43 @@ jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_
     if (k < 1) return fail(ctx, JWF_EINVAL, "jwf_step: k < 1");
     if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_step: no parameters set");
     if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_step: no state loaded");
-    const bool fused = ctx->kernel == JWF_KERNEL_FUSED;
+    const jwf_kernel kn = ctx->kernel;
+    const bool fused = kn == JWF_KERNEL_FUSED || kn == JWF_KERNEL_TILED_FUSED;
     if (fused && !ctx->have_terrain) return fail(ctx, JWF_ESTATE, "jwf_step: fused step needs jwf_set_terrain");
     if (!fused && !ctx->have_table) return fail(ctx, JWF_ESTATE, "jwf_step: no probability table");
-    if ((ctx->kernel == JWF_KERNEL_RESIDENT || fused) && !use_resident(ctx))
+    const bool fits = use_resident(ctx);
+    if (kn == JWF_KERNEL_RESIDENT && !fits)
         return fail(ctx, JWF_EUNSUPPORTED, "jwf_step: largest env does not fit shared memory");
+    bool tiled = kn == JWF_KERNEL_TILED || kn == JWF_KERNEL_TILED_FUSED ||
+                 ((kn == JWF_KERNEL_AUTO || kn == JWF_KERNEL_FUSED) && !fits);
+    bool plain = kn == JWF_KERNEL_PLAIN;
+    if (tiled && (ctx->flags & JWF_AUTO_RESET)) {
+        // rounds of several steps cannot restart an env part-way: one launch per step
+        if (fused) return fail(ctx, JWF_EUNSUPPORTED, "jwf_step: auto-reset on large grids needs the table");
+        tiled = false;
+        plain = true;
+    }
     cudaError_t err;
     if (fused && ctx->wexp_stale) {
         JWF_CUDA_TRY(ctx, jwf_launch_wind_exponent(ctx, ctx->t_ws, ctx->t_wd, S(stream)), "jwf_step");
         ctx->wexp_stale = false;
     }
-    if (use_resident(ctx))
-        err = jwf_launch_step_resident(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
-    else
-        err = jwf_launch_step_plain(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
+    if (tiled) {
+        err = jwf_launch_step_tiled(ctx, k, d_drops, d_burning, d_burnt, d_done, fused, S(stream));
+    } else {
+        ctx->tiles_valid = false;
+        if (plain)
+            err = jwf_launch_step_plain(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
+        else
+            err = jwf_launch_step_resident(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
+    }
     if (err != cudaSuccess) return cuda_fail(ctx, err, "jwf_step");
     return JWF_OK;
 }
 
 jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_env) {
     if (ctx == nullptr) return JWF_EINVAL;
-    if (kernel != JWF_KERNEL_AUTO && kernel != JWF_KERNEL_PLAIN && kernel != JWF_KERNEL_RESIDENT &&
-        kernel != JWF_KERNEL_FUSED)
+    if ((int)kernel < (int)JWF_KERNEL_AUTO || (int)kernel > (int)JWF_KERNEL_TILED_FUSED)
         return fail(ctx, JWF_EINVAL, "jwf_set_kernel: unknown kernel");
     if (threads_per_env != 0 && (threads_per_env < 32 || threads_per_env > 256 || threads_per_env % 32 != 0))
         return fail(ctx, JWF_EINVAL, "jwf_set_kernel: threads_per_env must be 0 or a multiple of 32 in [32, 256]");

@@ -106,6 +106,18 @@ struct jwf_ctx {
     const float* t_ws = nullptr;
     const float* t_wd = nullptr;
     bool have_terrain = false;
+    // tiled path: (env, tile row, tile column) per tile, per-env tile layout,
+    // per-tile activity (ping-pong), buffers-in-sync flags, burned counts,
+    // and the per-round count scratch [16][2][N]
+    int4* d_tiles4 = nullptr;
+    int4* d_env_tiles = nullptr;
+    int64_t n_tiles4 = 0;
+    uint8_t* d_tact[2] = {nullptr, nullptr};
+    int tact_cur = 0;
+    uint8_t* d_tsync = nullptr;
+    int32_t* d_tburnt = nullptr;
+    int32_t* d_tcnt = nullptr;
+    bool tiles_valid = false;
     bool wexp_stale = true;              // parameters changed since d_wexp was built
 
     JwfDevParams P{};
@@ -137,6 +149,10 @@ cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, i
 cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops,
                                      int32_t* burning, int32_t* burnt, uint8_t* done,
                                      cudaStream_t s);
+cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
+                                  int32_t* burnt, uint8_t* done, bool fused, cudaStream_t s);
+int jwf_tile_rows();
+int jwf_tile_cols();
 // shared memory a resident launch needs for env shape (H, W) with `threads`
 size_t jwf_resident_smem(int32_t H, int32_t W, int threads);
 int jwf_resident_threads(int32_t H, int32_t W);

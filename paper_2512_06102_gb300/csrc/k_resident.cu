@@ -49,7 +49,8 @@ struct ResArgs {
     int32_t* out_burnt;
     uint8_t* out_done;
     uint32_t* queue;            // [0] cursor, [1] CTAs finished
-    unsigned long long* pairs;  // optional: count of (target, source) pairs compared
+    unsigned long long* counts; // optional [4]: pairs compared, candidate Philox blocks,
+                                // burning-cell draws, bit-plane word-steps scanned
     int32_t k;
     int32_t t_max;
     int32_t R;
@@ -161,11 +162,31 @@ __device__ void res_action(int H, int W, int WW, uint32_t* Bp, uint32_t* D, int 
     }
 }
 
+// Chunk activity after a (re)load: flag[c] = chunk c of B holds a burning
+// cell; the other buffer's flags get `other` (0 after zeroing, 1 when it may
+// hold stale words).  Adds popc(D) to *burnt.  All threads; caller syncs.
+__device__ void res_init_flags(const uint32_t* Bp, const uint32_t* D, int WW, int words, int nchunks,
+                               uint8_t* fl_cur, uint8_t* fl_other, uint8_t other, int* burnt) {
+    int nd = 0;
+    for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
+        uint32_t any = 0u;
+        const int i1 = min(words, (c + 1) << 5);
+        for (int i = c << 5; i < i1; ++i) {
+            any |= Bp[WW + i];
+            nd += __popc(D[i]);
+        }
+        fl_cur[c] = any != 0u;
+        fl_other[c] = other;
+    }
+    atomicAdd(burnt, nd);
+}
+
 // Table variant: does can-burn cell `cell` ignite this step?  dm: bit d set
 // when its source in direction d burns.  Draws: slot 0 words -> d 0..3, slot 1
 // words -> d 4..7; success iff u < q.  Any success ignites, so the second half
 // is skipped once the first has succeeded.
-__device__ __forceinline__ bool ignites(const ResArgs& a, int e, int64_t off, uint32_t cell, uint32_t dm,
+template <class Args>
+__device__ __forceinline__ bool ignites(const Args& a, int e, int64_t off, uint32_t cell, uint32_t dm,
                                         uint32_t tt, uint32_t ep4) {
     const float4* q4 = reinterpret_cast<const float4*>(a.q + (off + cell) * 8);
     bool ign = false;
@@ -188,10 +209,13 @@ __device__ __forceinline__ bool ignites(const ResArgs& a, int e, int64_t off, ui
 // into (cell, direction) pairs, one pair per lane per round, so the rate code
 // of Eqs. 1-4 runs once per pair rather than once per direction present in
 // any lane.  A success sets the cell's bit in ignw.
-__device__ __forceinline__ void fused_pairs(const ResArgs& a, const RateConsts& K, const uint32_t* list,
+// (oy, ox): grid coordinates of word 0, bit 0 of the planes (0, 0 for a
+// whole env; the region origin for a tile).
+template <class Args>
+__device__ __forceinline__ void fused_pairs(const Args& a, const RateConsts& K, const uint32_t* list,
                                             uint32_t* plist, uint32_t* ignw, int it0, int n_pass, int base,
-                                            int e, int64_t off, int W, int WW, uint32_t tt, uint32_t ep4,
-                                            int lane) {
+                                            int e, int64_t off, int W, int WW, int oy, int ox, uint32_t tt,
+                                            uint32_t ep4, int lane) {
     const int it = it0 + lane;
     const uint32_t item = it < n_pass ? list[it] : 0u;
     const uint32_t dm = (item & (1u << 18)) ? (item >> 10) & 0xFFu : 0u;
@@ -213,8 +237,9 @@ __device__ __forceinline__ void fused_pairs(const ResArgs& a, const RateConsts& 
         const int ol = (int)(itm >> 5) & 31;
         const int j = (int)itm & 31;
         const int ii = base + ol;
-        const int yy = ii / WW;
-        const int xx = ((ii - yy * WW) << 5) + j;
+        const int ry = ii / WW;
+        const int yy = oy + ry;
+        const int xx = ox + ((ii - ry * WW) << 5) + j;
         const uint32_t cell = (uint32_t)(yy * W + xx);
         const int64_t v = off + cell;
         const int64_t u = off + (int64_t)(yy - jwf_dr(d)) * W + (xx - jwf_dx(d));
@@ -234,8 +259,9 @@ __global__ void __launch_bounds__(NT)
 k_step_resident(const ResArgs a, const RateConsts Kc) {
     extern __shared__ uint32_t sm[];
     __shared__ int32_t s_env;
-    __shared__ int32_t s_cnt[3][2];
+    __shared__ int32_t s_cnt[3][3];     // burning, new burn-outs, doused (per step)
     __shared__ int32_t s_chunk[3];
+    __shared__ int32_t s_burnt;
     // the rate constants live in shared memory only in the fused variant
     __shared__ typename std::conditional<FUSED, RateConsts, int>::type sK_store;
     const RateConsts& sK = *reinterpret_cast<const RateConsts*>(&sK_store);
@@ -268,14 +294,19 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         uint32_t* ignw = list + kListCap;
         uint32_t* outw = ignw + 32;
         uint32_t* plist = outw + 32;
+        // chunk activity flags of the two burning buffers
+        uint8_t* flag0 = reinterpret_cast<uint8_t*>(D + words + (NT / 32) * kWarpScratch);
+        uint8_t* flag1 = flag0 + nchunks;
+        const int reach = (WW + 1 + 31) >> 5;                 // chunks a word's neighbours span
         const int64_t off = a.off[e];
         uint8_t* Fe = a.F + off;
         const bool vec = ((W & 31) == 0) && ((off & 15) == 0);
 
         // zero both burning planes (the padding rows must read as 0), then load
         for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
-        if (threadIdx.x < 6) s_cnt[threadIdx.x / 2][threadIdx.x & 1] = 0;
+        if (threadIdx.x < 9) s_cnt[threadIdx.x / 3][threadIdx.x % 3] = 0;
         if (threadIdx.x < 3) s_chunk[threadIdx.x] = 0;
+        if (threadIdx.x == 0) s_burnt = 0;
         ignw[lane] = 0u;
         outw[lane] = 0u;
         __syncthreads();
@@ -285,6 +316,11 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
             res_action(H, W, WW, B0, D, a.drops[(int64_t)e * 2], a.drops[(int64_t)e * 2 + 1], a.R);
             __syncthreads();
         }
+        res_init_flags(B0, D, WW, words, nchunks, flag0, flag1, 0, &s_burnt);
+        __syncthreads();
+        int32_t burnt_now = s_burnt;
+        uint8_t* fl_c = flag0;
+        uint8_t* fl_n = flag1;
 
         int32_t t = a.t[e];
         int32_t ep = a.episode[e];
@@ -297,6 +333,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
             if (threadIdx.x == 0) {
                 s_cnt[(s + 1) % 3][0] = 0;
                 s_cnt[(s + 1) % 3][1] = 0;
+                s_cnt[(s + 1) % 3][2] = 0;
                 s_chunk[(s + 1) % 3] = 0;
             }
             // the next step's drop is applied while the new planes are written
@@ -305,13 +342,20 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 cxn = a.drops[((int64_t)(s + 1) * a.N + e) * 2];
                 cyn = a.drops[((int64_t)(s + 1) * a.N + e) * 2 + 1];
             }
-            int my_b = 0, my_d = 0;
-            uint32_t my_pairs = 0;
+            int my_b = 0, my_o = 0, my_x = 0;
+            uint32_t my_pairs = 0, my_blocks = 0, my_burn = 0, my_chunks = 0;
             for (;;) {
                 int c = 0;
                 if (lane == 0) c = atomicAdd(&s_chunk[s % 3], 1);
                 c = __shfl_sync(0xffffffffu, c, 0);
                 if (c >= nchunks) break;
+                // a chunk with no burning cell within reach, whose write buffer
+                // holds no burning word, cannot change: skip it
+                bool need = fl_n[c] != 0;
+                for (int cc = max(c - reach, 0); cc <= min(c + reach, nchunks - 1) && !need; ++cc)
+                    need = fl_c[cc] != 0;
+                if (!need) continue;
+                ++my_chunks;
                 const int base = c << 5;
                 const int i = base + lane;
                 uint32_t burn = 0, cand = 0;
@@ -384,55 +428,73 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                             if (item & (1u << 18)) {
                                 const uint32_t dm = (item >> 10) & 0xFFu;
                                 my_pairs += __popc(dm);
+                                my_blocks += ((dm & 0x0Fu) ? 1u : 0u) + ((dm & 0xF0u) ? 1u : 0u);
                                 if (!FUSED && ignites(a, e, off, cell, dm, tt, ep4))
                                     atomicOr(&ignw[ol], 1u << j);
                             } else {
+                                ++my_burn;
                                 const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
                                 if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&outw[ol], 1u << j);
                             }
                         }
                         if (FUSED) {
                             for (int it0 = 0; it0 < n_pass; it0 += 32)
-                                fused_pairs(a, sK, list, plist, ignw, it0, n_pass, base, e, off, W, WW, tt, ep4,
-                                            lane);
+                                fused_pairs(a, sK, list, plist, ignw, it0, n_pass, base, e, off, W, WW, 0, 0, tt,
+                                            ep4, lane);
                         }
                         __syncwarp();
                     }
                 }
+                uint32_t nb = 0u;
                 if (i < words) {
                     const uint32_t ig = ignw[lane], ou = outw[lane];
-                    uint32_t nb = (burn & ~ou) | ig;
-                    uint32_t nd = D[i] | ou;
+                    nb = (burn & ~ou) | ig;
                     my_b += __popc(nb);
-                    my_d += __popc(nd);
+                    my_o += __popc(ou);
                     const uint32_t m = drop_bits(y, w, W, cxn, cyn, a.R);
-                    nd |= nb & m;
+                    const uint32_t doused = nb & m;
+                    my_x += __popc(doused);
                     nb &= ~m;
                     Bn[WW + i] = nb;
-                    D[i] = nd;
+                    D[i] |= ou | doused;
                     C[i] &= ~ig;
                     ignw[lane] = 0u;
                     outw[lane] = 0u;
                 }
+                const uint32_t any_nb = __ballot_sync(0xffffffffu, nb != 0u);
+                if (lane == 0) fl_n[c] = any_nb != 0u;
                 __syncwarp();
             }
             // counts of this step (before the next drop), one barrier
-            if (a.pairs != nullptr) {
+            if (a.counts != nullptr) {
                 my_pairs = __reduce_add_sync(0xffffffffu, my_pairs);
-                if (lane == 0 && my_pairs) atomicAdd(a.pairs, (unsigned long long)my_pairs);
+                my_blocks = __reduce_add_sync(0xffffffffu, my_blocks);
+                my_burn = __reduce_add_sync(0xffffffffu, my_burn);
+                if (lane == 0) {
+                    atomicAdd(&a.counts[0], (unsigned long long)my_pairs);
+                    atomicAdd(&a.counts[1], (unsigned long long)my_blocks);
+                    atomicAdd(&a.counts[2], (unsigned long long)my_burn);
+                }
+                if (lane == 0 && my_chunks) atomicAdd(&a.counts[3], 32ull * my_chunks);
             }
             my_b = __reduce_add_sync(0xffffffffu, my_b);
-            my_d = __reduce_add_sync(0xffffffffu, my_d);
+            my_o = __reduce_add_sync(0xffffffffu, my_o);
+            my_x = __reduce_add_sync(0xffffffffu, my_x);
             if (lane == 0) {
                 atomicAdd(&s_cnt[s % 3][0], my_b);
-                atomicAdd(&s_cnt[s % 3][1], my_d);
+                atomicAdd(&s_cnt[s % 3][1], my_o);
+                atomicAdd(&s_cnt[s % 3][2], my_x);
             }
             __syncthreads();
             const int32_t nb = s_cnt[s % 3][0];
-            const int32_t nd = s_cnt[s % 3][1];
+            const int32_t nd = burnt_now + s_cnt[s % 3][1];      // burned after the step
+            burnt_now = nd + s_cnt[s % 3][2];                   // and after the next drop
             uint32_t* tmp = Bc;
             Bc = Bn;
             Bn = tmp;
+            uint8_t* ftmp = fl_c;
+            fl_c = fl_n;
+            fl_n = ftmp;
             t += 1;
             const bool done = (nb == 0) || (a.t_max > 0 && t >= a.t_max);
             if (threadIdx.x == 0) {
@@ -447,6 +509,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 t = 0;
                 ep += 1;
                 for (int i2 = threadIdx.x; i2 < pw; i2 += NT) Bc[i2] = 0u;
+                if (threadIdx.x == 0) s_burnt = 0;
                 __syncthreads();
                 res_load(a.F0 + off, H, W, WW, vec, Bc, C, D);
                 __syncthreads();
@@ -454,6 +517,10 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                     res_action(H, W, WW, Bc, D, cxn, cyn, a.R);
                     __syncthreads();
                 }
+                // the other buffer may hold stale burning words: mark it active
+                res_init_flags(Bc, D, WW, words, nchunks, fl_c, fl_n, 1, &s_burnt);
+                __syncthreads();
+                burnt_now = s_burnt;
                 continue;
             }
             if (nb == 0) {
@@ -486,6 +553,420 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
             __threadfence();
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled, temporally blocked step for grids that do not fit shared memory.
+//
+// One CTA per tile of up to kTileRows x kTileCols interior cells and one
+// launch per round of kb <= kMaxRound steps.  The CTA loads the tile with a
+// halo of kb rows and one 32-cell word of columns on each side (cells outside
+// the grid read as no fuel), runs kb steps over the whole region (halo cells
+// are recomputed redundantly; after s steps the outer s cells of the region
+// are stale, never the interior), then writes the interior to the other state
+// buffer.  A tile none of whose 3x3 neighbour tiles held a burning cell after
+// the previous round cannot change this round: it copies its interior to the
+// other buffer once and otherwise only reports its counts.
+// ---------------------------------------------------------------------------
+constexpr int kTileRows = 128, kTileCols = 256, kMaxRound = 16;
+constexpr int kRegionRows = kTileRows + 2 * kMaxRound;
+constexpr int kRegionWords = kTileCols / 32 + 2;
+
+struct TileArgs {
+    const int32_t* H;
+    const int32_t* W;
+    const int64_t* off;
+    const int4* tiles;           // (env, tile row, tile column, 0)
+    const int4* env_tiles;       // per env: (first tile, tiles per row, tile rows, 0)
+    int32_t N;
+    const uint8_t* Fin;
+    uint8_t* Fout;
+    const float* q;
+    const uint8_t* cls;
+    const float* dem;
+    const float2* wexp;
+    const int32_t* drops;        // [kb][N][2] of this round, or null
+    const int32_t* t;            // step counters at the start of the round
+    const int32_t* episode;
+    int32_t* cnt;                // [kb][2][N] per-step counts (zeroed before the round)
+    const uint8_t* act_in;       // [tiles] a burning interior cell after the last round
+    uint8_t* act_out;
+    uint8_t* synced;             // [tiles] both buffers hold this tile's interior
+    int32_t* tile_burnt;         // [tiles] burned interior cells after the last round
+    unsigned long long* counts;
+    int32_t kb;
+    int32_t R;
+    uint32_t key0, key1;
+    float p_continue;
+};
+
+size_t tiled_smem_bytes(int threads) {
+    return (size_t)(2 * (kRegionRows + 2) * kRegionWords + 2 * kRegionRows * kRegionWords +
+                    (threads / 32) * kWarpScratch) * sizeof(uint32_t);
+}
+
+// Region-relative drops: the centre (cx, cy) may lie outside the region (even
+// at negative coordinates) while its footprint reaches in; `has` is false for
+// a step without a drop.
+__device__ __forceinline__ uint32_t drop_bits_rel(int y, int w, int cx, int cy, int R, bool has) {
+    if (!has || abs(y - cy) > R) return 0u;
+    const int lo = max(cx - R - (w << 5), 0), hi = min(cx + R - (w << 5), 31);
+    if (lo > hi) return 0u;
+    const uint32_t span = (hi - lo == 31) ? 0xffffffffu : ((1u << (hi - lo + 1)) - 1u);
+    return span << lo;
+}
+
+__device__ void res_action_rel(int RH, int WW, uint32_t* Bp, uint32_t* D, int cx, int cy, int R, bool has) {
+    if (!has) return;
+    const int y0 = max(cy - R, 0), y1 = min(cy + R, RH - 1);
+    const int x0 = max(cx - R, 0), x1 = min(cx + R, (WW << 5) - 1);
+    if (y0 > y1 || x0 > x1) return;
+    const int w0 = x0 >> 5, w1 = x1 >> 5;
+    const int nw = w1 - w0 + 1;
+    const int total = (y1 - y0 + 1) * nw;
+    for (int j = threadIdx.x; j < total; j += blockDim.x) {
+        const int y = y0 + j / nw, w = w0 + j % nw;
+        const uint32_t m = drop_bits_rel(y, w, cx, cy, R, true);
+        uint32_t* bp = &Bp[(y + 1) * WW + w];
+        const uint32_t doused = *bp & m;
+        *bp &= ~m;
+        D[y * WW + w] |= doused;
+    }
+}
+
+// bits of region word w inside the column range [c0, c1) of the region
+__device__ __forceinline__ uint32_t col_bits(int w, int c0, int c1) {
+    const int lo = max(c0 - (w << 5), 0), hi = min(c1 - (w << 5), 32) - 1;
+    if (lo > hi) return 0u;
+    const uint32_t span = (hi - lo == 31) ? 0xffffffffu : ((1u << (hi - lo + 1)) - 1u);
+    return span << lo;
+}
+
+template <int NT, bool FUSED>
+__global__ void __launch_bounds__(NT)
+k_step_tiled(const TileArgs a, const RateConsts Kc) {
+    extern __shared__ uint32_t sm[];
+    __shared__ int32_t s_cnt[3][3];     // interior burning, interior burned, region burning
+    __shared__ int32_t s_chunk[3];
+    __shared__ int s_active;
+    __shared__ typename std::conditional<FUSED, RateConsts, int>::type sK_store;
+    const RateConsts& sK = *reinterpret_cast<const RateConsts*>(&sK_store);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tix = blockIdx.x;
+    const int4 tl = a.tiles[tix];
+    const int e = tl.x, tr = tl.y, tc = tl.z;
+    const int H = a.H[e], W = a.W[e];
+    const int64_t off = a.off[e];
+    const int4 et = a.env_tiles[e];
+    const int ty0 = tr * kTileRows, tx0 = tc * kTileCols;
+    const int TY = min(kTileRows, H - ty0), TX = min(kTileCols, W - tx0);
+    const int kb = a.kb;
+    if (threadIdx.x == 0) {
+        int act = 0;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int r = tr + dy, c = tc + dx;
+                if (r >= 0 && r < et.z && c >= 0 && c < et.y) act |= a.act_in[et.x + r * et.y + c];
+            }
+        s_active = act;
+    }
+    __syncthreads();
+    if (!s_active) {
+        // no fire within reach: the interior stays as it is this round
+        if (!a.synced[tix]) {
+            for (int i = threadIdx.x; i < TY * TX; i += NT) {
+                const int64_t g = off + (int64_t)(ty0 + i / TX) * W + tx0 + i % TX;
+                a.Fout[g] = a.Fin[g];
+            }
+        }
+        if ((int)threadIdx.x < kb) atomicAdd(&a.cnt[((int64_t)threadIdx.x * 2 + 1) * a.N + e], a.tile_burnt[tix]);
+        if (threadIdx.x == 0) {
+            a.act_out[tix] = 0;
+            a.synced[tix] = 1;
+        }
+        return;
+    }
+    if (FUSED) {
+        for (int i = threadIdx.x; i < (int)(sizeof(RateConsts) / 4); i += NT)
+            reinterpret_cast<float*>(&sK_store)[i] = reinterpret_cast<const float*>(&Kc)[i];
+    }
+    // region: rows [ty0 - kb, ty0 + TY + kb), columns [tx0 - 32, tx0 + TX + 32)
+    const int oy = ty0 - kb, ox = tx0 - 32;
+    const int RH = TY + 2 * kb;
+    const int WW = (TX + 64 + 31) >> 5;
+    const int pw = (RH + 2) * WW;
+    const int words = RH * WW;
+    const int nchunks = (words + 31) >> 5;
+    uint32_t* B0 = sm;
+    uint32_t* B1 = B0 + pw;
+    uint32_t* C = B1 + pw;
+    uint32_t* D = C + words;
+    uint32_t* list = D + words + warp * kWarpScratch;
+    uint32_t* ignw = list + kListCap;
+    uint32_t* outw = ignw + 32;
+    uint32_t* plist = outw + 32;
+    for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
+    if (threadIdx.x < 9) s_cnt[threadIdx.x / 3][threadIdx.x % 3] = 0;
+    if (threadIdx.x < 3) s_chunk[threadIdx.x] = 0;
+    ignw[lane] = 0u;
+    outw[lane] = 0u;
+    __syncthreads();
+    // load the region (cells outside the grid read as no fuel)
+    for (int i = threadIdx.x; i < words; i += NT) {
+        const int ry = i / WW, w = i - (i / WW) * WW;
+        const int gy = oy + ry, gx0 = ox + (w << 5);
+        uint32_t b = 0, c = 0, dd = 0;
+        if (gy >= 0 && gy < H) {
+            const uint8_t* src = a.Fin + off + (int64_t)gy * W + gx0;
+            if (gx0 >= 0 && gx0 + 32 <= W && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+                const uint4 lo = __ldg(reinterpret_cast<const uint4*>(src));
+                const uint4 hi = __ldg(reinterpret_cast<const uint4*>(src) + 1);
+                const uint32_t v8[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    c |= nib_eq(v8[k], 0x01010101u) << (4 * k);
+                    b |= nib_eq(v8[k], 0x02020202u) << (4 * k);
+                    dd |= nib_eq(v8[k], 0x03030303u) << (4 * k);
+                }
+            } else {
+                for (int j = 0; j < 32; ++j) {
+                    const int gx = gx0 + j;
+                    if (gx < 0 || gx >= W) continue;
+                    const uint32_t st = src[j];
+                    b |= (uint32_t)(st == 2) << j;
+                    c |= (uint32_t)(st == 1) << j;
+                    dd |= (uint32_t)(st == 3) << j;
+                }
+            }
+        }
+        B0[(ry + 1) * WW + w] = b;
+        C[i] = c;
+        D[i] = dd;
+    }
+    __syncthreads();
+    if (a.drops != nullptr) {
+        const int gcx = a.drops[(int64_t)e * 2], gcy = a.drops[(int64_t)e * 2 + 1];
+        res_action_rel(RH, WW, B0, D, gcx - ox, gcy - oy, a.R, gcx >= 0 && gcy >= 0);
+        __syncthreads();
+    }
+    int32_t t0 = a.t[e];
+    const uint32_t ep4 = 4u * (uint32_t)a.episode[e];
+    uint32_t* Bc = B0;
+    uint32_t* Bn = B1;
+    int32_t fin_b = 0, fin_d = 0;
+    for (int s = 0; s < kb; ++s) {
+        const uint32_t tt = (uint32_t)(t0 + s);
+        if (threadIdx.x == 0) {
+            s_cnt[(s + 1) % 3][0] = 0;
+            s_cnt[(s + 1) % 3][1] = 0;
+            s_cnt[(s + 1) % 3][2] = 0;
+            s_chunk[(s + 1) % 3] = 0;
+        }
+        bool hasn = false;
+        int cxn = 0, cyn = 0;
+        if (a.drops != nullptr && s + 1 < kb) {
+            const int gcx = a.drops[((int64_t)(s + 1) * a.N + e) * 2];
+            const int gcy = a.drops[((int64_t)(s + 1) * a.N + e) * 2 + 1];
+            hasn = gcx >= 0 && gcy >= 0;
+            cxn = gcx - ox;
+            cyn = gcy - oy;
+        }
+        int my_b = 0, my_d = 0, my_r = 0;
+        uint32_t my_pairs = 0, my_blocks = 0, my_burn = 0;
+        for (;;) {
+            int c = 0;
+            if (lane == 0) c = atomicAdd(&s_chunk[s % 3], 1);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= nchunks) break;
+            const int base = c << 5;
+            const int i = base + lane;
+            uint32_t burn = 0, cand = 0;
+            uint32_t sd[8];
+            int y = 0, w = 0;
+            if (i < words) {
+                y = i / WW;
+                w = i - y * WW;
+                const uint32_t* bp = &Bc[WW + i];
+                const bool hl = w > 0, hr = w + 1 < WW;
+                const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
+                const uint32_t uc = bp[-WW], ul = hl ? bp[-WW - 1] : 0u, ur = hr ? bp[-WW + 1] : 0u;
+                const uint32_t dc = bp[WW], dl = hl ? bp[WW - 1] : 0u, dr = hr ? bp[WW + 1] : 0u;
+                sd[0] = (bc << 1) | (bl >> 31);
+                sd[1] = (dc << 1) | (dl >> 31);
+                sd[2] = dc;
+                sd[3] = (dc >> 1) | (dr << 31);
+                sd[4] = (bc >> 1) | (br << 31);
+                sd[5] = (uc >> 1) | (ur << 31);
+                sd[6] = uc;
+                sd[7] = (uc << 1) | (ul >> 31);
+                const uint32_t any = sd[0] | sd[1] | sd[2] | sd[3] | sd[4] | sd[5] | sd[6] | sd[7];
+                cand = C[i] & any;
+                burn = bc;
+            } else {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) sd[d] = 0u;
+            }
+            const uint32_t act = cand | burn;
+            if (__ballot_sync(0xffffffffu, act != 0u) != 0u) {
+                const int n_act = __popc(act);
+                int incl = n_act;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                const int excl = incl - n_act;
+                for (int pass = 0; pass < total; pass += kListCap) {
+                    uint32_t rem = act;
+                    int idx = excl;
+                    while (rem != 0u) {
+                        const int j = __ffs(rem) - 1;
+                        rem &= rem - 1u;
+                        if (idx >= pass && idx < pass + kListCap) {
+                            uint32_t item = ((uint32_t)lane << 5) | (uint32_t)j;
+                            if ((cand >> j) & 1u) {
+                                uint32_t dm = 0;
+#pragma unroll
+                                for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
+                                item |= (dm << 10) | (1u << 18);
+                            }
+                            list[idx - pass] = item;
+                        }
+                        ++idx;
+                    }
+                    __syncwarp();
+                    const int n_pass = min(kListCap, total - pass);
+                    for (int it = lane; it < n_pass; it += 32) {
+                        const uint32_t item = list[it];
+                        const int ol = (int)(item >> 5) & 31;
+                        const int j = (int)item & 31;
+                        const int ii = base + ol;
+                        const int ry = ii / WW;
+                        const int gy = oy + ry, gx = ox + ((ii - ry * WW) << 5) + j;
+                        const uint32_t cell = (uint32_t)(gy * W + gx);
+                        if (item & (1u << 18)) {
+                            const uint32_t dm = (item >> 10) & 0xFFu;
+                            my_pairs += __popc(dm);
+                            my_blocks += ((dm & 0x0Fu) ? 1u : 0u) + ((dm & 0xF0u) ? 1u : 0u);
+                            if (!FUSED && ignites(a, e, off, cell, dm, tt, ep4))
+                                atomicOr(&ignw[ol], 1u << j);
+                        } else {
+                            ++my_burn;
+                            const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
+                            if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&outw[ol], 1u << j);
+                        }
+                    }
+                    if (FUSED) {
+                        for (int it0 = 0; it0 < n_pass; it0 += 32)
+                            fused_pairs(a, sK, list, plist, ignw, it0, n_pass, base, e, off, W, WW, oy, ox, tt,
+                                        ep4, lane);
+                    }
+                    __syncwarp();
+                }
+            }
+            if (i < words) {
+                const uint32_t ig = ignw[lane], ou = outw[lane];
+                uint32_t nb = (burn & ~ou) | ig;
+                uint32_t nd = D[i] | ou;
+                const uint32_t im = (y >= kb && y < kb + TY) ? col_bits(w, 32, 32 + TX) : 0u;
+                my_r += __popc(nb);
+                my_b += __popc(nb & im);
+                my_d += __popc(nd & im);
+                const uint32_t m = drop_bits_rel(y, w, cxn, cyn, a.R, hasn);
+                nd |= nb & m;
+                nb &= ~m;
+                Bn[WW + i] = nb;
+                D[i] = nd;
+                C[i] &= ~ig;
+                ignw[lane] = 0u;
+                outw[lane] = 0u;
+            }
+            __syncwarp();
+        }
+        if (a.counts != nullptr) {
+            my_pairs = __reduce_add_sync(0xffffffffu, my_pairs);
+            my_blocks = __reduce_add_sync(0xffffffffu, my_blocks);
+            my_burn = __reduce_add_sync(0xffffffffu, my_burn);
+            if (lane == 0) {
+                atomicAdd(&a.counts[0], (unsigned long long)my_pairs);
+                atomicAdd(&a.counts[1], (unsigned long long)my_blocks);
+                atomicAdd(&a.counts[2], (unsigned long long)my_burn);
+            }
+            if (threadIdx.x == 0) atomicAdd(&a.counts[3], (unsigned long long)words);
+        }
+        my_b = __reduce_add_sync(0xffffffffu, my_b);
+        my_d = __reduce_add_sync(0xffffffffu, my_d);
+        my_r = __reduce_add_sync(0xffffffffu, my_r);
+        if (lane == 0) {
+            atomicAdd(&s_cnt[s % 3][0], my_b);
+            atomicAdd(&s_cnt[s % 3][1], my_d);
+            atomicAdd(&s_cnt[s % 3][2], my_r);
+        }
+        __syncthreads();
+        fin_b = s_cnt[s % 3][0];
+        fin_d = s_cnt[s % 3][1];
+        const int32_t nr = s_cnt[s % 3][2];
+        if (threadIdx.x == 0) {
+            if (fin_b) atomicAdd(&a.cnt[((int64_t)s * 2) * a.N + e], fin_b);
+            if (fin_d) atomicAdd(&a.cnt[((int64_t)s * 2 + 1) * a.N + e], fin_d);
+        }
+        uint32_t* tmp = Bc;
+        Bc = Bn;
+        Bn = tmp;
+        if (nr == 0) {
+            // no fire left in the region: the remaining steps change nothing
+            for (int s2 = s + 1 + (int)threadIdx.x; s2 < kb; s2 += NT)
+                if (fin_d) atomicAdd(&a.cnt[((int64_t)s2 * 2 + 1) * a.N + e], fin_d);
+            break;
+        }
+    }
+    __syncthreads();
+    // write the interior back to the other buffer
+    const int iwords = (TX + 31) >> 5;
+    for (int i = threadIdx.x; i < TY * iwords; i += NT) {
+        const int ry = kb + i / iwords, w = 1 + i % iwords;
+        const int gy = oy + ry, gx0 = ox + (w << 5);
+        uint8_t* dst = a.Fout + off + (int64_t)gy * W + gx0;
+        const uint32_t b = Bc[(ry + 1) * WW + w], c = C[ry * WW + w], dd = D[ry * WW + w];
+        const int n = min(32, tx0 + TX - gx0);
+        if (n == 32 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+            uint32_t v8[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int sh = 4 * k;
+                v8[k] = nib_spread((c >> sh) & 0xFu) + 2u * nib_spread((b >> sh) & 0xFu) +
+                        3u * nib_spread((dd >> sh) & 0xFu);
+            }
+            reinterpret_cast<uint4*>(dst)[0] = make_uint4(v8[0], v8[1], v8[2], v8[3]);
+            reinterpret_cast<uint4*>(dst)[1] = make_uint4(v8[4], v8[5], v8[6], v8[7]);
+        } else {
+            for (int j = 0; j < n; ++j)
+                dst[j] = (uint8_t)(((c >> j) & 1u) + ((b >> j) & 1u) * 2u + ((dd >> j) & 1u) * 3u);
+        }
+    }
+    if (threadIdx.x == 0) {
+        a.tile_burnt[tix] = fin_d;
+        a.act_out[tix] = fin_b > 0 ? 1 : 0;
+        a.synced[tix] = 0;
+    }
+}
+
+// After a round: per-step outputs, done flags and t += kb, one thread per env.
+__global__ void k_round_finalize(int32_t N, int32_t kb, const int32_t* __restrict__ cnt, int32_t* __restrict__ t,
+                                 int32_t t_max, int32_t* __restrict__ burning, int32_t* __restrict__ burnt,
+                                 uint8_t* __restrict__ done) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int32_t t0 = t[e];
+    for (int s = 0; s < kb; ++s) {
+        const int32_t nb = cnt[((int64_t)s * 2) * N + e], nd = cnt[((int64_t)s * 2 + 1) * N + e];
+        const int64_t o = (int64_t)s * N + e;
+        if (burning) burning[o] = nb;
+        if (burnt) burnt[o] = nd;
+        if (done) done[o] = (nb == 0 || (t_max > 0 && t0 + s + 1 >= t_max)) ? 1 : 0;
+    }
+    t[e] = t0 + kb;
 }
 
 constexpr int kMaxDev = 64;
@@ -531,13 +1012,94 @@ cudaError_t launch_v(const jwf_ctx* c, int threads, const ResArgs& a, const Rate
     }
 }
 
+template <int NT, bool FUSED>
+cudaError_t launch_tiled_t(const jwf_ctx* c, const TileArgs& a, const RateConsts& K, cudaStream_t s) {
+    static size_t set_smem[kMaxDev] = {};
+    const size_t smem = tiled_smem_bytes(NT);
+    const int dev = c->device;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    if (smem > set_smem[dev]) {
+        const cudaError_t err = cudaFuncSetAttribute(k_step_tiled<NT, FUSED>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        set_smem[dev] = smem;
+    }
+    k_step_tiled<NT, FUSED><<<(unsigned)c->n_tiles4, NT, smem, s>>>(a, K);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 void jwf_rate_consts(const jwf_ctx* c, RateConsts* K);
 
+int jwf_tile_rows() { return kTileRows; }
+int jwf_tile_cols() { return kTileCols; }
+
+cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
+                                  int32_t* burnt, uint8_t* done, bool fused, cudaStream_t s) {
+    cudaError_t err;
+    if (!c->tiles_valid) {
+        // the state changed outside the tiled path: every tile may be active
+        err = cudaMemsetAsync(c->d_tact[c->tact_cur], 1, (size_t)c->n_tiles4, s);
+        if (err == cudaSuccess) err = cudaMemsetAsync(c->d_tsync, 0, (size_t)c->n_tiles4, s);
+        if (err != cudaSuccess) return err;
+        c->tiles_valid = true;
+    }
+    RateConsts K;
+    if (fused)
+        jwf_rate_consts(c, &K);
+    else
+        K = RateConsts{};
+    for (int32_t s0 = 0; s0 < k; s0 += kMaxRound) {
+        const int32_t kb = (k - s0) < kMaxRound ? (k - s0) : kMaxRound;
+        err = cudaMemsetAsync(c->d_tcnt, 0, (size_t)kb * 2 * c->N * sizeof(int32_t), s);
+        if (err != cudaSuccess) return err;
+        TileArgs a;
+        a.H = c->d_H;
+        a.W = c->d_W;
+        a.off = c->d_off;
+        a.tiles = c->d_tiles4;
+        a.env_tiles = c->d_env_tiles;
+        a.N = c->N;
+        a.Fin = c->d_state[c->cur];
+        a.Fout = c->d_state[c->cur ^ 1];
+        a.q = c->d_q;
+        a.cls = c->t_cls;
+        a.dem = c->t_dem;
+        a.wexp = c->d_wexp;
+        a.drops = drops ? drops + (int64_t)s0 * c->N * 2 : nullptr;
+        a.t = c->d_t;
+        a.episode = c->d_episode;
+        a.cnt = c->d_tcnt;
+        a.act_in = c->d_tact[c->tact_cur];
+        a.act_out = c->d_tact[c->tact_cur ^ 1];
+        a.synced = c->d_tsync;
+        a.tile_burnt = c->d_tburnt;
+        a.counts = c->d_pairs;
+        a.kb = kb;
+        a.R = c->drop_radius;
+        a.key0 = (uint32_t)(c->seed & 0xffffffffu);
+        a.key1 = (uint32_t)(c->seed >> 32);
+        a.p_continue = c->P.p_continue;
+        err = fused ? launch_tiled_t<256, true>(c, a, K, s) : launch_tiled_t<256, false>(c, a, K, s);
+        if (err != cudaSuccess) return err;
+        const int64_t o = (int64_t)s0 * c->N;
+        k_round_finalize<<<(c->N + 255) / 256, 256, 0, s>>>(c->N, kb, c->d_tcnt, c->d_t, c->t_max,
+                                                             burning ? burning + o : nullptr,
+                                                             burnt ? burnt + o : nullptr, done ? done + o : nullptr);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        c->cur ^= 1;
+        c->tact_cur ^= 1;
+    }
+    return cudaSuccess;
+}
+
 size_t jwf_resident_smem(int32_t H, int32_t W, int threads) {
     const int nwarps = threads / 32;
-    return (size_t)(res_plane_words(H, W) + nwarps * kWarpScratch) * sizeof(uint32_t);
+    const int64_t nchunks = ((int64_t)H * ((W + 31) / 32) + 31) / 32;
+    const int64_t flag_words = (2 * nchunks + 3) / 4;
+    return (size_t)(res_plane_words(H, W) + nwarps * kWarpScratch + flag_words) * sizeof(uint32_t);
 }
 
 int jwf_resident_threads(int32_t H, int32_t W) {
@@ -573,7 +1135,7 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
     a.out_burnt = burnt;
     a.out_done = done;
     a.queue = c->d_queue;
-    a.pairs = c->d_pairs;
+    a.counts = c->d_pairs;
     a.k = k;
     a.t_max = c->t_max;
     a.R = c->drop_radius;

@@ -21,7 +21,7 @@ JWF_AUTO_RESET = 0x1
 JWF_WIND_PER_CELL = 0x2
 JWF_KEEP_RATES = 0x4
 
-KERNEL_AUTO, KERNEL_PLAIN, KERNEL_RESIDENT, KERNEL_FUSED = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_RESIDENT, KERNEL_FUSED, KERNEL_TILED, KERNEL_TILED_FUSED = 0, 1, 2, 3, 4, 5
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
           4: "device wait timed out", 5: "call out of order", 6: "unsupported"}
@@ -267,7 +267,8 @@ class Sim:
         self._check(lib().jwf_set_kernel(self._h, int(kernel), int(threads_per_env)), "jwf_set_kernel")
 
     def set_pair_counter(self, counter):
-        """counter: int64 device tensor of one element, or None (off)."""
+        """counter: int64 device tensor of four elements (pairs compared,
+        candidate Philox blocks, remain-burning draws, words scanned), or None."""
         self._check(lib().jwf_set_pair_counter(self._h, _ptr(counter)), "jwf_set_pair_counter")
 
     def step(self, k: int = 1, drops=None, burning=None, burnt=None, done=None, stream=None):

@@ -2,6 +2,11 @@
 done flags, for both step kernels, given the same float table (computed by the
 FP64 oracle and rounded) and the same Philox stream.
 
+Kernels: plain (one launch per step), resident (whole env in shared memory,
+k steps per launch), tiled (128 x 256 tiles with halos, up to 16 steps per
+launch, cold tiles skipped), and the fused variants of the last two, which
+evaluate probabilities from the terrain and must equal the table path.
+
 Edge cases: single grid of the plain workload (64x64, 100 steps), the batched
 workload at reduced and full size (sampled), ragged batches, widths that are
 not multiples of 32 (1, 17, 33, 37), one-row and one-cell grids, no fuel at
@@ -17,7 +22,7 @@ from paper_2512_06102_gb300 import jwf, scenarios
 from tests.gpu_util import make_sim, oracle_tables, require_gpu, to
 
 pytestmark = pytest.mark.gpu
-KERNELS = [jwf.KERNEL_PLAIN, jwf.KERNEL_RESIDENT]
+KERNELS = [jwf.KERNEL_PLAIN, jwf.KERNEL_RESIDENT, jwf.KERNEL_TILED]
 
 
 def _run_both(scn, q32, k, drops=None, seed=0, kernel=jwf.KERNEL_AUTO, t_max=0, auto_reset=False,
@@ -304,3 +309,90 @@ def test_fused_equals_table_path_full_size():
     a = _gpu_run(scn, 200, drops, jwf.KERNEL_RESIDENT, 1000)
     b = _gpu_run(scn, 200, drops, jwf.KERNEL_FUSED, 1000)
     _same(a, b)
+
+
+# ---------------------------------------------------------------------------
+# tiled path on grids spanning several tiles
+# ---------------------------------------------------------------------------
+def _fire_drops(scn, k, seed):
+    """Drops aimed at the initial fires (so that they douse burning cells on
+    tile borders and corners), one per env and step, jittered by +-2 cells."""
+    rng = np.random.default_rng(seed)
+    out = np.full((k, scn.N, 2), -1, np.int32)
+    for e in range(scn.N):
+        F = scn.env(e, scn.F0)
+        ys, xs = np.nonzero(F == 2)
+        for s in range(k):
+            if len(ys) and rng.random() < 0.7:
+                j = rng.integers(len(ys))
+                out[s, e] = (xs[j] + rng.integers(-2, 3), ys[j] + rng.integers(-2, 3))
+            elif rng.random() < 0.5:
+                out[s, e] = (rng.integers(0, scn.W[e]), rng.integers(0, scn.H[e]))
+    return out
+
+
+def _fires_on_tile_corners(scn):
+    """Add fires at tile corners and edges (rows 127/128, columns 255/256)."""
+    for e in range(scn.N):
+        F = scn.env(e, scn.F0)
+        H, W = F.shape
+        for y, x in [(127, 255), (128, 256), (127, 256), (128, 255), (0, W - 1), (H - 1, 0), (64, 256)]:
+            if y < H and x < W:
+                F[y, x] = 2
+
+
+@pytest.mark.parametrize("shape,N,k", [((300, 700), 2, 37), ((129, 257), 3, 50), ((520, 300), 1, 33)])
+def test_tiled_multi_tile_matches_oracle(shape, N, k):
+    require_gpu()
+    H, W = shape
+    scn = scenarios.make_scenario(H, W, N=N, seed=31)
+    _fires_on_tile_corners(scn)
+    q32 = oracle_tables(scn)[0]
+    drops = _fire_drops(scn, k, 31)
+    _run_both(scn, q32, k, drops=drops, seed=8, kernel=jwf.KERNEL_TILED, splits=[k // 2, k - k // 2])
+
+
+def test_tiled_fused_equals_tiled_table():
+    require_gpu()
+    scn = scenarios.make_scenario(600, 900, N=2, seed=32)
+    _fires_on_tile_corners(scn)
+    k = 60
+    drops = _fire_drops(scn, k, 32)
+    a = _gpu_run(scn, k, drops, jwf.KERNEL_TILED, 3)
+    b = _gpu_run(scn, k, drops, jwf.KERNEL_TILED_FUSED, 3)
+    c = _gpu_run(scn, k, drops, jwf.KERNEL_PLAIN, 3)
+    _same(a, b)
+    _same(a, c)
+
+
+def test_tiled_large_grids_sampled():
+    """8 x 4096^2 (the large-map workload) for 48 steps with drops: tiled fused
+    against the plain path on all grids, and the oracle on one grid."""
+    require_gpu()
+    from oracle import prob
+    N, H, W, k = 8, 4096, 4096, 48
+    scn = scenarios.make_scenario(H, W, N=N, seed=0)
+    drops = _fire_drops(scn, k, 0)
+    a = _gpu_run(scn, k, drops, jwf.KERNEL_TILED_FUSED, 11)
+    b = _gpu_run(scn, k, drops, jwf.KERNEL_PLAIN, 11)
+    _same(a, b)
+    # the oracle on grid 5 with the GPU's own table for that grid replaced by the oracle's
+    e = 5
+    q32, _, _, _ = prob.table_f32(scn.env(e, scn.cls)[None], scn.env(e, scn.dem)[None],
+                                  scn.wind_speed[e:e + 1], scn.wind_dir[e:e + 1], scn.params.as_dict(), 30.0)
+    sim = make_sim(scn, seed=11)
+    sim.set_kernel(jwf.KERNEL_TILED)
+    sim.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    qg = sim.probs()[0]
+    qg[scn.offsets[e]:scn.offsets[e + 1]] = to(q32.reshape(-1, 8))
+    sim.load_state(to(scn.F0))
+    out = sim.step(k, drops=to(drops))
+    torch.cuda.synchronize()
+    st = sim.state()[scn.offsets[e]:scn.offsets[e + 1]].cpu().numpy()
+    ro = discrete.Rollout([H], [W], scn.env(e, scn.F0).reshape(-1), q32.reshape(-1, 8), scn.params.p_continue,
+                          seed=11, env_ids=[e])
+    ob, od, odone = ro.step(k, np.ascontiguousarray(drops[:, e:e + 1]))
+    np.testing.assert_array_equal(st, ro.F)
+    np.testing.assert_array_equal(out[0].cpu().numpy()[:, e:e + 1], ob)
+    np.testing.assert_array_equal(out[1].cpu().numpy()[:, e:e + 1], od)
+    sim.close()
