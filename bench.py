@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 
 N_ENVS, SIDE, EPISODE = 4096, 128, 200
 REL_ENVS, REL_T = 256, 100
+RAG_ENVS, RAG_T, RAG_TMAX = 10000, 500, 200
 METRIC = "CA cell-updates/s at 4096x128^2 (200-step episode with tanker drops)"
 CPU_SAMPLE_ENVS = 48
 # lane-operation model of the step (instruction counts of the work the model
@@ -57,6 +58,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-relaxed", action="store_true")
+    ap.add_argument("--no-rollout", action="store_true")
     return ap.parse_args()
 
 
@@ -338,6 +340,9 @@ def run_ours(args):
     rel = None
     if not args.no_relaxed:
         rel = bench_relaxed(args, D, dev, rank)
+    rag = None
+    if not args.no_rollout:
+        rag = bench_rollout(args, D, dev, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -360,6 +365,8 @@ def run_ours(args):
             "clocks": clocks}
     if rel is not None:
         line["relaxed"] = rel
+    if rag is not None:
+        line["rollout"] = rag
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -437,6 +444,73 @@ def bench_relaxed(args, D, dev, rank):
                          "traffic": kernel_traffic("k_relaxed_fwd", "paper_2512_06102_gb300/csrc/k_relaxed.cu"),
                          "kernel": "k_relaxed_fwd", "kernel_us": round(t_fwd * 1e6, 2),
                          "bytes_model": "48 B/cell-step (8 B state in, 32 B rates, 8 B state out)"}}
+
+
+def bench_rollout(args, D, dev, rank):
+    """10,000 grids, side log-uniform in [32, 512], 500-step RL rollout with a
+    random 3x3 drop per grid and step, auto-reset (episode limit 200), one CUDA
+    graph; steps per launch and block sizes from the autotuner."""
+    import torch
+
+    from paper_2512_06102_gb300 import autotune, jwf, rollout, scenarios
+
+    sides = scenarios.ragged_sides(RAG_ENVS, 32, 512, seed=7 + rank)
+    scn = scenarios.make_scenario(sides, sides, seed=7 + rank)
+    drops = scenarios.drops(RAG_T, scn.H, scn.W, seed=7 + rank)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    terrain = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    F0, dr = to(scn.F0), to(drops)
+    cells = int(scn.cls.size)
+    sim = jwf.Sim(scn.H, scn.W, n_classes=scenarios.N_CLASSES, seed=2000 + rank, t_max=RAG_TMAX, auto_reset=True)
+    sim.set_params(scn.params)
+    sim.set_kernel(jwf.KERNEL_FUSED)
+    sim.set_terrain(*terrain)
+    choice = autotune.tune(sim, F0, dr, kernel=jwf.KERNEL_FUSED, probe_steps=16, use_cache=False)
+    k_best = autotune.tune_steps_per_launch(sim, F0, dr, 64, candidates=(1, 8, 32, 64))
+
+    def timed(fn, reps=1):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            best = t if best is None else min(best, t)
+        return best
+
+    res = {}
+    for k in sorted({1, k_best}):
+        g = rollout.GraphRollout(sim, RAG_T, dr, steps_per_launch=k)
+        sim.load_state(F0)
+        g.run()
+        D.barrier()
+        t = timed(lambda: (sim.load_state(F0), g.run()), reps=max(1, min(args.steps, 3)))
+        res[k] = D.max(t)
+        del g
+    k_use = min(res, key=res.get)
+    t_graph = res[k_use]
+    eager = rollout.GraphRollout(sim, RAG_T, dr, capture=False, steps_per_launch=1)
+    t_eager = timed(lambda: (sim.load_state(F0), eager.run()))
+    # plain one-launch-per-step path on the same rollout (table built first)
+    sim.precompute_probs(*terrain)
+    sim.set_kernel(jwf.KERNEL_PLAIN)
+    plain = rollout.GraphRollout(sim, RAG_T, dr, capture=False, steps_per_launch=1)
+    t_plain = timed(lambda: (sim.load_state(F0), plain.run()))
+    sim.close()
+    world = D.world
+    return {"metric": "env-steps/s, 10000 ragged grids (side log-uniform 32..512), 500-step rollout, auto-reset",
+            "value": world * RAG_ENVS * RAG_T / t_graph, "unit": "env-steps/s",
+            "cell_updates_per_s": world * cells * RAG_T / t_graph, "cells": cells,
+            "ms_per_rollout": round(t_graph * 1e3, 3), "steps_per_launch": k_use,
+            "graph_ms_by_steps_per_launch": {str(k): round(v * 1e3, 3) for k, v in res.items()},
+            "autotune": choice,
+            "comparators": {"eager_one_step_launches_ms": round(t_eager * 1e3, 3),
+                            "plain_one_launch_per_step_ms": round(t_plain * 1e3, 3),
+                            "speedup_vs_plain": round(t_plain / t_graph, 2),
+                            "speedup_vs_eager": round(t_eager / t_graph, 2)}}
 
 
 # ---------------------------------------------------------------------------

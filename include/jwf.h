@@ -223,6 +223,20 @@ typedef enum {
  * else 32, 64, 128 or 256 threads per env (resident kernels). */
 JWF_API jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_env);
 
+/* Resident envs run as up to four size classes by their longer side (<= 64,
+ * <= 128, <= 256, > 256: classes 0..3), one persistent launch each, side by
+ * side on forked streams.  jwf_size_classes writes the classes present to
+ * h_classes (host, up to 4 entries, may be NULL) and returns their number;
+ * jwf_set_class_threads sets the block size of one class (0: by size; 32,
+ * 64, 128 or 256), e.g. from an autotuner.  jwf_set_kernel's explicit
+ * threads_per_env overrides both. */
+JWF_API int32_t jwf_size_classes(const jwf_ctx* ctx, int32_t* h_classes);
+JWF_API jwf_status jwf_set_class_threads(jwf_ctx* ctx, int32_t size_class, int32_t threads);
+
+/* Steps per launch of the tiled kernel (1..16, default 16; the halo, and so
+ * the redundant work per tile, grows with it). */
+JWF_API jwf_status jwf_set_round_steps(jwf_ctx* ctx, int32_t steps);
+
 /* Instrumentation: while d_counts (four uint64 on the device, owned by the
  * caller) is set, the resident step kernels add to them the work they did:
  * [0] (target, burning source) pairs compared (the table reads of the byte

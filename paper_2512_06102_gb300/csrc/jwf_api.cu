@@ -38,6 +38,11 @@ cudaError_t dev_alloc(T** p, size_t count) {
 }
 
 void free_all(jwf_ctx* c) {
+    for (int g = 0; g < JWF_MAX_GROUPS; ++g) {
+        if (c->side[g] != nullptr) cudaStreamDestroy(c->side[g]);
+        if (c->ev_join[g] != nullptr) cudaEventDestroy(c->ev_join[g]);
+    }
+    if (c->ev_fork != nullptr) cudaEventDestroy(c->ev_fork);
     void* ptrs[] = {c->d_H, c->d_W, c->d_off, c->d_order, c->d_tiles, c->d_state[0], c->d_state[1],
                     c->d_F0, c->d_q, c->d_r, c->d_t, c->d_episode, c->d_cnt, c->d_flag,
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_wexp,
@@ -135,11 +140,32 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
             for (int q = 0; q < tcn; ++q) tiles4.push_back(make_int4(e, r, q, 0));
     }
     c->n_tiles4 = (int64_t)tiles4.size();
+    // processing order: size class (by the longer side) descending, then
+    // cells descending; each class is one resident launch
+    auto size_class = [&](int32_t e) {
+        const int32_t side = std::max(c->H[e], c->W[e]);
+        return side <= 64 ? 0 : side <= 128 ? 1 : side <= 256 ? 2 : 3;
+    };
     std::vector<int32_t> order(N);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        const int ca = size_class(a), cb = size_class(b);
+        if (ca != cb) return ca > cb;
         return (int64_t)c->H[a] * c->W[a] > (int64_t)c->H[b] * c->W[b];
     });
+    for (int32_t i = 0; i < N; ++i) {
+        const int32_t e = order[i];
+        if (c->groups.empty() || c->groups.back().size_class != size_class(e)) {
+            JwfGroup G;
+            G.start = i;
+            G.size_class = size_class(e);
+            c->groups.push_back(G);
+        }
+        JwfGroup& G = c->groups.back();
+        G.count += 1;
+        G.maxH = std::max(G.maxH, c->H[e]);
+        G.maxW = std::max(G.maxW, c->W[e]);
+    }
 
     cudaError_t err = cudaGetDevice(&c->device);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -161,7 +187,7 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = dev_alloc(&c->d_cnt, 2 * (size_t)N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_flag, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_status, 1);
-    if (err == cudaSuccess) err = dev_alloc(&c->d_queue, 2);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_queue, 2 * JWF_MAX_GROUPS);
     if (err == cudaSuccess) err = dev_alloc(&c->d_partials, (size_t)c->partial_cap);
     if (err == cudaSuccess) err = dev_alloc(&c->d_red_counter, 1);
     if (err == cudaSuccess) err = dev_alloc(&c->d_wexp, (size_t)N * 8);
@@ -187,7 +213,14 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = cudaMemset(c->d_cnt, 0, 2 * N * sizeof(int32_t));
     if (err == cudaSuccess) err = cudaMemset(c->d_flag, 0, N);
     if (err == cudaSuccess) err = cudaMemset(c->d_status, 0, sizeof(uint32_t));
-    if (err == cudaSuccess) err = cudaMemset(c->d_queue, 0, 2 * sizeof(uint32_t));
+    if (err == cudaSuccess) err = cudaMemset(c->d_queue, 0, 2 * JWF_MAX_GROUPS * sizeof(uint32_t));
+    if (err == cudaSuccess && c->groups.size() > 1) {
+        err = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        for (size_t g = 0; g < c->groups.size() && err == cudaSuccess; ++g) {
+            err = cudaStreamCreateWithFlags(&c->side[g], cudaStreamNonBlocking);
+            if (err == cudaSuccess) err = cudaEventCreateWithFlags(&c->ev_join[g], cudaEventDisableTiming);
+        }
+    }
     if (err == cudaSuccess) err = cudaMemset(c->d_red_counter, 0, sizeof(uint32_t));
     if (err == cudaSuccess) err = cudaDeviceSynchronize();
     if (err != cudaSuccess) {
@@ -398,6 +431,30 @@ jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_e
     ctx->kernel = kernel;
     ctx->threads_per_env = threads_per_env;
     return JWF_OK;
+}
+
+jwf_status jwf_set_class_threads(jwf_ctx* ctx, int32_t size_class, int32_t threads) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (size_class < 0 || size_class > 3) return fail(ctx, JWF_EINVAL, "jwf_set_class_threads: class must be 0..3");
+    if (threads != 0 && threads != 32 && threads != 64 && threads != 128 && threads != 256)
+        return fail(ctx, JWF_EINVAL, "jwf_set_class_threads: threads must be 0, 32, 64, 128 or 256");
+    for (JwfGroup& G : ctx->groups)
+        if (G.size_class == size_class) G.threads = threads;
+    return JWF_OK;
+}
+
+jwf_status jwf_set_round_steps(jwf_ctx* ctx, int32_t steps) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (steps < 1 || steps > 16) return fail(ctx, JWF_EINVAL, "jwf_set_round_steps: steps must be 1..16");
+    ctx->round_steps = steps;
+    return JWF_OK;
+}
+
+int32_t jwf_size_classes(const jwf_ctx* ctx, int32_t* h_classes) {
+    if (ctx == nullptr) return 0;
+    for (size_t g = 0; g < ctx->groups.size(); ++g)
+        if (h_classes != nullptr) h_classes[g] = ctx->groups[g].size_class;
+    return (int32_t)ctx->groups.size();
 }
 
 jwf_status jwf_set_pair_counter(jwf_ctx* ctx, unsigned long long* d_pairs) {

@@ -61,6 +61,13 @@ struct JwfDevParams {
 // Per-cell kernels walk blocks of JWF_TILE consecutive cells of one env.
 #define JWF_TILE 256
 
+// A size class of envs run by one resident launch: envs order[start ..
+// start + count), the largest shape in it, and its block size (0: by size).
+struct JwfGroup {
+    int32_t start = 0, count = 0, maxH = 0, maxW = 0, threads = 0, size_class = 0;
+};
+#define JWF_MAX_GROUPS 4
+
 struct jwf_ctx {
     int device = 0;
     int num_sms = 0;
@@ -118,6 +125,12 @@ struct jwf_ctx {
     int32_t* d_tburnt = nullptr;
     int32_t* d_tcnt = nullptr;
     bool tiles_valid = false;
+    int32_t round_steps = 16;            // steps per tiled launch (1..16)
+    // size classes of the resident path and the streams/events they fork onto
+    std::vector<JwfGroup> groups;
+    cudaStream_t side[JWF_MAX_GROUPS] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[JWF_MAX_GROUPS] = {};
     bool wexp_stale = true;              // parameters changed since d_wexp was built
 
     JwfDevParams P{};

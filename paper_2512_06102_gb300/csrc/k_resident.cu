@@ -34,8 +34,9 @@ struct ResArgs {
     const int32_t* H;
     const int32_t* W;
     const int64_t* off;
-    const int32_t* order;
-    int32_t N;
+    const int32_t* order;       // envs of this launch's queue, largest first
+    int32_t nq;                 // length of the queue
+    int32_t N;                  // envs in the context (row length of drops and outputs)
     uint8_t* F;                 // in/out (in place: one CTA per env)
     const uint8_t* F0;
     const float* q;             // table variant
@@ -274,7 +275,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
     for (;;) {
         if (threadIdx.x == 0) {
             const uint32_t slot = atomicAdd(&a.queue[0], 1u);
-            s_env = (slot < (uint32_t)a.N) ? a.order[slot] : -1;
+            s_env = (slot < (uint32_t)a.nq) ? a.order[slot] : -1;
         }
         __syncthreads();
         const int e = s_env;
@@ -974,10 +975,12 @@ constexpr int kMaxDev = 64;
 // Per-instantiation launch facts, cached per device so that a launch after
 // the first one makes no attribute or occupancy query.
 template <int NT, bool FUSED>
-cudaError_t launch_t(const jwf_ctx* c, const ResArgs& a, const RateConsts& K, size_t smem, cudaStream_t s) {
+cudaError_t launch_t(const jwf_ctx* c, const ResArgs& a, const RateConsts& K, size_t smem, cudaStream_t s,
+                     int32_t nq) {
+    constexpr int kSlots = 8;
     static size_t set_smem[kMaxDev] = {};
-    static size_t occ_smem[kMaxDev] = {};
-    static int occ_blocks[kMaxDev] = {};
+    static size_t occ_smem[kMaxDev][kSlots] = {};
+    static int occ_blocks[kMaxDev][kSlots] = {};
     const int dev = c->device;
     if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
     cudaError_t err;
@@ -986,28 +989,34 @@ cudaError_t launch_t(const jwf_ctx* c, const ResArgs& a, const RateConsts& K, si
         if (err != cudaSuccess) return err;
         set_smem[dev] = smem;
     }
-    if (occ_smem[dev] != smem || occ_blocks[dev] == 0) {
+    int slot = -1;
+    for (int i = 0; i < kSlots; ++i)
+        if (occ_blocks[dev][i] > 0 && occ_smem[dev][i] == smem) slot = i;
+    if (slot < 0) {
         int per_sm = 0;
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_resident<NT, FUSED>, NT, smem);
         if (err != cudaSuccess) return err;
-        occ_blocks[dev] = per_sm;
-        occ_smem[dev] = smem;
+        slot = 0;
+        for (int i = 0; i < kSlots; ++i)
+            if (occ_blocks[dev][i] == 0) { slot = i; break; }
+        occ_blocks[dev][slot] = per_sm;
+        occ_smem[dev][slot] = smem;
     }
-    if (occ_blocks[dev] < 1) return cudaErrorInvalidConfiguration;
-    int64_t grid = (int64_t)occ_blocks[dev] * c->num_sms;
-    if (grid > c->N) grid = c->N;
+    if (occ_blocks[dev][slot] < 1) return cudaErrorInvalidConfiguration;
+    int64_t grid = (int64_t)occ_blocks[dev][slot] * c->num_sms;
+    if (grid > nq) grid = nq;
     k_step_resident<NT, FUSED><<<(unsigned)grid, NT, smem, s>>>(a, K);
     return cudaGetLastError();
 }
 
 template <bool FUSED>
 cudaError_t launch_v(const jwf_ctx* c, int threads, const ResArgs& a, const RateConsts& K, size_t smem,
-                     cudaStream_t s) {
+                     cudaStream_t s, int32_t nq) {
     switch (threads) {
-        case 32: return launch_t<32, FUSED>(c, a, K, smem, s);
-        case 64: return launch_t<64, FUSED>(c, a, K, smem, s);
-        case 128: return launch_t<128, FUSED>(c, a, K, smem, s);
-        case 256: return launch_t<256, FUSED>(c, a, K, smem, s);
+        case 32: return launch_t<32, FUSED>(c, a, K, smem, s, nq);
+        case 64: return launch_t<64, FUSED>(c, a, K, smem, s, nq);
+        case 128: return launch_t<128, FUSED>(c, a, K, smem, s, nq);
+        case 256: return launch_t<256, FUSED>(c, a, K, smem, s, nq);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1050,8 +1059,9 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         jwf_rate_consts(c, &K);
     else
         K = RateConsts{};
-    for (int32_t s0 = 0; s0 < k; s0 += kMaxRound) {
-        const int32_t kb = (k - s0) < kMaxRound ? (k - s0) : kMaxRound;
+    const int32_t rs = (c->round_steps >= 1 && c->round_steps <= kMaxRound) ? c->round_steps : kMaxRound;
+    for (int32_t s0 = 0; s0 < k; s0 += rs) {
+        const int32_t kb = (k - s0) < rs ? (k - s0) : rs;
         err = cudaMemsetAsync(c->d_tcnt, 0, (size_t)kb * 2 * c->N * sizeof(int32_t), s);
         if (err != cudaSuccess) return err;
         TileArgs a;
@@ -1112,15 +1122,11 @@ int jwf_resident_threads(int32_t H, int32_t W) {
 
 cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
                                      int32_t* burnt, uint8_t* done, cudaStream_t s) {
-    int threads = c->threads_per_env > 0 ? c->threads_per_env : jwf_resident_threads(c->maxH, c->maxW);
-    if (threads != 32 && threads != 64 && threads != 128) threads = 256;
-    const size_t smem = jwf_resident_smem(c->maxH, c->maxW, threads);
     const bool fused = c->kernel == JWF_KERNEL_FUSED;
     ResArgs a;
     a.H = c->d_H;
     a.W = c->d_W;
     a.off = c->d_off;
-    a.order = c->d_order;
     a.N = c->N;
     a.F = c->d_state[c->cur];
     a.F0 = c->d_F0;
@@ -1134,7 +1140,6 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
     a.out_burning = burning;
     a.out_burnt = burnt;
     a.out_done = done;
-    a.queue = c->d_queue;
     a.counts = c->d_pairs;
     a.k = k;
     a.t_max = c->t_max;
@@ -1144,10 +1149,41 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
     a.key1 = (uint32_t)(c->seed >> 32);
     a.p_continue = c->P.p_continue;
     RateConsts K;
-    if (fused) {
+    if (fused)
         jwf_rate_consts(c, &K);
-        return launch_v<true>(c, threads, a, K, smem, s);
+    else
+        K = RateConsts{};
+    // one persistent launch per size class; classes run side by side on
+    // forked streams when there is more than one
+    const int ng = (int)c->groups.size();
+    cudaError_t err = cudaSuccess;
+    if (ng > 1) {
+        err = cudaEventRecord(c->ev_fork, s);
+        if (err != cudaSuccess) return err;
     }
-    K = RateConsts{};
-    return launch_v<false>(c, threads, a, K, smem, s);
+    for (int g = 0; g < ng; ++g) {
+        const JwfGroup& G = c->groups[g];
+        int threads = c->threads_per_env > 0 ? c->threads_per_env
+                                             : (G.threads > 0 ? G.threads : jwf_resident_threads(G.maxH, G.maxW));
+        if (threads != 32 && threads != 64 && threads != 128) threads = 256;
+        const size_t smem = jwf_resident_smem(G.maxH, G.maxW, threads);
+        cudaStream_t gs = s;
+        if (ng > 1) {
+            gs = c->side[g];
+            err = cudaStreamWaitEvent(gs, c->ev_fork, 0);
+            if (err != cudaSuccess) return err;
+        }
+        a.order = c->d_order + G.start;
+        a.nq = G.count;
+        a.queue = c->d_queue + 2 * g;
+        err = fused ? launch_v<true>(c, threads, a, K, smem, gs, G.count)
+                    : launch_v<false>(c, threads, a, K, smem, gs, G.count);
+        if (err != cudaSuccess) return err;
+        if (ng > 1) {
+            err = cudaEventRecord(c->ev_join[g], gs);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(s, c->ev_join[g], 0);
+            if (err != cudaSuccess) return err;
+        }
+    }
+    return cudaSuccess;
 }

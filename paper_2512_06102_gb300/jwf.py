@@ -69,6 +69,9 @@ _SIGS = {
     "jwf_step": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP]),
     "jwf_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int32]),
     "jwf_set_pair_counter": (ctypes.c_int, [_VP, _VP]),
+    "jwf_size_classes": (ctypes.c_int32, [_VP, _VP]),
+    "jwf_set_class_threads": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "jwf_set_round_steps": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "jwf_get_state": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "jwf_step_relaxed_fwd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_step_relaxed_bwd": (ctypes.c_int, [_VP] * 11),
@@ -265,6 +268,17 @@ class Sim:
 
     def set_kernel(self, kernel: int = KERNEL_AUTO, threads_per_env: int = 0):
         self._check(lib().jwf_set_kernel(self._h, int(kernel), int(threads_per_env)), "jwf_set_kernel")
+
+    def size_classes(self) -> list:
+        buf = (ctypes.c_int32 * 4)()
+        n = lib().jwf_size_classes(self._h, ctypes.cast(buf, _VP))
+        return [int(buf[i]) for i in range(n)]
+
+    def set_class_threads(self, size_class: int, threads: int):
+        self._check(lib().jwf_set_class_threads(self._h, int(size_class), int(threads)), "jwf_set_class_threads")
+
+    def set_round_steps(self, steps: int):
+        self._check(lib().jwf_set_round_steps(self._h, int(steps)), "jwf_set_round_steps")
 
     def set_pair_counter(self, counter):
         """counter: int64 device tensor of four elements (pairs compared,
