@@ -291,6 +291,22 @@ JWF_API jwf_status jwf_rates_bwd(jwf_ctx* ctx, int32_t n_steps, const float* d_g
                          const float* d_dem, const float* d_wind_speed,
                          const float* d_wind_dir, double* d_gparams, void* stream);
 
+/* The two halves of jwf_rates_bwd, for a backward pass that contracts once:
+ * jwf_rates_accumulate adds the rate adjoint of n_steps relaxed steps,
+ *   d_gr[v][d] += sum_t glam_t(v) pb_t(v - Delta_d)     (float [cells][8]),
+ * summing the chunk in step order before adding (d_glam, d_pburn, d_mask as
+ * in jwf_rates_bwd); jwf_rates_contract adds
+ *   dL/dtheta += sum_{v,d} d_gr[v][d] dr[v][d]/dtheta
+ * to d_gparams (JWF_GRAD_SIZE doubles, fixed summation order).  Calling
+ * accumulate on fixed step chunks and contract once gives a result that does
+ * not depend on how the steps were recomputed (checkpointing). */
+JWF_API jwf_status jwf_rates_accumulate(jwf_ctx* ctx, int32_t n_steps, const float* d_glam,
+                                        const float* d_pburn, const float* d_mask, float* d_gr,
+                                        void* stream);
+JWF_API jwf_status jwf_rates_contract(jwf_ctx* ctx, const float* d_gr, const uint8_t* d_class,
+                                      const float* d_dem, const float* d_wind_speed,
+                                      const float* d_wind_dir, double* d_gparams, void* stream);
+
 /* ---- no-allocation variant ------------------------------------------------ */
 
 /* Largest batch, in cells (n_envs * H * W), that

@@ -45,7 +45,7 @@ void free_all(jwf_ctx* c) {
     if (c->ev_fork != nullptr) cudaEventDestroy(c->ev_fork);
     void* ptrs[] = {c->d_H, c->d_W, c->d_off, c->d_order, c->d_tiles, c->d_state[0], c->d_state[1],
                     c->d_F0, c->d_q, c->d_r, c->d_t, c->d_episode, c->d_cnt, c->d_flag,
-                    c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_wexp,
+                    c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
                     c->d_tcnt};
     for (void* p : ptrs)
@@ -182,6 +182,7 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = dev_alloc(&c->d_q, (size_t)c->cells * 8);
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_r, (size_t)c->cells * 8);
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_glam, (size_t)c->cells);
+    if (err == cudaSuccess && rates) err = dev_alloc(&c->d_gr, (size_t)c->cells * 8);
     if (err == cudaSuccess) err = dev_alloc(&c->d_t, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_episode, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_cnt, 2 * (size_t)N);
@@ -508,6 +509,32 @@ jwf_status jwf_step_relaxed_bwd(jwf_ctx* ctx, const float* d_pun, const float* d
     return JWF_OK;
 }
 
+jwf_status jwf_rates_accumulate(jwf_ctx* ctx, int32_t n_steps, const float* d_glam, const float* d_pburn,
+                                const float* d_mask, float* d_gr, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (n_steps < 0) return fail(ctx, JWF_EINVAL, "jwf_rates_accumulate: n_steps < 0");
+    if (d_glam == nullptr || d_pburn == nullptr || d_gr == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_rates_accumulate: null pointer");
+    if (n_steps == 0) return JWF_OK;
+    JWF_CUDA_TRY(ctx, jwf_launch_rates_accumulate(ctx, n_steps, d_glam, d_pburn, d_mask, d_gr, S(stream)),
+                 "jwf_rates_accumulate");
+    return JWF_OK;
+}
+
+jwf_status jwf_rates_contract(jwf_ctx* ctx, const float* d_gr, const uint8_t* d_class, const float* d_dem,
+                              const float* d_wind_speed, const float* d_wind_dir, double* d_gparams,
+                              void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_gr == nullptr || d_class == nullptr || d_dem == nullptr || d_wind_speed == nullptr ||
+        d_wind_dir == nullptr || d_gparams == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_rates_contract: null pointer");
+    if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_rates_contract: no parameters set");
+    JWF_CUDA_TRY(ctx, jwf_launch_rates_contract(ctx, d_gr, d_class, d_dem, d_wind_speed, d_wind_dir, d_gparams,
+                                                S(stream)),
+                 "jwf_rates_contract");
+    return JWF_OK;
+}
+
 jwf_status jwf_rates_bwd(jwf_ctx* ctx, int32_t n_steps, const float* d_glam,
                          const float* d_pburn, const float* d_mask, const uint8_t* d_class,
                          const float* d_dem, const float* d_wind_speed,
@@ -518,6 +545,7 @@ jwf_status jwf_rates_bwd(jwf_ctx* ctx, int32_t n_steps, const float* d_glam,
         d_wind_speed == nullptr || d_wind_dir == nullptr || d_gparams == nullptr)
         return fail(ctx, JWF_EINVAL, "jwf_rates_bwd: null pointer");
     if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_rates_bwd: no parameters set");
+    if (ctx->d_gr == nullptr) return fail(ctx, JWF_EUNSUPPORTED, "jwf_rates_bwd: needs JWF_KEEP_RATES");
     if (n_steps == 0) return JWF_OK;
     JWF_CUDA_TRY(ctx, jwf_launch_rates_bwd(ctx, n_steps, d_glam, d_pburn, d_mask, d_class, d_dem, d_wind_speed,
                                            d_wind_dir, d_gparams, S(stream)),

@@ -105,6 +105,7 @@ struct jwf_ctx {
     int64_t partial_cap = 0;             // doubles available in d_partials
     uint32_t* d_red_counter = nullptr;   // blocks finished (last-block reduction)
     float* d_glam = nullptr;             // [cells] adjoint scratch of the relaxed step
+    float* d_gr = nullptr;               // [cells][8] rate-adjoint scratch of jwf_rates_bwd
     unsigned long long* d_pairs = nullptr;  // caller's instrumentation counter (not owned)
     float2* d_wexp = nullptr;            // [N][8] wind exponent (hi, lo) scratch of the table build
     // terrain borrowed from the caller for the fused step (jwf_set_terrain)
@@ -149,6 +150,10 @@ struct jwf_ctx {
 cudaError_t jwf_launch_wind_exponent(const jwf_ctx* c, const float* ws, const float* wd, cudaStream_t s);
 cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
                                   const float* ws, const float* wd, cudaStream_t s);
+cudaError_t jwf_launch_rates_accumulate(const jwf_ctx* c, int32_t n_steps, const float* glam,
+                                        const float* pburn, const float* mask, float* gr, cudaStream_t s);
+cudaError_t jwf_launch_rates_contract(jwf_ctx* c, const float* gr, const uint8_t* cls, const float* dem,
+                                      const float* ws, const float* wd, double* gparams, cudaStream_t s);
 cudaError_t jwf_launch_rates_bwd(jwf_ctx* c, int32_t n_steps, const float* glam,
                                  const float* pburn, const float* mask, const uint8_t* cls,
                                  const float* dem, const float* ws, const float* wd,

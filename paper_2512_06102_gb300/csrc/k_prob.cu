@@ -158,22 +158,79 @@ __device__ void block_reduce_vec(double (&val)[NV], double* smem /* [32][NV] */)
 constexpr int kRbThreads = 256;
 constexpr int kRbScalars = 5;   // p_base, alpha_w1, alpha_w2, alpha_s, alpha_gamma
 
+// Rate adjoint of a chunk of relaxed steps: gr[v][d] += sum_t glam_t(v) pb_t(v - Delta_d)
+// (pb = (1 - m) p_burn), summed over the chunk in step order, then added once.
+__global__ void __launch_bounds__(JWF_TILE)
+k_rates_accumulate(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
+                   const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs, int64_t cells,
+                   int32_t n_steps, const float* __restrict__ glam, const float* __restrict__ pburn,
+                   const float* __restrict__ mask, float* __restrict__ gr) {
+    const int2 tile = tiles[blockIdx.x];
+    const int e = tile.x;
+    const int W = Ws[e], H = Hs[e];
+    const int local = tile.y + (int)threadIdx.x;
+    if (local >= H * W) return;
+    const int64_t off = offs[e];
+    const int y = local / W, x = local - (local / W) * W;
+    const int64_t v = off + local;
+    float w[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) w[d] = 0.f;
+    bool any = false;
+    for (int t = 0; t < n_steps; ++t) {
+        const int64_t base = (int64_t)t * cells;
+        const float g = glam[base + v];
+        if (g == 0.f) continue;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int uy = y - jwf_dr(d), ux = x - jwf_dx(d);
+            if (uy < 0 || uy >= H || ux < 0 || ux >= W) continue;
+            const int64_t u = off + (int64_t)uy * W + ux;
+            float pb = pburn[base + u];
+            if (mask != nullptr) pb *= 1.0f - mask[base + u];
+            if (pb != 0.f) {
+                w[d] += g * pb;
+                any = true;
+            }
+        }
+    }
+    if (!any) return;
+    float4* g4 = reinterpret_cast<float4*>(gr + v * 8);
+    float4 a = g4[0], b = g4[1];
+    a.x += w[0]; a.y += w[1]; a.z += w[2]; a.w += w[3];
+    b.x += w[4]; b.y += w[5]; b.z += w[6]; b.w += w[7];
+    g4[0] = a;
+    g4[1] = b;
+}
+
+// Parameter gradient through the rates.  Per target cell v and direction d
+// (source u = v - Delta_d), w = gr[v][d] is the adjoint of r(v, d); with
+// r = gamma(v) phi(u, d),
+//   dr/dp_base = gamma A_u K,   dr/dalpha_gamma = A_v phi,
+//   dr/dalpha_w1 = r V,  dr/dalpha_w2 = r V (cos - 1),  dr/dalpha_s = r S,
+//   dr/dmu_veg[k] = (1 + mu_den[k]) B_k,  dr/dmu_den[k] = (1 + mu_veg[k]) B_k,
+// where B_k gathers alpha_gamma phi (target of class k) and gamma p_base K
+// (source of class k); no division, so classes without fuel are exact.
+// Each thread sums its cells in float (a few dozen terms); the class bins sit
+// in shared memory, one column per thread (class-major, conflict-free); the
+// block and the grid are reduced in double in a fixed order (the last block
+// to finish adds the per-block partials), so the result is deterministic.
 template <int C>
 __global__ void __launch_bounds__(kRbThreads)
 k_rates_bwd(const int2* __restrict__ tiles, int64_t n_tiles, const int32_t* __restrict__ Hs,
             const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs, int64_t cells,
-            int32_t n_steps, const float* __restrict__ glam, const float* __restrict__ pburn,
-            const float* __restrict__ mask, const uint8_t* __restrict__ cls,
+            const float* __restrict__ gr, const uint8_t* __restrict__ cls,
             const float* __restrict__ dem, const float* __restrict__ ws,
             const float* __restrict__ wd, int per_cell_wind, const JwfDevParams P,
             double* __restrict__ partials, uint32_t* __restrict__ counter,
             double* __restrict__ gparams) {
     constexpr int NV = kRbScalars + 2 * C;
-    __shared__ double red[32 * NV];
+    __shared__ float bins[C * kRbThreads];
+    __shared__ double red[kRbThreads];
     __shared__ bool am_last;
-    double acc[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    const int tid = threadIdx.x;
+    for (int k = 0; k < C; ++k) bins[k * kRbThreads + tid] = 0.f;
+    float g_pb = 0.f, g_w1 = 0.f, g_w2 = 0.f, g_s = 0.f, g_gam = 0.f;
     const DirConst dc = dir_const();
     const float slope_scale = 57.295779513082320876f;
     const float inv_cell = 1.0f / P.cell_size;
@@ -182,29 +239,14 @@ k_rates_bwd(const int2* __restrict__ tiles, int64_t n_tiles, const int32_t* __re
         const int2 tile = tiles[ti];
         const int e = tile.x;
         const int W = Ws[e], H = Hs[e];
-        const int local = tile.y + (int)threadIdx.x;
+        const int local = tile.y + tid;
         if (local >= H * W) continue;
         const int64_t off = offs[e];
         const int y = local / W, x = local - (local / W) * W;
         const int64_t v = off + local;
-        // w[d] = sum_t glam_t(v) * pb_t(v - Delta_d)
-        float w[8];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) w[d] = 0.f;
-        for (int t = 0; t < n_steps; ++t) {
-            const int64_t base = (int64_t)t * cells;
-            const float g = glam[base + v];
-            if (g == 0.f) continue;
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const int uy = y - jwf_dr(d), ux = x - jwf_dx(d);
-                if (uy < 0 || uy >= H || ux < 0 || ux >= W) continue;
-                const int64_t u = off + (int64_t)uy * W + ux;
-                float pb = pburn[base + u];
-                if (mask != nullptr) pb *= 1.0f - mask[base + u];
-                if (pb != 0.f) w[d] += g * pb;
-            }
-        }
+        const float4* g4 = reinterpret_cast<const float4*>(gr + v * 8);
+        const float4 ga = __ldg(g4), gb = __ldg(g4 + 1);
+        const float w[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
         const int cv = cls[v];
         const float zv = dem[v];
         const float Av = (1.0f + P.mu_veg[cv]) * (1.0f + P.mu_den[cv]);
@@ -214,14 +256,10 @@ k_rates_bwd(const int2* __restrict__ tiles, int64_t n_tiles, const int32_t* __re
             Venv = ws[e];
             sincosf(wd[e], &sth, &cth);
         }
-        float g_pb = 0.f, g_w1 = 0.f, g_w2 = 0.f, g_s = 0.f, g_gam = 0.f;
-        float tgt = 0.f;        // sum_d w phi: dL/dgamma(v)
-        float src[8];           // w * gamma(v) * p_base * K: dL/dA(c_u)
-        int cu_d[8];
+        float tgt = 0.f;
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
-            src[d] = 0.f;
-            cu_d[d] = -1;
+            if (w[d] == 0.f) continue;
             const int uy = y - jwf_dr(d), ux = x - jwf_dx(d);
             if (uy < 0 || uy >= H || ux < 0 || ux >= W) continue;
             const int64_t u = off + (int64_t)uy * W + ux;
@@ -235,79 +273,84 @@ k_rates_bwd(const int2* __restrict__ tiles, int64_t n_tiles, const int32_t* __re
                                            dc.inv_len[d] * inv_cell, slope_scale);
             const float Au = (1.0f + P.mu_veg[cu]) * (1.0f + P.mu_den[cu]);
             const float phi = P.p_base * Au * t.K;
-            const float rate = gamma * phi;
-            const float wr = w[d] * rate;
-            g_pb += w[d] * gamma * Au * t.K;   // dr/dp_base
-            g_w1 += wr * t.V;                  // dr/dalpha_w1
-            g_w2 += wr * t.V * t.cosm1;        // dr/dalpha_w2
-            g_s += wr * t.S;                   // dr/dalpha_s
-            g_gam += w[d] * Av * phi;          // dr/dalpha_gamma
+            const float wr = w[d] * gamma * phi;
+            g_pb += w[d] * gamma * Au * t.K;
+            g_w1 += wr * t.V;
+            g_w2 += wr * t.V * t.cosm1;
+            g_s += wr * t.S;
+            g_gam += w[d] * Av * phi;
             tgt += w[d] * phi;
-            src[d] = w[d] * gamma * P.p_base * t.K;
-            cu_d[d] = cu;
+            bins[cu * kRbThreads + tid] += w[d] * gamma * P.p_base * t.K;   // source of class cu
         }
-        acc[0] += g_pb;
-        acc[1] += g_w1;
-        acc[2] += g_w2;
-        acc[3] += g_s;
-        acc[4] += g_gam;
-        // mu_veg[k]: target role alpha_gamma (1 + mu_den[k]) tgt; source role (1 + mu_den[k]) src
-        // mu_den[k]: target role alpha_gamma (1 + mu_veg[k]) tgt; source role (1 + mu_veg[k]) src
-#pragma unroll
-        for (int k = 0; k < C; ++k) {
-            float sk = 0.f;
-#pragma unroll
-            for (int d = 0; d < 8; ++d) sk += (cu_d[d] == k) ? src[d] : 0.f;
-            const float tk = (cv == k) ? P.alpha_gamma * tgt : 0.f;
-            acc[kRbScalars + k] += (double)((tk + sk) * (1.0f + P.mu_den[k]));
-            acc[kRbScalars + C + k] += (double)((tk + sk) * (1.0f + P.mu_veg[k]));
-        }
+        if (tgt != 0.f) bins[cv * kRbThreads + tid] += P.alpha_gamma * tgt;  // target of class cv
     }
-    block_reduce_vec<NV>(acc, red);
-    if (threadIdx.x < NV) partials[(int64_t)blockIdx.x * NV + threadIdx.x] = acc[threadIdx.x];
+    // block reduction in double, fixed order: thread values -> red[] tree
+    const float sc[kRbScalars] = {g_pb, g_w1, g_w2, g_s, g_gam};
+#pragma unroll 1
+    for (int i = 0; i < NV; ++i) {
+        double val;
+        if (i < kRbScalars) {
+            val = (double)(i == 0 ? sc[0] : i == 1 ? sc[1] : i == 2 ? sc[2] : i == 3 ? sc[3] : sc[4]);
+        } else {
+            const int k = (i - kRbScalars) % C;
+            const float b = bins[k * kRbThreads + tid];
+            val = (i - kRbScalars) < C ? (double)(b * (1.0f + P.mu_den[k])) : (double)(b * (1.0f + P.mu_veg[k]));
+        }
+        red[tid] = val;
+        __syncthreads();
+        for (int o = kRbThreads / 2; o > 0; o >>= 1) {
+            if (tid < o) red[tid] += red[tid + o];
+            __syncthreads();
+        }
+        if (tid == 0) partials[(int64_t)blockIdx.x * NV + i] = red[0];
+        __syncthreads();
+    }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (tid == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!am_last) return;
     __threadfence();
     // the last block sums the block partials in a fixed order
-    double tot[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) tot[i] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-#pragma unroll
-        for (int j = 0; j < NV; ++j) tot[j] += __ldcg(&partials[(int64_t)b * NV + j]);
-    }
-    block_reduce_vec<NV>(tot, red);
-    // layout [p_base, alpha_w1, alpha_w2, alpha_s, alpha_gamma, mu_veg[nC], mu_den[nC]]
     const int nC = P.n_classes;
-    const int i = threadIdx.x;
-    if (i < kRbScalars) {
-        gparams[i] += tot[i];
-    } else if (i < kRbScalars + C) {
-        if (i - kRbScalars < nC) gparams[i] += tot[i];
-    } else if (i < NV) {
-        const int k = i - kRbScalars - C;
-        if (k < nC) gparams[kRbScalars + nC + k] += tot[i];
+#pragma unroll 1
+    for (int i = 0; i < NV; ++i) {
+        double s2 = 0.0;
+        for (int b = tid; b < (int)gridDim.x; b += kRbThreads) s2 += __ldcg(&partials[(int64_t)b * NV + i]);
+        red[tid] = s2;
+        __syncthreads();
+        for (int o = kRbThreads / 2; o > 0; o >>= 1) {
+            if (tid < o) red[tid] += red[tid + o];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            // layout [p_base, alpha_w1, alpha_w2, alpha_s, alpha_gamma, mu_veg[nC], mu_den[nC]]
+            const double g = red[0];
+            if (i < kRbScalars) {
+                gparams[i] += g;
+            } else if (i < kRbScalars + C) {
+                if (i - kRbScalars < nC) gparams[i] += g;
+            } else {
+                const int k = i - kRbScalars - C;
+                if (k < nC) gparams[kRbScalars + nC + k] += g;
+            }
+        }
+        __syncthreads();
     }
-    if (threadIdx.x == 0) *counter = 0u;
+    if (tid == 0) *counter = 0u;
 }
 
 template <int C>
-cudaError_t launch_rates_bwd_c(jwf_ctx* c, int32_t n_steps, const float* glam,
-                               const float* pburn, const float* mask, const uint8_t* cls,
-                               const float* dem, const float* ws, const float* wd,
-                               double* gparams, cudaStream_t s) {
+cudaError_t launch_rates_contract_c(jwf_ctx* c, const float* gr, const uint8_t* cls, const float* dem,
+                                    const float* ws, const float* wd, double* gparams, cudaStream_t s) {
     constexpr int NV = kRbScalars + 2 * C;
-    int64_t grid = (int64_t)c->num_sms * 4;
+    int64_t grid = (int64_t)c->num_sms * 6;
     if (grid > c->n_tiles) grid = c->n_tiles;
     if (grid * NV > c->partial_cap) grid = c->partial_cap / NV;
     if (grid < 1) return cudaErrorInvalidValue;
     k_rates_bwd<C><<<(unsigned)grid, kRbThreads, 0, s>>>(
-        c->d_tiles, c->n_tiles, c->d_H, c->d_W, c->d_off, c->cells, n_steps, glam, pburn, mask,
-        cls, dem, ws, wd, (c->flags & JWF_WIND_PER_CELL) ? 1 : 0, c->P, c->d_partials,
-        c->d_red_counter, gparams);
+        c->d_tiles, c->n_tiles, c->d_H, c->d_W, c->d_off, c->cells, gr, cls, dem, ws, wd,
+        (c->flags & JWF_WIND_PER_CELL) ? 1 : 0, c->P, c->d_partials, c->d_red_counter, gparams);
     return cudaGetLastError();
 }
 
@@ -367,15 +410,30 @@ cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const fl
     return cudaGetLastError();
 }
 
+cudaError_t jwf_launch_rates_accumulate(const jwf_ctx* c, int32_t n_steps, const float* glam,
+                                        const float* pburn, const float* mask, float* gr, cudaStream_t s) {
+    k_rates_accumulate<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(c->d_tiles, c->d_H, c->d_W, c->d_off, c->cells,
+                                                                  n_steps, glam, pburn, mask, gr);
+    return cudaGetLastError();
+}
+
+cudaError_t jwf_launch_rates_contract(jwf_ctx* c, const float* gr, const uint8_t* cls, const float* dem,
+                                      const float* ws, const float* wd, double* gparams, cudaStream_t s) {
+    // class-count specialisations keep the per-class bins sized to the table
+    const int C = c->n_classes;
+    if (C <= 1) return launch_rates_contract_c<1>(c, gr, cls, dem, ws, wd, gparams, s);
+    if (C <= 4) return launch_rates_contract_c<4>(c, gr, cls, dem, ws, wd, gparams, s);
+    if (C <= 11) return launch_rates_contract_c<11>(c, gr, cls, dem, ws, wd, gparams, s);
+    if (C <= 16) return launch_rates_contract_c<16>(c, gr, cls, dem, ws, wd, gparams, s);
+    return cudaErrorNotSupported;
+}
+
 cudaError_t jwf_launch_rates_bwd(jwf_ctx* c, int32_t n_steps, const float* glam,
                                  const float* pburn, const float* mask, const uint8_t* cls,
                                  const float* dem, const float* ws, const float* wd,
                                  double* gparams, cudaStream_t s) {
-    // class-count specialisations keep the per-class bins in registers
-    const int C = c->n_classes;
-    if (C <= 1) return launch_rates_bwd_c<1>(c, n_steps, glam, pburn, mask, cls, dem, ws, wd, gparams, s);
-    if (C <= 4) return launch_rates_bwd_c<4>(c, n_steps, glam, pburn, mask, cls, dem, ws, wd, gparams, s);
-    if (C <= 11) return launch_rates_bwd_c<11>(c, n_steps, glam, pburn, mask, cls, dem, ws, wd, gparams, s);
-    if (C <= 16) return launch_rates_bwd_c<16>(c, n_steps, glam, pburn, mask, cls, dem, ws, wd, gparams, s);
-    return cudaErrorNotSupported;
+    cudaError_t err = cudaMemsetAsync(c->d_gr, 0, (size_t)c->cells * 8 * sizeof(float), s);
+    if (err == cudaSuccess) err = jwf_launch_rates_accumulate(c, n_steps, glam, pburn, mask, c->d_gr, s);
+    if (err == cudaSuccess) err = jwf_launch_rates_contract(c, c->d_gr, cls, dem, ws, wd, gparams, s);
+    return err;
 }

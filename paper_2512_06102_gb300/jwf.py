@@ -76,6 +76,8 @@ _SIGS = {
     "jwf_step_relaxed_fwd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_step_relaxed_bwd": (ctypes.c_int, [_VP] * 11),
     "jwf_rates_bwd": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 9),
+    "jwf_rates_accumulate": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 5),
+    "jwf_rates_contract": (ctypes.c_int, [_VP] * 8),
     "jwf_step_relaxed_bwd_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP,
                                                     ctypes.c_float] + [_VP] * 9),
 }
@@ -335,6 +337,17 @@ class Sim:
         self._check(lib().jwf_rates_bwd(self._h, int(n), _ptr(glam), _ptr(pburn), _ptr(mask), _ptr(cls),
                                         _ptr(dem), _ptr(wind_speed), _ptr(wind_dir), _ptr(gparams),
                                         _stream(stream)), "jwf_rates_bwd")
+        return gparams
+
+    def rates_accumulate(self, glam, pburn, gr, mask=None, stream=None):
+        n = glam.shape[0] if glam.dim() == 2 else 1
+        self._check(lib().jwf_rates_accumulate(self._h, int(n), _ptr(glam), _ptr(pburn), _ptr(mask), _ptr(gr),
+                                               _stream(stream)), "jwf_rates_accumulate")
+        return gr
+
+    def rates_contract(self, gr, cls, dem, wind_speed, wind_dir, gparams, stream=None):
+        self._check(lib().jwf_rates_contract(self._h, _ptr(gr), _ptr(cls), _ptr(dem), _ptr(wind_speed),
+                                             _ptr(wind_dir), _ptr(gparams), _stream(stream)), "jwf_rates_contract")
         return gparams
 
     @property

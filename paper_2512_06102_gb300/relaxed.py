@@ -2,19 +2,20 @@
 
 `RelaxedRollout.apply(theta, p_un0, p_burn0, sim, scene, T, masks, ckpt_every)`
 runs T relaxed steps with libjwf's forward kernel and returns (p_un_T,
-p_burn_T); its backward runs libjwf's adjoint kernels step by step in reverse
-and contracts the per-step rate adjoints into parameter gradients with
-jwf_rates_bwd.  This is the gradient the paper's calibration uses (Section 4:
-Adam on the raw-probabilities routine).
+p_burn_T); its backward runs libjwf's adjoint kernels step by step in reverse,
+accumulates the rate adjoint over fixed step chunks (jwf_rates_accumulate)
+and contracts it into parameter gradients once (jwf_rates_contract).  This
+is the gradient the paper's calibration uses (Section 4: Adam on the
+raw-probabilities routine).
 
 theta (float64, any device) = [p_base, alpha_w1, alpha_w2, alpha_s,
 alpha_gamma, p_continue, mu_veg[C], mu_den[C]].
 
 Memory: only the states at every `ckpt_every`-th step are kept by the
 forward; the backward recomputes one segment at a time (default segment
-ceil(sqrt(T)) rounded up to a multiple of CHUNK).  The rate contraction runs on
-CHUNK-step blocks aligned to absolute step indices, so checkpointed and
-non-checkpointed gradients are bit-identical.
+ceil(sqrt(T)) rounded up to a multiple of CHUNK).  The rate adjoint is
+accumulated on CHUNK-step blocks aligned to absolute step indices, so
+checkpointed and non-checkpointed gradients are bit-identical.
 """
 from __future__ import annotations
 
@@ -89,6 +90,7 @@ class RelaxedRollout(torch.autograd.Function):
         pu_buf = torch.empty((seg, cells), dtype=torch.float32, device=dev)
         pb_buf = torch.empty((seg, cells), dtype=torch.float32, device=dev)
         glam = torch.empty((seg, cells), dtype=torch.float32, device=dev)
+        gr = torch.zeros((cells, 8), dtype=torch.float32, device=dev)     # rate adjoint
         mk_buf = None if masks is None else torch.empty((seg, cells), dtype=torch.float32, device=dev)
         ngu, ngb = torch.empty_like(gu), torch.empty_like(gb)
         for si in reversed(range(n_seg)):
@@ -111,10 +113,11 @@ class RelaxedRollout(torch.autograd.Function):
                 gb, ngb = ngb, gb
                 if t % CHUNK == 0:
                     lo = t
-                    sim.rates_bwd(glam[lo - a:hi - a], pb_buf[lo - a:hi - a], cls, dem, ws, wd, gparams,
-                                  mask=None if masks is None else mk_buf[lo - a:hi - a])
+                    sim.rates_accumulate(glam[lo - a:hi - a], pb_buf[lo - a:hi - a], gr,
+                                         mask=None if masks is None else mk_buf[lo - a:hi - a])
                     hi = lo
             assert hi == a
+        sim.rates_contract(gr, cls, dem, ws, wd, gparams)
         C = sim.n_classes
         g = torch.empty(6 + 2 * C, dtype=torch.float64, device=dev)
         g[0:5] = gparams[0:5]

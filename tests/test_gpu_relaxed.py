@@ -8,6 +8,10 @@
     initial maps (T = 12) within 1e-4 relative of the oracle's autograd (which
     the CPU suite pins to central differences), with tanker masks, on several
     tiles and a ragged tail;
+  * the rate-adjoint accumulation (sum over steps of lambda-bar times the
+    masked source burn probability) within 1e-6 relative, and its contraction
+    with dr/dtheta within 1e-4 relative of the oracle's autograd; the one-call
+    jwf_rates_bwd agrees with the two halves;
   * checkpointed and non-checkpointed gradients are bit-identical;
   * T = 1000 on the 256 x 128^2 differentiation workload with sqrt(T)
     checkpoints: the parameter gradient of a loss on a sample of envs equals
@@ -185,6 +189,48 @@ def test_rollout_gradient_matches_oracle(T, check_maps):
             ref = ref.reshape(-1).numpy()
             noise = np.abs(ref32.reshape(-1).numpy() - ref)
             _close(g.cpu().numpy(), ref, floor=0.0, atol=10.0 * noise + 1e-20)
+
+
+def test_rate_adjoint_accumulate_and_contract():
+    require_gpu()
+    H, W, N, T = 70, 66, 3, 5
+    scn = scenarios.make_scenario(H, W, N=N, seed=6)
+    rng = np.random.default_rng(6)
+    cells = N * H * W
+    glam = rng.standard_normal((T, cells)).astype(np.float32)
+    pb = rng.random((T, cells)).astype(np.float32)
+    m = ((rng.random((T, cells)) < 0.1) * rng.random((T, cells))).astype(np.float32)
+    sim = make_sim(scn, keep_rates=True)
+    scene = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    sim.precompute_probs(*scene)
+    gr = torch.zeros((cells, 8), dtype=torch.float32, device="cuda")
+    sim.rates_accumulate(to(glam[:2]), to(pb[:2]), gr, mask=to(m[:2]))
+    sim.rates_accumulate(to(glam[2:]), to(pb[2:]), gr, mask=to(m[2:]))
+    gp = torch.zeros(sim.grad_size, dtype=f64, device="cuda")
+    sim.rates_contract(gr, *scene, gp)
+    gp1 = torch.zeros(sim.grad_size, dtype=f64, device="cuda")
+    sim.rates_bwd(to(glam), to(pb), *scene, gp1, mask=to(m))
+    # oracle: gr[v, d] = sum_t glam_t(v) (1 - m_t(u)) pb_t(u), u = v - Delta_d
+    shp = (T, N, H, W)
+    G = torch.as_tensor(glam.astype(np.float64)).reshape(shp)
+    PB = torch.as_tensor(((1.0 - m.astype(np.float64)) * pb.astype(np.float64))).reshape(shp)
+    ref = torch.stack([(G * prob.shift_from_source(PB, d)).sum(0) for d in range(8)], -1)
+    got = gr.cpu().double().reshape(N, H, W, 8)
+    scale = (G.abs() * prob.shift_from_source(PB.abs(), 0)).sum(0).max()
+    assert torch.allclose(got, ref, rtol=1e-6, atol=1e-6 * float(scale))
+    # contraction: d/dtheta sum_{v,d} gr[v, d] r(v, d; theta) with the GPU's gr
+    C = scenarios.N_CLASSES
+    th = _theta(scn.params, C).float().double().requires_grad_(True)
+    r = prob.rates(torch.as_tensor(scn.cls).long().reshape(N, H, W),
+                   torch.as_tensor(scn.dem.astype(np.float64)).reshape(N, H, W),
+                   torch.as_tensor(scn.wind_speed.astype(np.float64)),
+                   torch.as_tensor(scn.wind_dir.astype(np.float64)), th[0], th[1], th[2], th[3], th[4],
+                   th[6:6 + C], th[6 + C:6 + 2 * C], scn.params.cell_size)
+    (gth,) = torch.autograd.grad((got * r).sum(), [th])
+    rg = torch.cat([gth[0:5], gth[6:]]).numpy()
+    torch.cuda.synchronize()
+    _close(gp.cpu().numpy(), rg)
+    _close(gp1.cpu().numpy(), rg)
 
 
 def test_checkpointing_is_bit_identical():
