@@ -375,7 +375,10 @@ def run_ours(args):
 
 
 def bench_relaxed(args, D, dev, rank):
-    """fwd+bwd of T relaxed steps on 256 x 128^2 with sqrt(T) checkpoints."""
+    """fwd+bwd of T relaxed steps on 256 x 128^2: tiled kernels with every state
+    kept (the default policy when the states fit), then sqrt(T) checkpoints,
+    then the plain kernels (one thread per cell, two-pass adjoint) with sqrt(T)
+    checkpoints as the comparator; T = 1000 with sqrt(T) checkpoints once."""
     import torch
 
     from paper_2512_06102_gb300 import jwf, scenarios
@@ -392,58 +395,100 @@ def bench_relaxed(args, D, dev, rank):
     pu0 = 1.0 - pb0
     target = torch.rand(pu0.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
     stream = torch.cuda.current_stream()
-    ev_f = []
+    cells = REL_ENVS * SIDE * SIDE
 
-    def fwd_bwd():
+    def fwd_bwd(T, ckpt):
         th = theta0.clone().requires_grad_(True)
         pu = pu0.clone().requires_grad_(True)
         pb = pb0.clone().requires_grad_(True)
-        ou, ob = rlx.rollout(th, pu, pb, sim, scene, REL_T)
+        ou, ob = rlx.rollout(th, pu, pb, sim, scene, T, ckpt_every=ckpt)
         loss = ((ou - target) ** 2).mean() + ob.mean()
         loss.backward()
         return th.grad
 
-    # dominant kernel timing: one forward step launch, measured in isolation
-    def time_fwd_kernel(n=20):
-        bufs = [(pu0.clone(), pb0.clone()), (torch.empty_like(pu0), torch.empty_like(pb0))]
-        sim.set_params(rlx.theta_to_params(theta0, sim.n_classes))
-        sim.precompute_probs(*scene)
-        sim.relaxed_fwd(bufs[0][0], bufs[0][1], None, bufs[1][0], bufs[1][1])
+    def timed(T, ckpt, steps, warmup):
+        for _ in range(max(1, warmup)):
+            fwd_bwd(T, ckpt)
+        torch.cuda.synchronize()
+        D.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for i in range(n):
-            src, dst = bufs[i % 2], bufs[(i + 1) % 2]
-            sim.relaxed_fwd(src[0], src[1], None, dst[0], dst[1])
+        for _ in range(steps):
+            fwd_bwd(T, ckpt)
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1e3 / n
+        D.barrier()
+        return D.max(e0.elapsed_time(e1) / 1e3) / steps
 
-    for _ in range(max(1, args.warmup)):
-        fwd_bwd()
-    torch.cuda.synchronize()
-    D.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        fwd_bwd()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    D.barrier()
-    t = D.max(e0.elapsed_time(e1) / 1e3)
-    t_fwd = time_fwd_kernel()
-    cells = REL_ENVS * SIDE * SIDE
+    # the two dominant kernels, timed in isolation over n launches
+    def time_kernels(n=20):
+        sim.set_params(rlx.theta_to_params(theta0, sim.n_classes))
+        sim.precompute_probs(*scene)
+        bufs = [(pu0.clone(), pb0.clone()), (torch.empty_like(pu0), torch.empty_like(pb0))]
+        g = [(torch.randn_like(pu0), torch.randn_like(pu0)), (torch.empty_like(pu0), torch.empty_like(pu0))]
+        glam = torch.empty_like(pu0)
+        gpc = torch.zeros(1, dtype=torch.float64, device=dev)
+        out = {}
+        for name in ("fwd", "bwd"):
+            for i in range(n + 1):
+                if i == 1:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                src, dst = bufs[i % 2], bufs[(i + 1) % 2]
+                if name == "fwd":
+                    sim.relaxed_fwd(src[0], src[1], None, dst[0], dst[1])
+                else:
+                    gs, gd = g[i % 2], g[(i + 1) % 2]
+                    sim.relaxed_bwd(bufs[0][0], bufs[0][1], gs[0], gs[1], None, gd[0], gd[1], glam, gpc)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name] = e0.elapsed_time(e1) / 1e3 / n
+        return out
+
+    sim.set_relaxed_kernel(jwf.RELAXED_TILED)
+    keep_all = rlx.resolve_ckpt(REL_T, cells, None, dev)
+    t_keep = timed(REL_T, None, args.steps, args.warmup)
+    t_sqrt = timed(REL_T, "sqrt", args.steps, args.warmup)
+    t_1000 = timed(1000, "sqrt", 1, 1)
+    k_tiled = time_kernels()
+    sim.set_relaxed_kernel(jwf.RELAXED_PLAIN)
+    t_plain = timed(REL_T, "sqrt", args.steps, args.warmup)
+    k_plain = time_kernels()
+    sim.set_relaxed_kernel(jwf.RELAXED_TILED)
     hbm, peak_kind = peaks()
-    fwd_bytes = 48 * cells
-    ach = fwd_bytes / t_fwd / 1e9
+    fwd_b, bwd_b, acc_b = 48, 60, 16
+    ach_b = bwd_b * cells / k_tiled["bwd"] / 1e9
+    ach_f = fwd_b * cells / k_tiled["fwd"] / 1e9
+    rate = D.world * cells * REL_T / t_keep
     sim.close()
-    return {"metric": "fwd+bwd cell-steps/s at 256x128^2, T=100 (sqrt(T) checkpoints)",
-            "value": D.world * cells * REL_T * args.steps / t, "unit": "fwd+bwd cell-steps/s",
-            "ms_per_step": t / args.steps * 1e3, "dtype": "f32",
-            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(ach / hbm, 4), "peak_source": peak_kind,
-                         "traffic": kernel_traffic("k_relaxed_fwd", "paper_2512_06102_gb300/csrc/k_relaxed.cu"),
-                         "kernel": "k_relaxed_fwd", "kernel_us": round(t_fwd * 1e6, 2),
-                         "bytes_model": "48 B/cell-step (8 B state in, 32 B rates, 8 B state out)"}}
+    return {"metric": "fwd+bwd cell-steps/s at 256x128^2, T=100",
+            "value": rate, "unit": "fwd+bwd cell-steps/s",
+            "ms_per_step": t_keep * 1e3, "dtype": "f32",
+            "memory_policy": "every state kept" if keep_all == 0 else "sqrt(T) checkpoints",
+            "path_bytes_model": f"{fwd_b + bwd_b + acc_b} B/cell-step ({fwd_b} fwd + {bwd_b} fused adjoint + "
+                                f"{acc_b} rate-adjoint accumulation)",
+            "path_gbs": round((fwd_b + bwd_b + acc_b) * rate / D.world / 1e9, 1),
+            "path_frac": round((fwd_b + bwd_b + acc_b) * rate / D.world / 1e9 / hbm, 4),
+            "roofline": {"bound": "hbm", "achieved": round(ach_b, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(ach_b / hbm, 4), "peak_source": peak_kind,
+                         "traffic": kernel_traffic("k_relaxed_bwd_tiled", "paper_2512_06102_gb300/csrc/k_relaxed.cu"),
+                         "kernel": "k_relaxed_bwd_tiled", "kernel_us": round(k_tiled["bwd"] * 1e6, 2),
+                         "bytes_model": "60 B/cell-step (32 B rates, 8 B state, 8 B adjoint in, 8 B adjoint "
+                                        "out, 4 B glam)"},
+            "roofline_fwd": {"bound": "hbm", "achieved": round(ach_f, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(ach_f / hbm, 4), "kernel": "k_relaxed_fwd_tiled",
+                             "kernel_us": round(k_tiled["fwd"] * 1e6, 2),
+                             "bytes_model": "48 B/cell-step (8 B state in, 32 B rates, 8 B state out)"},
+            "sqrt_checkpoints": {"ms_per_step": round(t_sqrt * 1e3, 3),
+                                 "value": D.world * cells * REL_T / t_sqrt},
+            "T1000_sqrt_checkpoints": {"ms_per_step": round(t_1000 * 1e3, 3),
+                                       "value": D.world * cells * 1000 / t_1000},
+            "comparators": {"plain_kernels_sqrt_ms_per_step": round(t_plain * 1e3, 3),
+                            "plain_fwd_us": round(k_plain["fwd"] * 1e6, 2),
+                            "plain_bwd_pair_us": round(k_plain["bwd"] * 1e6, 2),
+                            "speedup_vs_plain": round(t_plain / t_keep, 2),
+                            "speedup_vs_plain_same_checkpoints": round(t_plain / t_sqrt, 2),
+                            "adjoint_speedup_vs_unfused_pair": round(k_plain["bwd"] / k_tiled["bwd"], 2)}}
 
 
 def bench_rollout(args, D, dev, rank):

@@ -251,6 +251,18 @@ JWF_API jwf_status jwf_get_state(jwf_ctx* ctx, uint8_t** d_state, int32_t** d_t,
 
 /* ---- relaxed (raw-probabilities) update, Eqs. 5-10 ----------------------- */
 
+/* Kernels of the relaxed step.  JWF_RELAXED_TILED (default): persistent CTAs
+ * walk 2-D tiles of 16 x 64 cells staged in shared memory by asynchronous
+ * copies (the forward two tiles deep); the adjoint is one kernel that
+ * recomputes lam on a one-cell halo and gathers dL/dp_burn from shared
+ * memory.  Rates whose source lies outside the grid are multiplied by zero
+ * (they must be finite; jwf_precompute_probs writes 0 there).
+ * JWF_RELAXED_PLAIN: one thread per cell; the adjoint is two kernels (lam
+ * adjoint, then the transpose gather) with a round trip of glam through
+ * memory.  Both evaluate the same sums in the same order. */
+enum jwf_relaxed_kernel { JWF_RELAXED_TILED = 0, JWF_RELAXED_PLAIN = 1 };
+JWF_API jwf_status jwf_set_relaxed_kernel(jwf_ctx* ctx, int32_t kernel);
+
 /* One deterministic step on probability planes (float [cells] each; p_bd =
  * 1 - p_un - p_burn is implicit).  With m = d_mask[cell] in [0,1] (float
  * [cells], NULL = 0) the tanker acts first: pb = (1 - m) p_burn.  Then

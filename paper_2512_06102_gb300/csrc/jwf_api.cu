@@ -47,7 +47,7 @@ void free_all(jwf_ctx* c) {
                     c->d_F0, c->d_q, c->d_r, c->d_t, c->d_episode, c->d_cnt, c->d_flag,
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
-                    c->d_tcnt};
+                    c->d_tcnt, c->d_rtiles};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -140,6 +140,12 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
             for (int q = 0; q < tcn; ++q) tiles4.push_back(make_int4(e, r, q, 0));
     }
     c->n_tiles4 = (int64_t)tiles4.size();
+    // 2-D tiles of the relaxed kernels
+    std::vector<int4> rtiles;
+    for (int32_t e = 0; e < N; ++e)
+        for (int y = 0; y < c->H[e]; y += JWF_RT_ROWS)
+            for (int x = 0; x < c->W[e]; x += JWF_RT_COLS) rtiles.push_back(make_int4(e, y, x, 0));
+    c->n_rtiles = (int64_t)rtiles.size();
     // processing order: size class (by the longer side) descending, then
     // cells descending; each class is one resident launch
     auto size_class = [&](int32_t e) {
@@ -183,6 +189,7 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_r, (size_t)c->cells * 8);
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_glam, (size_t)c->cells);
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_gr, (size_t)c->cells * 8);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_rtiles, rtiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_t, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_episode, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_cnt, 2 * (size_t)N);
@@ -204,6 +211,8 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess)
         err = cudaMemcpy(c->d_env_tiles, env_tiles.data(), (size_t)N * sizeof(int4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemset(c->d_tburnt, 0, tiles4.size() * sizeof(int32_t));
+    if (err == cudaSuccess)
+        err = cudaMemcpy(c->d_rtiles, rtiles.data(), rtiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_H, c->H.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_W, c->W.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_off, c->off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -469,6 +478,14 @@ jwf_status jwf_get_state(jwf_ctx* ctx, uint8_t** d_state, int32_t** d_t, int32_t
     if (d_state) *d_state = ctx->d_state[ctx->cur];
     if (d_t) *d_t = ctx->d_t;
     if (d_episode) *d_episode = ctx->d_episode;
+    return JWF_OK;
+}
+
+jwf_status jwf_set_relaxed_kernel(jwf_ctx* ctx, int32_t kernel) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (kernel != JWF_RELAXED_TILED && kernel != JWF_RELAXED_PLAIN)
+        return fail(ctx, JWF_EINVAL, "jwf_set_relaxed_kernel: unknown kernel");
+    ctx->relaxed_kernel = kernel;
     return JWF_OK;
 }
 

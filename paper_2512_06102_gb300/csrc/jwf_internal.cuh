@@ -60,6 +60,9 @@ struct JwfDevParams {
 
 // Per-cell kernels walk blocks of JWF_TILE consecutive cells of one env.
 #define JWF_TILE 256
+// The tiled relaxed kernels walk 2-D tiles of JWF_RT_ROWS x JWF_RT_COLS cells.
+#define JWF_RT_ROWS 16
+#define JWF_RT_COLS 64
 
 // A size class of envs run by one resident launch: envs order[start ..
 // start + count), the largest shape in it, and its block size (0: by size).
@@ -120,6 +123,9 @@ struct jwf_ctx {
     int4* d_tiles4 = nullptr;
     int4* d_env_tiles = nullptr;
     int64_t n_tiles4 = 0;
+    int4* d_rtiles = nullptr;            // (env, first row, first column) per relaxed 2-D tile
+    int64_t n_rtiles = 0;
+    int relaxed_kernel = 0;              // 0: tiled (fused adjoint), 1: plain (two-pass adjoint)
     uint8_t* d_tact[2] = {nullptr, nullptr};
     int tact_cur = 0;
     uint8_t* d_tsync = nullptr;

@@ -171,14 +171,322 @@ k_relaxed_bwd_b(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
     gburn[u] = sat(g);
 }
 
+// ---------------------------------------------------------------------------
+// Tiled variant: 2-D tiles of kRH x kRW cells, staged in shared memory by
+// asynchronous copies.  Each warp covers 32 consecutive cells of a row, so the
+// rate rows (32 B a cell) stream in 1 KB runs.  The adjoint recomputes lam on
+// the tile and a one-cell halo, keeps glam and the rate rows of that region in
+// shared memory (rates transposed to [d][cell] so that the gather reads
+// consecutive words), and gathers dL/dp_burn from there: one kernel, no glam
+// round trip, each rate row read once (plus the halo's).  Sums run over
+// d = 0..7 in the same order as the plain kernels.
+constexpr int kRH = JWF_RT_ROWS, kRW = JWF_RT_COLS;
+
+// cp.async (sm_80+ asynchronous global -> shared copies): the staging of the
+// next tile is in flight while the current one is computed.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Forward: two persistent CTAs per SM walk the tiles, two tiles deep: the
+// copies of the next tile (rate rows and p_un of the tile, p_burn and the
+// mask of the tile and a one-cell halo, zero outside the grid) are in flight
+// while the current one is computed.
+constexpr int kFT = 256;                                   // threads of the forward CTA
+constexpr int kFW = kRW + 2, kFN = (kRH + 2) * kFW;        // tile + 1: pb
+struct FwdStage {
+    float r[kRH * kRW * 8];
+    float pu[kRH * kRW];
+    float pb[kFN], m[kFN];
+};
+struct FwdSmem {
+    FwdStage st[2];
+};
+size_t fwd_smem_bytes() { return sizeof(FwdSmem); }
+
+__device__ __forceinline__ void fwd_stage(FwdStage& b, const int4* __restrict__ tiles, int64_t ti,
+                                          const int32_t* __restrict__ Hs, const int32_t* __restrict__ Ws,
+                                          const int64_t* __restrict__ offs, const float* __restrict__ r,
+                                          const float* __restrict__ pun, const float* __restrict__ pburn,
+                                          const float* __restrict__ mask) {
+    const int4 tl = tiles[ti];
+    const int e = tl.x, y0 = tl.y, x0 = tl.z;
+    const int H = Hs[e], W = Ws[e];
+    const int64_t off = offs[e];
+    for (int i = threadIdx.x; i < kRH * kRW; i += kFT) {
+        const int y = y0 + i / kRW, x = x0 + i % kRW;
+        if (y >= H || x >= W) continue;
+        const int64_t v = off + (int64_t)y * W + x;
+        cp_async16(&b.r[i * 8], r + v * 8);
+        cp_async16(&b.r[i * 8 + 4], r + v * 8 + 4);
+        cp_async4(&b.pu[i], pun + v);
+    }
+    for (int i = threadIdx.x; i < kFN; i += kFT) {
+        const int y = y0 - 1 + i / kFW, x = x0 - 1 + i % kFW;
+        if (y < 0 || y >= H || x < 0 || x >= W) {
+            b.pb[i] = 0.f;
+            b.m[i] = 0.f;
+            continue;
+        }
+        const int64_t v = off + (int64_t)y * W + x;
+        cp_async4(&b.pb[i], pburn + v);
+        if (mask != nullptr)
+            cp_async4(&b.m[i], mask + v);
+        else
+            b.m[i] = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(kFT)
+k_relaxed_fwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32_t* __restrict__ Hs,
+                    const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs,
+                    const float* __restrict__ r, const float* __restrict__ pun,
+                    const float* __restrict__ pburn, const float* __restrict__ mask, float p_continue,
+                    float* __restrict__ pun_out, float* __restrict__ pburn_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
+    int cur = 0;
+    if ((int64_t)blockIdx.x < n_tiles) fwd_stage(S.st[0], tiles, blockIdx.x, Hs, Ws, offs, r, pun, pburn, mask);
+    cp_async_commit();
+    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, cur ^= 1) {
+        if (ti + gridDim.x < n_tiles)
+            fwd_stage(S.st[cur ^ 1], tiles, ti + gridDim.x, Hs, Ws, offs, r, pun, pburn, mask);
+        cp_async_commit();
+        const int4 tl = tiles[ti];
+        const int e = tl.x, y0 = tl.y, x0 = tl.z;
+        const int H = Hs[e], W = Ws[e];
+        const int64_t off = offs[e];
+        cp_async_wait_prev();
+        __syncthreads();
+        FwdStage& b = S.st[cur];
+        if (mask != nullptr) {
+            for (int i = threadIdx.x; i < kFN; i += kFT) b.pb[i] = b.pb[i] * (1.0f - b.m[i]);
+            __syncthreads();
+        }
+        for (int j = threadIdx.x; j < kRH * kRW; j += kFT) {
+            const int ty = j / kRW, tx = j - (j / kRW) * kRW;
+            const int y = y0 + ty, x = x0 + tx;
+            if (y >= H || x >= W) continue;
+            const float4 ra = *reinterpret_cast<const float4*>(&b.r[j * 8]);
+            const float4 rb = *reinterpret_cast<const float4*>(&b.r[j * 8 + 4]);
+            const float rv[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+            float lam = 0.f;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) lam += b.pb[(ty + 1 - jwf_dr(d)) * kFW + (tx + 1 - jwf_dx(d))] * rv[d];
+            const float p_ign = -expm1f(-lam);
+            const float pu = b.pu[j];
+            const float newly = pu * p_ign;
+            const int64_t v = off + (int64_t)y * W + x;
+            pun_out[v] = pu - newly;
+            pburn_out[v] = newly + p_continue * b.pb[(ty + 1) * kFW + tx + 1];
+        }
+        __syncthreads();
+    }
+}
+
+// Adjoint: two persistent CTAs per SM walk the tiles; per tile a CTA stages
+// in shared memory (asynchronous copies) the rate rows, p_un and the incoming
+// adjoints of the tile and a one-cell halo, and p_burn and the mask of a
+// two-cell halo (zero outside the grid, so that a source or target outside
+// the grid contributes nothing and the sums need no bounds tests).  One CTA
+// computes while the other one's copies are in flight.
+constexpr int kBT = 512;                                   // threads of the adjoint CTA
+constexpr int kEW = kRW + 2, kEH = kRH + 2, kEN = kEH * kEW;  // tile + 1: glam and rates
+constexpr int kPW = kRW + 4, kPH = kRH + 4, kPN = kPH * kPW;  // tile + 2: pb
+struct BwdStage {
+    float r[kEN * 8];       // rate rows, [cell][d] as in memory
+    float pu[kEN], au[kEN], ab[kEN];
+    float pb[kPN], m[kPN];  // p_burn and mask; pb becomes (1 - m) p_burn
+};
+struct BwdSmem {
+    BwdStage st;
+    float rt[8][kEN];       // rates transposed for the gather
+    float gl[kEN];
+    double red[kBT / 32];
+};
+size_t bwd_smem_bytes() { return sizeof(BwdSmem); }
+
+__device__ __forceinline__ void bwd_stage(BwdStage& b, const int4* __restrict__ tiles, int64_t ti,
+                                          const int32_t* __restrict__ Hs, const int32_t* __restrict__ Ws,
+                                          const int64_t* __restrict__ offs, const float* __restrict__ r,
+                                          const float* __restrict__ pun, const float* __restrict__ pburn,
+                                          const float* __restrict__ mask, const float* __restrict__ gun_out,
+                                          const float* __restrict__ gburn_out) {
+    const int4 tl = tiles[ti];
+    const int e = tl.x, y0 = tl.y, x0 = tl.z;
+    const int H = Hs[e], W = Ws[e];
+    const int64_t off = offs[e];
+    for (int i = threadIdx.x; i < kEN; i += kBT) {
+        const int y = y0 - 1 + i / kEW, x = x0 - 1 + i % kEW;
+        if (y < 0 || y >= H || x < 0 || x >= W) continue;
+        const int64_t v = off + (int64_t)y * W + x;
+        cp_async16(&b.r[i * 8], r + v * 8);
+        cp_async16(&b.r[i * 8 + 4], r + v * 8 + 4);
+        cp_async4(&b.pu[i], pun + v);
+        cp_async4(&b.au[i], gun_out + v);
+        cp_async4(&b.ab[i], gburn_out + v);
+    }
+    for (int i = threadIdx.x; i < kPN; i += kBT) {
+        const int y = y0 - 2 + i / kPW, x = x0 - 2 + i % kPW;
+        if (y < 0 || y >= H || x < 0 || x >= W) {
+            b.pb[i] = 0.f;
+            b.m[i] = 0.f;
+            continue;
+        }
+        const int64_t v = off + (int64_t)y * W + x;
+        cp_async4(&b.pb[i], pburn + v);
+        if (mask != nullptr)
+            cp_async4(&b.m[i], mask + v);
+        else
+            b.m[i] = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(kBT)
+k_relaxed_bwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32_t* __restrict__ Hs,
+                    const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs,
+                    const float* __restrict__ r, const float* __restrict__ pun,
+                    const float* __restrict__ pburn, const float* __restrict__ mask,
+                    const float* __restrict__ gun_out, const float* __restrict__ gburn_out, float p_continue,
+                    float* __restrict__ gun, float* __restrict__ gburn, float* __restrict__ glam,
+                    double* __restrict__ partials, uint32_t* __restrict__ counter, double* __restrict__ gpc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
+    __shared__ bool am_last;
+    double acc = 0.0;
+    BwdStage& b = S.st;
+    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
+        bwd_stage(b, tiles, ti, Hs, Ws, offs, r, pun, pburn, mask, gun_out, gburn_out);
+        cp_async_commit();
+        const int4 tl = tiles[ti];
+        const int e = tl.x, y0 = tl.y, x0 = tl.z;
+        const int H = Hs[e], W = Ws[e];
+        const int64_t off = offs[e];
+        cp_async_wait_all();
+        __syncthreads();
+        if (mask != nullptr) {
+            for (int i = threadIdx.x; i < kPN; i += kBT) b.pb[i] = b.pb[i] * (1.0f - b.m[i]);
+            __syncthreads();
+        }
+        // glam (and, inside the tile, dL/dp_un) on the tile and its halo
+        for (int i = threadIdx.x; i < kEN; i += kBT) {
+            const int ly = i / kEW, lx = i - (i / kEW) * kEW;
+            const int y = y0 - 1 + ly, x = x0 - 1 + lx;
+            float rv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float g = 0.f;
+            if (y >= 0 && y < H && x >= 0 && x < W) {
+                const float4 ra = *reinterpret_cast<const float4*>(&b.r[i * 8]);
+                const float4 rb = *reinterpret_cast<const float4*>(&b.r[i * 8 + 4]);
+                rv[0] = ra.x; rv[1] = ra.y; rv[2] = ra.z; rv[3] = ra.w;
+                rv[4] = rb.x; rv[5] = rb.y; rv[6] = rb.z; rv[7] = rb.w;
+                const float pu = b.pu[i], au = b.au[i], ab = b.ab[i];
+                float lam = 0.f;
+#pragma unroll
+                for (int d = 0; d < 8; ++d) lam += b.pb[(ly + 1 - jwf_dr(d)) * kPW + (lx + 1 - jwf_dx(d))] * rv[d];
+                const float em = expf(-lam);
+                const float p_ign = -expm1f(-lam);
+                const float nb = ab - au;
+                const float pe = pu * em;
+                g = pe != 0.f ? sat(nb * pe) : 0.f;
+                if (ly >= 1 && ly <= kRH && lx >= 1 && lx <= kRW) {
+                    const int64_t v = off + (int64_t)y * W + x;
+                    gun[v] = sat(p_ign != 0.f ? au + nb * p_ign : au);
+                    glam[v] = g;
+                    const float pbv = b.pb[(ly + 1) * kPW + lx + 1];
+                    if (pbv != 0.f) acc += (double)(ab * pbv);
+                }
+            }
+            S.gl[i] = g;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) S.rt[d][i] = rv[d];
+        }
+        __syncthreads();
+        // dL/dp_burn(u) = (1 - m(u)) (p_continue a_b(u) + sum_d glam(u + Delta_d) r[u + Delta_d][d])
+        for (int j = threadIdx.x; j < kRH * kRW; j += kBT) {
+            const int ty = j / kRW, tx = j - (j / kRW) * kRW;
+            const int y = y0 + ty, x = x0 + tx;
+            if (y >= H || x >= W) continue;
+            const int ei = (ty + 1) * kEW + tx + 1;
+            const float abu = b.ab[ei];
+            float g = p_continue != 0.f ? p_continue * abu : 0.f;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const int li = (ty + 1 + jwf_dr(d)) * kEW + (tx + 1 + jwf_dx(d));
+                const float rv = S.rt[d][li], gl = S.gl[li];
+                if (rv != 0.f && gl != 0.f) g += gl * rv;
+            }
+            if (mask != nullptr) {
+                const float keep = 1.0f - b.m[(ty + 2) * kPW + tx + 2];
+                g = keep != 0.f ? g * keep : 0.f;
+            }
+            gburn[off + (int64_t)y * W + x] = sat(g);
+        }
+        __syncthreads();
+    }
+    if (gpc == nullptr) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kBT / 32; ++w) s += S.red[w];
+        partials[blockIdx.x] = s;
+        __threadfence();
+        am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&partials[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < kBT / 32; ++w) tot += S.red[w];
+        *gpc += tot;
+        *counter = 0u;
+    }
+}
+
 }  // namespace
 
 cudaError_t jwf_launch_relaxed_fwd(const jwf_ctx* c, const float* pun, const float* pburn,
                                    const float* mask, float* pun_out, float* pburn_out,
                                    cudaStream_t s) {
-    k_relaxed_fwd<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(c->d_tiles, c->d_H, c->d_W, c->d_off, c->d_r,
-                                                             pun, pburn, mask, c->P.p_continue, pun_out,
-                                                             pburn_out);
+    if (c->relaxed_kernel == JWF_RELAXED_PLAIN) {
+        k_relaxed_fwd<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(c->d_tiles, c->d_H, c->d_W, c->d_off, c->d_r,
+                                                                 pun, pburn, mask, c->P.p_continue, pun_out,
+                                                                 pburn_out);
+    } else {
+        // two persistent CTAs per SM
+        static int smem_set[64] = {};
+        const size_t smem = fwd_smem_bytes();
+        if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
+        if (!smem_set[c->device]) {
+            const cudaError_t err =
+                cudaFuncSetAttribute(k_relaxed_fwd_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            smem_set[c->device] = 1;
+        }
+        int64_t grid = (int64_t)c->num_sms * 2;
+        if (grid > c->n_rtiles) grid = c->n_rtiles;
+        if (grid < 1) grid = 1;
+        k_relaxed_fwd_tiled<<<(unsigned)grid, kFT, smem, s>>>(c->d_rtiles, c->n_rtiles, c->d_H, c->d_W, c->d_off,
+                                                               c->d_r, pun, pburn, mask, c->P.p_continue, pun_out,
+                                                               pburn_out);
+    }
     return cudaGetLastError();
 }
 
@@ -186,13 +494,35 @@ cudaError_t jwf_launch_relaxed_bwd(jwf_ctx* c, const float* pun, const float* pb
                                    const float* mask, const float* gun_out,
                                    const float* gburn_out, float* gun, float* gburn,
                                    float* glam, double* gpc, cudaStream_t s) {
-    int64_t grid = (int64_t)c->num_sms * 8;
-    if (grid > c->n_tiles) grid = c->n_tiles;
-    if (grid > c->partial_cap) grid = c->partial_cap;
-    k_relaxed_bwd_a<<<(unsigned)grid, JWF_TILE, 0, s>>>(c->d_tiles, c->n_tiles, c->d_H, c->d_W, c->d_off,
-                                                         c->d_r, pun, pburn, mask, gun_out, gburn_out,
-                                                         gun, glam, c->d_partials, c->d_red_counter, gpc);
-    k_relaxed_bwd_b<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(c->d_tiles, c->d_H, c->d_W, c->d_off, c->d_r,
-                                                               mask, gburn_out, glam, c->P.p_continue, gburn);
+    if (c->relaxed_kernel == JWF_RELAXED_PLAIN) {
+        int64_t grid = (int64_t)c->num_sms * 8;
+        if (grid > c->n_tiles) grid = c->n_tiles;
+        if (grid > c->partial_cap) grid = c->partial_cap;
+        k_relaxed_bwd_a<<<(unsigned)grid, JWF_TILE, 0, s>>>(c->d_tiles, c->n_tiles, c->d_H, c->d_W, c->d_off,
+                                                             c->d_r, pun, pburn, mask, gun_out, gburn_out,
+                                                             gun, glam, c->d_partials, c->d_red_counter, gpc);
+        k_relaxed_bwd_b<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(c->d_tiles, c->d_H, c->d_W, c->d_off, c->d_r,
+                                                                   mask, gburn_out, glam, c->P.p_continue,
+                                                                   gburn);
+    } else {
+        // two persistent CTAs per SM
+        static int smem_set[64] = {};
+        const size_t smem = bwd_smem_bytes();
+        if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
+        if (!smem_set[c->device]) {
+            const cudaError_t err =
+                cudaFuncSetAttribute(k_relaxed_bwd_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            smem_set[c->device] = 1;
+        }
+        int64_t grid = (int64_t)c->num_sms * 2;
+        if (grid > c->n_rtiles) grid = c->n_rtiles;
+        if (grid > c->partial_cap) grid = c->partial_cap;
+        if (grid < 1) grid = 1;
+        k_relaxed_bwd_tiled<<<(unsigned)grid, kBT, smem, s>>>(c->d_rtiles, c->n_rtiles, c->d_H, c->d_W, c->d_off,
+                                                            c->d_r, pun, pburn, mask, gun_out, gburn_out,
+                                                            c->P.p_continue, gun, gburn, glam, c->d_partials,
+                                                            c->d_red_counter, gpc);
+    }
     return cudaGetLastError();
 }

@@ -22,6 +22,7 @@ JWF_WIND_PER_CELL = 0x2
 JWF_KEEP_RATES = 0x4
 
 KERNEL_AUTO, KERNEL_PLAIN, KERNEL_RESIDENT, KERNEL_FUSED, KERNEL_TILED, KERNEL_TILED_FUSED = 0, 1, 2, 3, 4, 5
+RELAXED_TILED, RELAXED_PLAIN = 0, 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
           4: "device wait timed out", 5: "call out of order", 6: "unsupported"}
@@ -68,6 +69,7 @@ _SIGS = {
     "jwf_apply_action": (ctypes.c_int, [_VP, _VP, _VP]),
     "jwf_step": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP]),
     "jwf_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int32]),
+    "jwf_set_relaxed_kernel": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "jwf_set_pair_counter": (ctypes.c_int, [_VP, _VP]),
     "jwf_size_classes": (ctypes.c_int32, [_VP, _VP]),
     "jwf_set_class_threads": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
@@ -270,6 +272,9 @@ class Sim:
 
     def set_kernel(self, kernel: int = KERNEL_AUTO, threads_per_env: int = 0):
         self._check(lib().jwf_set_kernel(self._h, int(kernel), int(threads_per_env)), "jwf_set_kernel")
+
+    def set_relaxed_kernel(self, kernel: int = RELAXED_TILED):
+        self._check(lib().jwf_set_relaxed_kernel(self._h, int(kernel)), "jwf_set_relaxed_kernel")
 
     def size_classes(self) -> list:
         buf = (ctypes.c_int32 * 4)()

@@ -11,11 +11,14 @@ raw-probabilities routine).
 theta (float64, any device) = [p_base, alpha_w1, alpha_w2, alpha_s,
 alpha_gamma, p_continue, mu_veg[C], mu_den[C]].
 
-Memory: only the states at every `ckpt_every`-th step are kept by the
-forward; the backward recomputes one segment at a time (default segment
-ceil(sqrt(T)) rounded up to a multiple of CHUNK).  The rate adjoint is
-accumulated on CHUNK-step blocks aligned to absolute step indices, so
-checkpointed and non-checkpointed gradients are bit-identical.
+Memory: `ckpt_every` = 0 keeps every state of the forward (2 x 4 B a cell
+and step) and the backward recomputes nothing; k > 0 keeps the states at
+every k-th step (k rounded up to a multiple of CHUNK) and the backward
+recomputes one segment at a time; "sqrt" takes k = ceil(sqrt(T)); None (the
+default) keeps every state when they take at most a quarter of the free
+device memory, else uses "sqrt".  The rate adjoint is accumulated on
+CHUNK-step blocks aligned to absolute step indices, so the gradients do not
+depend on the choice (bit for bit).
 """
 from __future__ import annotations
 
@@ -28,11 +31,23 @@ from . import jwf
 CHUNK = 8
 
 
-def segment_length(T: int, ckpt_every: int | None) -> int:
-    if ckpt_every is None:
+def segment_length(T: int, ckpt_every) -> int:
+    """Steps per checkpoint segment; T (one segment) when every state is kept."""
+    if ckpt_every == 0:
+        return max(T, 1)
+    if ckpt_every is None or ckpt_every == "sqrt":
         ckpt_every = int(math.ceil(math.sqrt(max(T, 1))))
-    s = max(CHUNK, int(math.ceil(ckpt_every / CHUNK)) * CHUNK)
+    s = max(CHUNK, int(math.ceil(int(ckpt_every) / CHUNK)) * CHUNK)
     return min(s, max(CHUNK, int(math.ceil(T / CHUNK)) * CHUNK))
+
+
+def resolve_ckpt(T: int, cells: int, ckpt_every, device) -> int | str:
+    """The checkpoint policy for a rollout of T steps on `cells` cells."""
+    if ckpt_every is not None:
+        return ckpt_every
+    need = (T + 1) * cells * 2 * 4
+    free, _ = torch.cuda.mem_get_info(device)
+    return 0 if need <= free // 4 else "sqrt"
 
 
 def theta_to_params(theta: torch.Tensor, n_classes: int, cell_size: float = 30.0) -> jwf.ParamSet:
@@ -47,31 +62,45 @@ def theta_to_params(theta: torch.Tensor, n_classes: int, cell_size: float = 30.0
 class RelaxedRollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, p_un0, p_burn0, sim: jwf.Sim, scene, T: int, masks=None,
-                ckpt_every: int | None = None, cell_size: float = 30.0):
+                ckpt_every=None, cell_size: float = 30.0):
         cls, dem, ws, wd = scene
         sim.set_params(theta_to_params(theta, sim.n_classes, cell_size))
         sim.precompute_probs(cls, dem, ws, wd)
+        ckpt_every = resolve_ckpt(T, sim.cells, ckpt_every, p_un0.device)
         seg = segment_length(T, ckpt_every)
         pu, pb = p_un0.contiguous(), p_burn0.contiguous()
-        ckpts = []
-        bu, bb = torch.empty_like(pu), torch.empty_like(pb)
-        for t in range(T):
-            if t % seg == 0:
-                ckpts.append((pu.clone(), pb.clone()))
-            m = None if masks is None else masks[t]
-            sim.relaxed_fwd(pu, pb, m, bu, bb)
-            if t == 0:
-                pu, pb = bu, bb
-                bu, bb = torch.empty_like(pu), torch.empty_like(pb)
-            else:
-                pu, bu = bu, pu
-                pb, bb = bb, pb
+        if ckpt_every == 0:
+            # keep every state: PU[t], PB[t] is the state before step t
+            PU = torch.empty((T + 1, sim.cells), dtype=torch.float32, device=pu.device)
+            PB = torch.empty_like(PU)
+            PU[0].copy_(pu)
+            PB[0].copy_(pb)
+            for t in range(T):
+                sim.relaxed_fwd(PU[t], PB[t], None if masks is None else masks[t], PU[t + 1], PB[t + 1])
+            ctx.ckpts = [(PU, PB)]
+            out_u, out_b = PU[T], PB[T]
+        else:
+            ckpts = []
+            bu, bb = torch.empty_like(pu), torch.empty_like(pb)
+            for t in range(T):
+                if t % seg == 0:
+                    ckpts.append((pu.clone(), pb.clone()))
+                m = None if masks is None else masks[t]
+                sim.relaxed_fwd(pu, pb, m, bu, bb)
+                if t == 0:
+                    pu, pb = bu, bb
+                    bu, bb = torch.empty_like(pu), torch.empty_like(pb)
+                else:
+                    pu, bu = bu, pu
+                    pb, bb = bb, pb
+            ctx.ckpts = ckpts
+            out_u, out_b = pu, pb
         ctx.sim, ctx.scene, ctx.T, ctx.masks, ctx.seg = sim, scene, T, masks, seg
-        ctx.ckpts = ckpts
+        ctx.keep_all = ckpt_every == 0
         ctx.theta_device = theta.device
         ctx.cell_size = cell_size
         ctx.theta = theta.detach().clone()
-        return pu.clone(), pb.clone()
+        return out_u.clone(), out_b.clone()
 
     @staticmethod
     def backward(ctx, g_un, g_burn):
@@ -86,35 +115,39 @@ class RelaxedRollout(torch.autograd.Function):
         gpc = torch.zeros(1, dtype=torch.float64, device=dev)
         gu = (g_un if g_un is not None else torch.zeros(cells, device=dev)).contiguous().clone()
         gb = (g_burn if g_burn is not None else torch.zeros(cells, device=dev)).contiguous().clone()
-        n_seg = len(ctx.ckpts)
-        pu_buf = torch.empty((seg, cells), dtype=torch.float32, device=dev)
-        pb_buf = torch.empty((seg, cells), dtype=torch.float32, device=dev)
-        glam = torch.empty((seg, cells), dtype=torch.float32, device=dev)
+        n_seg = (T + seg - 1) // seg if T > 0 else 0
+        if not ctx.keep_all:
+            pu_buf = torch.empty((seg, cells), dtype=torch.float32, device=dev)
+            pb_buf = torch.empty((seg, cells), dtype=torch.float32, device=dev)
+        glam = torch.empty((CHUNK, cells), dtype=torch.float32, device=dev)
         gr = torch.zeros((cells, 8), dtype=torch.float32, device=dev)     # rate adjoint
-        mk_buf = None if masks is None else torch.empty((seg, cells), dtype=torch.float32, device=dev)
         ngu, ngb = torch.empty_like(gu), torch.empty_like(gb)
         for si in reversed(range(n_seg)):
             a = si * seg
             b = min(a + seg, T)
-            # recompute the states p_a .. p_{b-1} from the checkpoint
-            pu_buf[0].copy_(ctx.ckpts[si][0])
-            pb_buf[0].copy_(ctx.ckpts[si][1])
-            for t in range(a, b - 1):
-                m = None if masks is None else masks[t]
-                sim.relaxed_fwd(pu_buf[t - a], pb_buf[t - a], m, pu_buf[t - a + 1], pb_buf[t - a + 1])
-            if masks is not None:
-                mk_buf[:b - a].copy_(masks[a:b])
-            # adjoint steps in reverse; rate contraction per aligned CHUNK
+            if ctx.keep_all:
+                PU, PB = ctx.ckpts[0]
+                su, sb = PU[a:b], PB[a:b]
+            else:
+                # recompute the states p_a .. p_{b-1} from the checkpoint
+                su, sb = pu_buf, pb_buf
+                su[0].copy_(ctx.ckpts[si][0])
+                sb[0].copy_(ctx.ckpts[si][1])
+                for t in range(a, b - 1):
+                    m = None if masks is None else masks[t]
+                    sim.relaxed_fwd(su[t - a], sb[t - a], m, su[t - a + 1], sb[t - a + 1])
+            # adjoint steps in reverse; the rate adjoint is accumulated per
+            # CHUNK-step block aligned to absolute step indices
             hi = b
             for t in reversed(range(a, b)):
+                lo = (t // CHUNK) * CHUNK
                 m = None if masks is None else masks[t]
-                sim.relaxed_bwd(pu_buf[t - a], pb_buf[t - a], gu, gb, m, ngu, ngb, glam[t - a], gpc)
+                sim.relaxed_bwd(su[t - a], sb[t - a], gu, gb, m, ngu, ngb, glam[t - lo], gpc)
                 gu, ngu = ngu, gu
                 gb, ngb = ngb, gb
-                if t % CHUNK == 0:
-                    lo = t
-                    sim.rates_accumulate(glam[lo - a:hi - a], pb_buf[lo - a:hi - a], gr,
-                                         mask=None if masks is None else mk_buf[lo - a:hi - a])
+                if t == lo:
+                    sim.rates_accumulate(glam[:hi - lo], sb[lo - a:hi - a], gr,
+                                         mask=None if masks is None else masks[lo:hi])
                     hi = lo
             assert hi == a
         sim.rates_contract(gr, cls, dem, ws, wd, gparams)

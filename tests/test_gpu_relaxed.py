@@ -13,6 +13,8 @@
     with dr/dtheta within 1e-4 relative of the oracle's autograd; the one-call
     jwf_rates_bwd agrees with the two halves;
   * checkpointed and non-checkpointed gradients are bit-identical;
+  * the tiled kernels (fused adjoint) and the plain one-thread-per-cell
+    kernels (two-pass adjoint) agree to float rounding on a ragged batch;
   * T = 1000 on the 256 x 128^2 differentiation workload with sqrt(T)
     checkpoints: the parameter gradient of a loss on a sample of envs equals
     the oracle's for those envs, and every map entry is finite (the adjoint
@@ -243,7 +245,7 @@ def test_checkpointing_is_bit_identical():
     sim = make_sim(scn, keep_rates=True)
     scene = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
     grads = []
-    for ck in (8, 16, 24, T):
+    for ck in (0, 8, 16, 24, T, "sqrt"):
         th = _theta(scn.params, scenarios.N_CLASSES).float().double().requires_grad_(True)
         U = to(pu.astype(np.float32)).requires_grad_(True)
         B = to(pb.astype(np.float32)).requires_grad_(True)
@@ -253,6 +255,35 @@ def test_checkpointing_is_bit_identical():
     for g in grads[1:]:
         for a, b in zip(grads[0], g):
             assert torch.equal(a, b)
+
+
+def test_tiled_and_plain_kernels_agree():
+    require_gpu()
+    from paper_2512_06102_gb300 import jwf
+    H = np.array([70, 33, 128, 17], np.int32)
+    W = np.array([66, 150, 64, 5], np.int32)
+    scn = scenarios.make_scenario(H, W, N=4, seed=8)
+    rng = np.random.default_rng(8)
+    pu, pb = _planes(scn, rng)
+    n = pu.size
+    au = to(rng.standard_normal(n).astype(np.float32))
+    ab = to(rng.standard_normal(n).astype(np.float32))
+    m = to((rng.random(n) < 0.05).astype(np.float32) * 0.7)
+    sim = make_sim(scn, keep_rates=True)
+    sim.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    out = {}
+    for kern in (jwf.RELAXED_TILED, jwf.RELAXED_PLAIN):
+        sim.set_relaxed_kernel(kern)
+        ou, ob = sim.relaxed_fwd(to(pu.astype(np.float32)), to(pb.astype(np.float32)), m)
+        gpc = torch.zeros(1, dtype=f64, device="cuda")
+        glam = torch.empty(n, device="cuda")
+        gu, gb = sim.relaxed_bwd(to(pu.astype(np.float32)), to(pb.astype(np.float32)), au, ab, mask=m,
+                                 glam=glam, gpc=gpc)
+        out[kern] = [x.cpu().double() for x in (ou, ob, gu, gb, glam)] + [gpc.cpu()]
+    sim.set_relaxed_kernel(jwf.RELAXED_TILED)
+    for a, b in zip(out[jwf.RELAXED_TILED][:5], out[jwf.RELAXED_PLAIN][:5]):
+        assert torch.allclose(a, b, rtol=1e-6, atol=1e-7 * float(b.abs().max()))
+    assert out[jwf.RELAXED_TILED][5].item() == pytest.approx(out[jwf.RELAXED_PLAIN][5].item(), rel=1e-12)
 
 
 def test_full_size_T1000_sampled():
