@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 N_ENVS, SIDE, EPISODE = 4096, 128, 200
 REL_ENVS, REL_T = 256, 100
 RAG_ENVS, RAG_T, RAG_TMAX = 10000, 500, 200
+BIG_ENVS, BIG_SIDE, BIG_T = 8, 4096, 1000
 METRIC = "CA cell-updates/s at 4096x128^2 (200-step episode with tanker drops)"
 CPU_SAMPLE_ENVS = 48
 # lane-operation model of the step (instruction counts of the work the model
@@ -59,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-rollout", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     return ap.parse_args()
 
 
@@ -343,6 +345,9 @@ def run_ours(args):
     rag = None
     if not args.no_rollout:
         rag = bench_rollout(args, D, dev, rank)
+    big = None
+    if not args.no_large:
+        big = bench_large(args, D, dev, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -367,6 +372,8 @@ def run_ours(args):
         line["relaxed"] = rel
     if rag is not None:
         line["rollout"] = rag
+    if big is not None:
+        line["large"] = big
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -489,6 +496,81 @@ def bench_relaxed(args, D, dev, rank):
                             "speedup_vs_plain": round(t_plain / t_keep, 2),
                             "speedup_vs_plain_same_checkpoints": round(t_plain / t_sqrt, 2),
                             "adjoint_speedup_vs_unfused_pair": round(k_plain["bwd"] / k_tiled["bwd"], 2)}}
+
+
+def bench_large(args, D, dev, rank):
+    """8 grids of 4096 x 4096, one 1000-step episode with a random 3x3 drop per
+    grid and step, on the tiled temporally blocked path: rates evaluated per
+    compared pair (no table), and the table variant with its table build
+    inside the timed region; the plain one-launch-per-step path over 200
+    steps as the comparator."""
+    import torch
+
+    from paper_2512_06102_gb300 import autotune, jwf, scenarios
+
+    scn = scenarios.make_scenario(BIG_SIDE, BIG_SIDE, N=BIG_ENVS, seed=200 + rank)
+    drops = scenarios.drops(BIG_T, scn.H, scn.W, seed=200 + rank)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    scene = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    F0, dr = to(scn.F0), to(drops)
+    sim = jwf.Sim(BIG_SIDE, BIG_SIDE, n_envs=BIG_ENVS, n_classes=scenarios.N_CLASSES, seed=rank)
+    sim.set_params(scn.params)
+    sim.set_terrain(*scene)
+    stream = torch.cuda.current_stream()
+    cells = BIG_ENVS * BIG_SIDE * BIG_SIDE
+
+    def timed(fn, reps):
+        best = float("inf")
+        for _ in range(reps):
+            sim.load_state(F0)
+            torch.cuda.synchronize()
+            D.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, D.max(e0.elapsed_time(e1) / 1e3))
+        return best
+
+    choice = autotune.tune(sim, F0, dr, kernel=jwf.KERNEL_TILED_FUSED, probe_steps=64, use_cache=False)
+    th = int(choice.get("tile_threads", 0))
+    sim.set_kernel(jwf.KERNEL_TILED_FUSED, th)
+    t_fused = timed(lambda: sim.step(BIG_T, dr), max(2, args.steps))
+    cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+    sim.set_pair_counter(cnt)
+    sim.load_state(F0)
+    sim.step(BIG_T, dr)
+    sim.set_pair_counter(None)
+    torch.cuda.synchronize()
+    pairs, blocks, draws, words = [int(x) for x in cnt.tolist()]
+    sim.set_kernel(jwf.KERNEL_TILED, th)
+
+    def table_episode():
+        sim.precompute_probs(*scene)
+        sim.step(BIG_T, dr)
+
+    t_table = timed(table_episode, max(2, args.steps))
+    sim.set_kernel(jwf.KERNEL_PLAIN)
+    t_plain200 = timed(lambda: sim.step(200, dr[:200]), 1)
+    sim.close()
+    best = min(t_fused, t_table)
+    ops = OPS_WORD * words + OPS_PHILOX * (blocks + draws) + OPS_DRAW * (pairs + draws) + OPS_RATE * pairs
+    peak_ops = 152 * 128 * 2.07e9 / 1e12
+    return {"metric": "CA cell-updates/s at 8x4096^2 (1000-step episode with tanker drops)",
+            "value": D.world * cells * BIG_T / best, "unit": "cell-updates/s", "ms_per_episode": round(best * 1e3, 3),
+            "kernel": "tiled table (table build included)" if t_table <= t_fused else "tiled fused",
+            "fused_ms": round(t_fused * 1e3, 3), "table_with_build_ms": round(t_table * 1e3, 3),
+            "round_steps": choice.get("round_steps"), "tile_threads": th,
+            "touched": {"word_steps": words, "cell_steps_scanned": 32 * words,
+                        "fraction_of_cell_steps": round(32 * words / (cells * BIG_T), 4),
+                        "per_touched_cell_rate": 32 * words / t_fused},
+            "roofline_fused": {"bound": "alu", "achieved": round(ops / t_fused / 1e12, 3), "peak": round(peak_ops, 2),
+                               "unit": "T lane-ops/s", "frac": round(ops / t_fused / 1e12 / peak_ops, 4),
+                               "work": {"pairs": pairs, "philox_blocks_candidates": blocks, "burning_draws": draws,
+                                        "word_steps": words}},
+            "comparators": {"plain_one_launch_per_step_ms_per_1000": round(t_plain200 * 5e3, 1),
+                            "speedup_vs_plain": round(t_plain200 * 5 / best, 2)}}
 
 
 def bench_rollout(args, D, dev, rank):

@@ -219,8 +219,10 @@ typedef enum {
                                  JWF_AUTO_RESET only                          */
     JWF_KERNEL_TILED_FUSED = 5 /* tiled, probabilities from the terrain      */
 } jwf_kernel;
-/* Choose the step kernel; threads_per_env = 0 picks a block size by env size,
- * else 32, 64, 128 or 256 threads per env (resident kernels). */
+/* Choose the step kernel; threads_per_env = 0 picks a block size by env size
+ * (resident kernels) or 256 threads a tile (tiled kernels); else 32, 64, 128
+ * or 256 threads per env (resident kernels) or 128, 256 or 512 threads a tile
+ * (tiled kernels).  Other values return JWF_EINVAL. */
 JWF_API jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_env);
 
 /* Resident envs run as up to four size classes by their longer side (<= 64,
@@ -302,6 +304,26 @@ JWF_API jwf_status jwf_rates_bwd(jwf_ctx* ctx, int32_t n_steps, const float* d_g
                          const float* d_pburn, const float* d_mask, const uint8_t* d_class,
                          const float* d_dem, const float* d_wind_speed,
                          const float* d_wind_dir, double* d_gparams, void* stream);
+
+/* n_steps relaxed steps in one call (one kernel launch per step, no host
+ * work in between).  Forward: d_pun_out / d_pburn_out are [n_steps][cells],
+ * row t the state after step t, which starts from row t - 1 (from d_pun /
+ * d_pburn for t = 0); d_masks is [n_steps][cells] or NULL.  The outputs must
+ * not overlap the inputs.  Same requirements as jwf_step_relaxed_fwd. */
+JWF_API jwf_status jwf_relaxed_fwd_steps(jwf_ctx* ctx, int32_t n_steps, const float* d_pun,
+                                         const float* d_pburn, const float* d_masks, float* d_pun_out,
+                                         float* d_pburn_out, void* stream);
+
+/* Adjoint of n_steps (>= 1) steps in reverse order: d_pun / d_pburn are
+ * [n_steps][cells], row t the state before step t; d_gun_out / d_gburn_out
+ * the adjoints of the state after step n_steps - 1; d_gun / d_gburn receive
+ * the adjoints of the state before step 0; d_glam ([n_steps][cells], row t
+ * for step t, or NULL) and d_gpc as in jwf_step_relaxed_bwd.  Uses the
+ * context's adjoint scratch (JWF_KEEP_RATES); outputs must not overlap inputs. */
+JWF_API jwf_status jwf_relaxed_bwd_steps(jwf_ctx* ctx, int32_t n_steps, const float* d_pun,
+                                         const float* d_pburn, const float* d_masks,
+                                         const float* d_gun_out, const float* d_gburn_out, float* d_gun,
+                                         float* d_gburn, float* d_glam, double* d_gpc, void* stream);
 
 /* The two halves of jwf_rates_bwd, for a backward pass that contracts once:
  * jwf_rates_accumulate adds the rate adjoint of n_steps relaxed steps,

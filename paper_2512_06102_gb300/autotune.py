@@ -1,6 +1,6 @@
 """Autotuner for the step kernels: block size per size class (resident path),
-steps per launch of the tiled path, and steps per launch for rollouts whose
-actions are known in advance.
+threads a tile and steps per launch of the tiled path, and steps per launch
+for rollouts whose actions are known in advance.
 
 Each candidate is timed with CUDA events on a short probe of the caller's own
 workload (the Sim, its initial states and drops); the Sim is restored to the
@@ -20,6 +20,7 @@ import torch
 from . import jwf
 
 THREADS = (32, 64, 128, 256)
+TILE_THREADS = (128, 256, 512)
 ROUND_STEPS = (4, 8, 16)
 
 
@@ -45,6 +46,10 @@ def _store_cache(cache: dict):
         os.replace(tmp, p)
     except OSError:
         pass
+
+
+def tiled_kernel(kernel: int) -> bool:
+    return kernel in (jwf.KERNEL_TILED, jwf.KERNEL_TILED_FUSED)
 
 
 def signature(sim: jwf.Sim, kernel: int, probe_steps: int) -> str:
@@ -88,17 +93,19 @@ def tune(sim: jwf.Sim, F0: torch.Tensor, drops: torch.Tensor | None = None, kern
             sim.load_state(F0)
             sim.step(probe_steps, dr)
 
-        choice = {"class_threads": {}, "round_steps": 16}
+        choice = {"class_threads": {}, "round_steps": 16, "tile_threads": 0}
         tiled = kernel in (jwf.KERNEL_TILED, jwf.KERNEL_TILED_FUSED)
         if tiled:
             best = None
-            for rs in ROUND_STEPS:
-                sim.set_round_steps(rs)
-                t = _time(probe)
-                if best is None or t < best[0]:
-                    best = (t, rs)
+            for th in TILE_THREADS:
+                sim.set_kernel(kernel, th)
+                for rs in ROUND_STEPS:
+                    sim.set_round_steps(rs)
+                    t = _time(probe)
+                    if best is None or t < best[0]:
+                        best = (t, rs, th)
             choice["round_steps"] = best[1]
-            sim.set_round_steps(best[1])
+            choice["tile_threads"] = best[2]
         else:
             # coordinate descent over the classes (they run side by side)
             for c in classes:
@@ -116,6 +123,7 @@ def tune(sim: jwf.Sim, F0: torch.Tensor, drops: torch.Tensor | None = None, kern
     for c, th in choice.get("class_threads", {}).items():
         if int(c) in classes:
             sim.set_class_threads(int(c), int(th))
+    sim.set_kernel(kernel, int(choice.get("tile_threads", 0)) if tiled_kernel(kernel) else 0)
     sim.set_round_steps(int(choice.get("round_steps", 16)))
     sim.load_state(F0)
     torch.cuda.synchronize()

@@ -47,7 +47,7 @@ void free_all(jwf_ctx* c) {
                     c->d_F0, c->d_q, c->d_r, c->d_t, c->d_episode, c->d_cnt, c->d_flag,
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
-                    c->d_tcnt, c->d_rtiles};
+                    c->d_tcnt, c->d_rtiles, c->d_adj};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -189,6 +189,7 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_r, (size_t)c->cells * 8);
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_glam, (size_t)c->cells);
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_gr, (size_t)c->cells * 8);
+    if (err == cudaSuccess && rates) err = dev_alloc(&c->d_adj, (size_t)c->cells * 2);
     if (err == cudaSuccess) err = dev_alloc(&c->d_rtiles, rtiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_t, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_episode, N);
@@ -436,8 +437,12 @@ jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_e
     if (ctx == nullptr) return JWF_EINVAL;
     if ((int)kernel < (int)JWF_KERNEL_AUTO || (int)kernel > (int)JWF_KERNEL_TILED_FUSED)
         return fail(ctx, JWF_EINVAL, "jwf_set_kernel: unknown kernel");
-    if (threads_per_env != 0 && (threads_per_env < 32 || threads_per_env > 256 || threads_per_env % 32 != 0))
-        return fail(ctx, JWF_EINVAL, "jwf_set_kernel: threads_per_env must be 0 or a multiple of 32 in [32, 256]");
+    const bool tiled = kernel == JWF_KERNEL_TILED || kernel == JWF_KERNEL_TILED_FUSED;
+    const int t = threads_per_env;
+    if (tiled && !(t == 0 || t == 128 || t == 256 || t == 512))
+        return fail(ctx, JWF_EINVAL, "jwf_set_kernel: tiled kernels take 0, 128, 256 or 512 threads a tile");
+    if (!tiled && !(t == 0 || t == 32 || t == 64 || t == 128 || t == 256))
+        return fail(ctx, JWF_EINVAL, "jwf_set_kernel: threads_per_env must be 0, 32, 64, 128 or 256");
     ctx->kernel = kernel;
     ctx->threads_per_env = threads_per_env;
     return JWF_OK;
@@ -523,6 +528,74 @@ jwf_status jwf_step_relaxed_bwd(jwf_ctx* ctx, const float* d_pun, const float* d
     JWF_CUDA_TRY(ctx, jwf_launch_relaxed_bwd(ctx, d_pun, d_pburn, d_mask, d_gun_out, d_gburn_out, d_gun, d_gburn,
                                              glam, d_gpc, S(stream)),
                  "jwf_step_relaxed_bwd");
+    return JWF_OK;
+}
+
+namespace {
+// [p, p + n) and [q, q + m) overlap (element counts)
+bool overlap(const float* p, int64_t n, const float* q, int64_t m) {
+    return p != nullptr && q != nullptr && p < q + m && q < p + n;
+}
+}  // namespace
+
+jwf_status jwf_relaxed_fwd_steps(jwf_ctx* ctx, int32_t n_steps, const float* d_pun, const float* d_pburn,
+                                 const float* d_masks, float* d_pun_out, float* d_pburn_out, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (n_steps < 0) return fail(ctx, JWF_EINVAL, "jwf_relaxed_fwd_steps: n_steps < 0");
+    if (d_pun == nullptr || d_pburn == nullptr || d_pun_out == nullptr || d_pburn_out == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_relaxed_fwd_steps: null pointer");
+    const int64_t C = ctx->cells, nC = (int64_t)n_steps * C;
+    if (overlap(d_pun_out, nC, d_pun, C) || overlap(d_pun_out, nC, d_pburn, C) ||
+        overlap(d_pburn_out, nC, d_pun, C) || overlap(d_pburn_out, nC, d_pburn, C) ||
+        overlap(d_pun_out, nC, d_pburn_out, nC))
+        return fail(ctx, JWF_EINVAL, "jwf_relaxed_fwd_steps: outputs overlap inputs");
+    if (!ctx->have_params || !ctx->have_rates)
+        return fail(ctx, JWF_ESTATE, "jwf_relaxed_fwd_steps: needs parameters and a rate table");
+    for (int32_t t = 0; t < n_steps; ++t) {
+        const float* iu = t == 0 ? d_pun : d_pun_out + (t - 1) * C;
+        const float* ib = t == 0 ? d_pburn : d_pburn_out + (t - 1) * C;
+        const float* m = d_masks != nullptr ? d_masks + (int64_t)t * C : nullptr;
+        JWF_CUDA_TRY(ctx, jwf_launch_relaxed_fwd(ctx, iu, ib, m, d_pun_out + t * C, d_pburn_out + t * C, S(stream)),
+                     "jwf_relaxed_fwd_steps");
+    }
+    return JWF_OK;
+}
+
+jwf_status jwf_relaxed_bwd_steps(jwf_ctx* ctx, int32_t n_steps, const float* d_pun, const float* d_pburn,
+                                 const float* d_masks, const float* d_gun_out, const float* d_gburn_out,
+                                 float* d_gun, float* d_gburn, float* d_glam, double* d_gpc, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (n_steps < 1) return fail(ctx, JWF_EINVAL, "jwf_relaxed_bwd_steps: n_steps < 1");
+    if (d_pun == nullptr || d_pburn == nullptr || d_gun_out == nullptr || d_gburn_out == nullptr ||
+        d_gun == nullptr || d_gburn == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_relaxed_bwd_steps: null pointer");
+    if (ctx->d_adj == nullptr) return fail(ctx, JWF_EUNSUPPORTED, "jwf_relaxed_bwd_steps: needs JWF_KEEP_RATES");
+    const int64_t C = ctx->cells, nC = (int64_t)n_steps * C;
+    const float* outs[] = {d_gun, d_gburn};
+    for (const float* o : outs)
+        if (overlap(o, C, d_pun, nC) || overlap(o, C, d_pburn, nC) || overlap(o, C, d_masks, nC) ||
+            overlap(o, C, d_gun_out, C) || overlap(o, C, d_gburn_out, C) || overlap(o, C, d_glam, nC))
+            return fail(ctx, JWF_EINVAL, "jwf_relaxed_bwd_steps: outputs overlap inputs");
+    if (overlap(d_gun, C, d_gburn, C) || overlap(d_glam, nC, d_pun, nC) || overlap(d_glam, nC, d_pburn, nC) ||
+        overlap(d_glam, nC, d_gun_out, C) || overlap(d_glam, nC, d_gburn_out, C))
+        return fail(ctx, JWF_EINVAL, "jwf_relaxed_bwd_steps: outputs overlap inputs");
+    if (!ctx->have_params || !ctx->have_rates)
+        return fail(ctx, JWF_ESTATE, "jwf_relaxed_bwd_steps: needs parameters and a rate table");
+    // step t writes its adjoints to the outputs when t is even, else to the
+    // context's scratch, so that step 0 ends in the outputs
+    float* su = ctx->d_adj;
+    float* sb = ctx->d_adj + C;
+    for (int32_t t = n_steps - 1; t >= 0; --t) {
+        const float* iu = t == n_steps - 1 ? d_gun_out : ((t + 1) % 2 == 0 ? d_gun : su);
+        const float* ib = t == n_steps - 1 ? d_gburn_out : ((t + 1) % 2 == 0 ? d_gburn : sb);
+        float* ou = t % 2 == 0 ? d_gun : su;
+        float* ob = t % 2 == 0 ? d_gburn : sb;
+        const float* m = d_masks != nullptr ? d_masks + (int64_t)t * C : nullptr;
+        float* glam = d_glam != nullptr ? d_glam + (int64_t)t * C : ctx->d_glam;
+        JWF_CUDA_TRY(ctx, jwf_launch_relaxed_bwd(ctx, d_pun + t * C, d_pburn + t * C, m, iu, ib, ou, ob, glam, d_gpc,
+                                                 S(stream)),
+                     "jwf_relaxed_bwd_steps");
+    }
     return JWF_OK;
 }
 

@@ -48,6 +48,20 @@ __device__ __forceinline__ uint4 jwf_philox(uint4 c, uint32_t k0, uint32_t k1) {
 // Uniform in [0,1) with 24 random bits; exact in float.
 __device__ __forceinline__ float jwf_u24(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
 
+// cp.async (asynchronous global -> shared copies, completed by groups): the
+// tiled kernels stage the next tile or step while computing the current one.
+__device__ __forceinline__ void jwf_cp_async4(float* dst, const float* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void jwf_cp_async16(float* dst, const float* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void jwf_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void jwf_cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void jwf_cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Parameters as the kernels see them (by value).
 // ---------------------------------------------------------------------------
@@ -108,6 +122,7 @@ struct jwf_ctx {
     int64_t partial_cap = 0;             // doubles available in d_partials
     uint32_t* d_red_counter = nullptr;   // blocks finished (last-block reduction)
     float* d_glam = nullptr;             // [cells] adjoint scratch of the relaxed step
+    float* d_adj = nullptr;              // [2][cells] adjoint ping-pong of the multi-step relaxed adjoint
     float* d_gr = nullptr;               // [cells][8] rate-adjoint scratch of jwf_rates_bwd
     unsigned long long* d_pairs = nullptr;  // caller's instrumentation counter (not owned)
     float2* d_wexp = nullptr;            // [N][8] wind exponent (hi, lo) scratch of the table build
@@ -126,7 +141,7 @@ struct jwf_ctx {
     int4* d_rtiles = nullptr;            // (env, first row, first column) per relaxed 2-D tile
     int64_t n_rtiles = 0;
     int relaxed_kernel = 0;              // 0: tiled (fused adjoint), 1: plain (two-pass adjoint)
-    uint8_t* d_tact[2] = {nullptr, nullptr};
+    uint16_t* d_tact[2] = {nullptr, nullptr};
     int tact_cur = 0;
     uint8_t* d_tsync = nullptr;
     int32_t* d_tburnt = nullptr;

@@ -160,47 +160,102 @@ constexpr int kRbScalars = 5;   // p_base, alpha_w1, alpha_w2, alpha_s, alpha_ga
 
 // Rate adjoint of a chunk of relaxed steps: gr[v][d] += sum_t glam_t(v) pb_t(v - Delta_d)
 // (pb = (1 - m) p_burn), summed over the chunk in step order, then added once.
-__global__ void __launch_bounds__(JWF_TILE)
-k_rates_accumulate(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
-                   const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs, int64_t cells,
-                   int32_t n_steps, const float* __restrict__ glam, const float* __restrict__ pburn,
+// Rate adjoint of a block of steps, on the 2-D tiles of the relaxed step:
+//   gr[v][d] += sum_t glam_t(v) pb_t(v - Delta_d),  pb = (1 - m) p_burn,
+// each thread summing four cells of the tile over the steps in registers (in
+// step order, skipping zero factors) and updating gr once.  Step t + 1's
+// p_burn and mask (tile and a one-cell halo, zero outside the grid) and glam
+// (tile) are copied to shared memory while step t is summed.
+constexpr int kAccT = 256;
+constexpr int kAccRows = JWF_RT_ROWS, kAccCols = JWF_RT_COLS;
+constexpr int kAccW = kAccCols + 2, kAccN = (kAccRows + 2) * kAccW;
+constexpr int kAccCPT = kAccRows * kAccCols / kAccT;       // cells a thread
+constexpr int kAccRowStep = kAccT / kAccCols;              // rows between a thread's cells
+struct AccStage {
+    float pb[kAccN], m[kAccN];
+    float gl[kAccRows * kAccCols];
+};
+
+__device__ __forceinline__ void acc_stage(AccStage& b, int y0, int x0, int H, int W, int64_t off, int64_t base,
+                                          const float* __restrict__ glam, const float* __restrict__ pburn,
+                                          const float* __restrict__ mask) {
+    for (int i = threadIdx.x; i < kAccN; i += kAccT) {
+        const int y = y0 - 1 + i / kAccW, x = x0 - 1 + i % kAccW;
+        if (y < 0 || y >= H || x < 0 || x >= W) {
+            b.pb[i] = 0.f;
+            b.m[i] = 0.f;
+            continue;
+        }
+        const int64_t u = base + off + (int64_t)y * W + x;
+        jwf_cp_async4(&b.pb[i], pburn + u);
+        if (mask != nullptr)
+            jwf_cp_async4(&b.m[i], mask + u);
+        else
+            b.m[i] = 0.f;
+    }
+    for (int i = threadIdx.x; i < kAccRows * kAccCols; i += kAccT) {
+        const int y = y0 + i / kAccCols, x = x0 + i % kAccCols;
+        if (y < H && x < W) jwf_cp_async4(&b.gl[i], glam + base + off + (int64_t)y * W + x);
+    }
+}
+
+__global__ void __launch_bounds__(kAccT)
+k_rates_accumulate(const int4* __restrict__ tiles, const int32_t* __restrict__ Hs, const int32_t* __restrict__ Ws,
+                   const int64_t* __restrict__ offs, int64_t cells, int32_t n_steps,
+                   const float* __restrict__ glam, const float* __restrict__ pburn,
                    const float* __restrict__ mask, float* __restrict__ gr) {
-    const int2 tile = tiles[blockIdx.x];
-    const int e = tile.x;
-    const int W = Ws[e], H = Hs[e];
-    const int local = tile.y + (int)threadIdx.x;
-    if (local >= H * W) return;
+    __shared__ __align__(16) AccStage st[2];
+    const int4 tl = tiles[blockIdx.x];
+    const int e = tl.x, y0 = tl.y, x0 = tl.z;
+    const int H = Hs[e], W = Ws[e];
     const int64_t off = offs[e];
-    const int y = local / W, x = local - (local / W) * W;
-    const int64_t v = off + local;
-    float w[8];
+    const int tx = (int)threadIdx.x % kAccCols, ty = (int)threadIdx.x / kAccCols;
+    float w[kAccCPT][8];
 #pragma unroll
-    for (int d = 0; d < 8; ++d) w[d] = 0.f;
+    for (int k = 0; k < kAccCPT; ++k)
+#pragma unroll
+        for (int d = 0; d < 8; ++d) w[k][d] = 0.f;
     bool any = false;
+    acc_stage(st[0], y0, x0, H, W, off, 0, glam, pburn, mask);
+    jwf_cp_async_commit();
     for (int t = 0; t < n_steps; ++t) {
-        const int64_t base = (int64_t)t * cells;
-        const float g = glam[base + v];
-        if (g == 0.f) continue;
+        if (t + 1 < n_steps)
+            acc_stage(st[(t + 1) & 1], y0, x0, H, W, off, (int64_t)(t + 1) * cells, glam, pburn, mask);
+        jwf_cp_async_commit();
+        jwf_cp_async_wait_prev();
+        __syncthreads();
+        AccStage& b = st[t & 1];
 #pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            const int uy = y - jwf_dr(d), ux = x - jwf_dx(d);
-            if (uy < 0 || uy >= H || ux < 0 || ux >= W) continue;
-            const int64_t u = off + (int64_t)uy * W + ux;
-            float pb = pburn[base + u];
-            if (mask != nullptr) pb *= 1.0f - mask[base + u];
-            if (pb != 0.f) {
-                w[d] += g * pb;
-                any = true;
+        for (int k = 0; k < kAccCPT; ++k) {
+            const int ly = ty + k * kAccRowStep;
+            if (y0 + ly >= H || x0 + tx >= W) continue;
+            const float g = b.gl[ly * kAccCols + tx];
+            if (g == 0.f) continue;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const int li = (ly + 1 - jwf_dr(d)) * kAccW + (tx + 1 - jwf_dx(d));
+                float pb = b.pb[li];
+                if (mask != nullptr) pb *= 1.0f - b.m[li];
+                if (pb != 0.f) {
+                    w[k][d] += g * pb;
+                    any = true;
+                }
             }
         }
+        __syncthreads();
     }
     if (!any) return;
-    float4* g4 = reinterpret_cast<float4*>(gr + v * 8);
-    float4 a = g4[0], b = g4[1];
-    a.x += w[0]; a.y += w[1]; a.z += w[2]; a.w += w[3];
-    b.x += w[4]; b.y += w[5]; b.z += w[6]; b.w += w[7];
-    g4[0] = a;
-    g4[1] = b;
+#pragma unroll
+    for (int k = 0; k < kAccCPT; ++k) {
+        const int y = y0 + ty + k * kAccRowStep, x = x0 + tx;
+        if (y >= H || x >= W) continue;
+        float4* g4 = reinterpret_cast<float4*>(gr + (off + (int64_t)y * W + x) * 8);
+        float4 a = g4[0], c = g4[1];
+        a.x += w[k][0]; a.y += w[k][1]; a.z += w[k][2]; a.w += w[k][3];
+        c.x += w[k][4]; c.y += w[k][5]; c.z += w[k][6]; c.w += w[k][7];
+        g4[0] = a;
+        g4[1] = c;
+    }
 }
 
 // Parameter gradient through the rates.  Per target cell v and direction d
@@ -412,8 +467,8 @@ cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const fl
 
 cudaError_t jwf_launch_rates_accumulate(const jwf_ctx* c, int32_t n_steps, const float* glam,
                                         const float* pburn, const float* mask, float* gr, cudaStream_t s) {
-    k_rates_accumulate<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(c->d_tiles, c->d_H, c->d_W, c->d_off, c->cells,
-                                                                  n_steps, glam, pburn, mask, gr);
+    k_rates_accumulate<<<(unsigned)c->n_rtiles, kAccT, 0, s>>>(c->d_rtiles, c->d_H, c->d_W, c->d_off, c->cells,
+                                                                n_steps, glam, pburn, mask, gr);
     return cudaGetLastError();
 }
 

@@ -182,19 +182,6 @@ k_relaxed_bwd_b(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
 // d = 0..7 in the same order as the plain kernels.
 constexpr int kRH = JWF_RT_ROWS, kRW = JWF_RT_COLS;
 
-// cp.async (sm_80+ asynchronous global -> shared copies): the staging of the
-// next tile is in flight while the current one is computed.
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Forward: two persistent CTAs per SM walk the tiles, two tiles deep: the
 // copies of the next tile (rate rows and p_un of the tile, p_burn and the
@@ -225,9 +212,9 @@ __device__ __forceinline__ void fwd_stage(FwdStage& b, const int4* __restrict__ 
         const int y = y0 + i / kRW, x = x0 + i % kRW;
         if (y >= H || x >= W) continue;
         const int64_t v = off + (int64_t)y * W + x;
-        cp_async16(&b.r[i * 8], r + v * 8);
-        cp_async16(&b.r[i * 8 + 4], r + v * 8 + 4);
-        cp_async4(&b.pu[i], pun + v);
+        jwf_cp_async16(&b.r[i * 8], r + v * 8);
+        jwf_cp_async16(&b.r[i * 8 + 4], r + v * 8 + 4);
+        jwf_cp_async4(&b.pu[i], pun + v);
     }
     for (int i = threadIdx.x; i < kFN; i += kFT) {
         const int y = y0 - 1 + i / kFW, x = x0 - 1 + i % kFW;
@@ -237,9 +224,9 @@ __device__ __forceinline__ void fwd_stage(FwdStage& b, const int4* __restrict__ 
             continue;
         }
         const int64_t v = off + (int64_t)y * W + x;
-        cp_async4(&b.pb[i], pburn + v);
+        jwf_cp_async4(&b.pb[i], pburn + v);
         if (mask != nullptr)
-            cp_async4(&b.m[i], mask + v);
+            jwf_cp_async4(&b.m[i], mask + v);
         else
             b.m[i] = 0.f;
     }
@@ -255,16 +242,16 @@ k_relaxed_fwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32
     FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw);
     int cur = 0;
     if ((int64_t)blockIdx.x < n_tiles) fwd_stage(S.st[0], tiles, blockIdx.x, Hs, Ws, offs, r, pun, pburn, mask);
-    cp_async_commit();
+    jwf_cp_async_commit();
     for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, cur ^= 1) {
         if (ti + gridDim.x < n_tiles)
             fwd_stage(S.st[cur ^ 1], tiles, ti + gridDim.x, Hs, Ws, offs, r, pun, pburn, mask);
-        cp_async_commit();
+        jwf_cp_async_commit();
         const int4 tl = tiles[ti];
         const int e = tl.x, y0 = tl.y, x0 = tl.z;
         const int H = Hs[e], W = Ws[e];
         const int64_t off = offs[e];
-        cp_async_wait_prev();
+        jwf_cp_async_wait_prev();
         __syncthreads();
         FwdStage& b = S.st[cur];
         if (mask != nullptr) {
@@ -328,11 +315,11 @@ __device__ __forceinline__ void bwd_stage(BwdStage& b, const int4* __restrict__ 
         const int y = y0 - 1 + i / kEW, x = x0 - 1 + i % kEW;
         if (y < 0 || y >= H || x < 0 || x >= W) continue;
         const int64_t v = off + (int64_t)y * W + x;
-        cp_async16(&b.r[i * 8], r + v * 8);
-        cp_async16(&b.r[i * 8 + 4], r + v * 8 + 4);
-        cp_async4(&b.pu[i], pun + v);
-        cp_async4(&b.au[i], gun_out + v);
-        cp_async4(&b.ab[i], gburn_out + v);
+        jwf_cp_async16(&b.r[i * 8], r + v * 8);
+        jwf_cp_async16(&b.r[i * 8 + 4], r + v * 8 + 4);
+        jwf_cp_async4(&b.pu[i], pun + v);
+        jwf_cp_async4(&b.au[i], gun_out + v);
+        jwf_cp_async4(&b.ab[i], gburn_out + v);
     }
     for (int i = threadIdx.x; i < kPN; i += kBT) {
         const int y = y0 - 2 + i / kPW, x = x0 - 2 + i % kPW;
@@ -342,9 +329,9 @@ __device__ __forceinline__ void bwd_stage(BwdStage& b, const int4* __restrict__ 
             continue;
         }
         const int64_t v = off + (int64_t)y * W + x;
-        cp_async4(&b.pb[i], pburn + v);
+        jwf_cp_async4(&b.pb[i], pburn + v);
         if (mask != nullptr)
-            cp_async4(&b.m[i], mask + v);
+            jwf_cp_async4(&b.m[i], mask + v);
         else
             b.m[i] = 0.f;
     }
@@ -365,12 +352,12 @@ k_relaxed_bwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32
     BwdStage& b = S.st;
     for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
         bwd_stage(b, tiles, ti, Hs, Ws, offs, r, pun, pburn, mask, gun_out, gburn_out);
-        cp_async_commit();
+        jwf_cp_async_commit();
         const int4 tl = tiles[ti];
         const int e = tl.x, y0 = tl.y, x0 = tl.z;
         const int H = Hs[e], W = Ws[e];
         const int64_t off = offs[e];
-        cp_async_wait_all();
+        jwf_cp_async_wait_all();
         __syncthreads();
         if (mask != nullptr) {
             for (int i = threadIdx.x; i < kPN; i += kBT) b.pb[i] = b.pb[i] * (1.0f - b.m[i]);

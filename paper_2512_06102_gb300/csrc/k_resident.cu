@@ -206,6 +206,25 @@ __device__ __forceinline__ bool ignites(const Args& a, int e, int64_t off, uint3
     return ign;
 }
 
+// Fused variant, one (target, source) pair: does the burning source in
+// direction d ignite can-burn cell (yy, xx) of env e this step?  The rate of
+// Eqs. 1-4 is evaluated on the spot (rate_model.cuh, as the table kernel does)
+// and compared with the Philox word of that direction.
+template <class Args>
+__device__ __forceinline__ bool pair_ignites(const Args& a, const RateConsts& K, int e, int64_t off, int W, int yy,
+                                             int xx, int d, uint32_t tt, uint32_t ep4) {
+    const uint32_t cell = (uint32_t)(yy * W + xx);
+    const int64_t v = off + cell;
+    const int64_t u = off + (int64_t)(yy - jwf_dr(d)) * W + (xx - jwf_dx(d));
+    const int cv = a.cls[v], cu = a.cls[u];
+    const float zv = a.dem[v], zu = a.dem[u];
+    const float2 w2 = a.wexp[e * 8 + d];
+    const uint4 u4 = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + (uint32_t)(d >> 2)), a.key0, a.key1);
+    const uint32_t uw = (d & 3) == 0 ? u4.x : (d & 3) == 1 ? u4.y : (d & 3) == 2 ? u4.z : u4.w;
+    const float r = rate_of(K.G[cv][cu], zv, zu, {w2.x, w2.y}, d, K);
+    return jwf_u24(uw) < prob_of(r);
+}
+
 // Fused variant: the candidate cells of list[it0 .. it0+32) are flattened
 // into (cell, direction) pairs, one pair per lane per round, so the rate code
 // of Eqs. 1-4 runs once per pair rather than once per direction present in
@@ -241,16 +260,7 @@ __device__ __forceinline__ void fused_pairs(const Args& a, const RateConsts& K, 
         const int ry = ii / WW;
         const int yy = oy + ry;
         const int xx = ox + ((ii - ry * WW) << 5) + j;
-        const uint32_t cell = (uint32_t)(yy * W + xx);
-        const int64_t v = off + cell;
-        const int64_t u = off + (int64_t)(yy - jwf_dr(d)) * W + (xx - jwf_dx(d));
-        const int cv = a.cls[v], cu = a.cls[u];
-        const float zv = a.dem[v], zu = a.dem[u];
-        const float2 w2 = a.wexp[e * 8 + d];
-        const uint4 u4 = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + (uint32_t)(d >> 2)), a.key0, a.key1);
-        const uint32_t uw = (d & 3) == 0 ? u4.x : (d & 3) == 1 ? u4.y : (d & 3) == 2 ? u4.z : u4.w;
-        const float r = rate_of(K.G[cv][cu], zv, zu, {w2.x, w2.y}, d, K);
-        if (jwf_u24(uw) < prob_of(r)) atomicOr(&ignw[ol], 1u << j);
+        if (pair_ignites(a, K, e, off, W, yy, xx, d, tt, ep4)) atomicOr(&ignw[ol], 1u << j);
     }
     __syncwarp();
 }
@@ -565,13 +575,21 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
 // the grid read as no fuel), runs kb steps over the whole region (halo cells
 // are recomputed redundantly; after s steps the outer s cells of the region
 // are stale, never the interior), then writes the interior to the other state
-// buffer.  A tile none of whose 3x3 neighbour tiles held a burning cell after
-// the previous round cannot change this round: it copies its interior to the
-// other buffer once and otherwise only reports its counts.
+// buffer.  A tile that holds no burning cell, and none of whose eight
+// neighbours holds one within kMaxRound cells of the side or corner they
+// share, cannot change this round: it copies its interior to the other buffer
+// once and otherwise only reports its counts.
 // ---------------------------------------------------------------------------
-constexpr int kTileRows = 128, kTileCols = 256, kMaxRound = 16;
+constexpr int kTileRows = 64, kTileCols = 128, kMaxRound = 16;
 constexpr int kRegionRows = kTileRows + 2 * kMaxRound;
 constexpr int kRegionWords = kTileCols / 32 + 2;
+// chunk flag bytes of one burning buffer (a chunk is 32 words), rounded to words
+constexpr int kRegionWordsAll = kRegionRows * kRegionWords;
+constexpr int kRegionChunks = (kRegionWordsAll + 31) / 32;
+constexpr int kTileFlagBytes = (kRegionChunks + 3) / 4 * 4;
+// block-wide queue of the step's work items (burning-cell draws and compared
+// pairs); a chunk whose items do not fit is evaluated by its own warp
+constexpr int kQCap = 4096;
 
 struct TileArgs {
     const int32_t* H;
@@ -590,8 +608,8 @@ struct TileArgs {
     const int32_t* t;            // step counters at the start of the round
     const int32_t* episode;
     int32_t* cnt;                // [kb][2][N] per-step counts (zeroed before the round)
-    const uint8_t* act_in;       // [tiles] a burning interior cell after the last round
-    uint8_t* act_out;
+    const uint16_t* act_in;      // [tiles] where the last round left burning cells (kAct* bits)
+    uint16_t* act_out;
     uint8_t* synced;             // [tiles] both buffers hold this tile's interior
     int32_t* tile_burnt;         // [tiles] burned interior cells after the last round
     unsigned long long* counts;
@@ -602,8 +620,11 @@ struct TileArgs {
 };
 
 size_t tiled_smem_bytes(int threads) {
-    return (size_t)(2 * (kRegionRows + 2) * kRegionWords + 2 * kRegionRows * kRegionWords +
-                    (threads / 32) * kWarpScratch) * sizeof(uint32_t);
+    // planes, warp scratch, chunk flags, ignition and burn-out planes, queue,
+    // per-warp claimed-chunk lists
+    return (size_t)(2 * (kRegionRows + 2) * kRegionWords + 2 * kRegionWordsAll + (threads / 32) * kWarpScratch +
+                    2 * kTileFlagBytes / 4 + 2 * kRegionWordsAll + kQCap + (threads / 32) * kRegionChunks) *
+           sizeof(uint32_t);
 }
 
 // Region-relative drops: the centre (cx, cy) may lie outside the region (even
@@ -635,6 +656,15 @@ __device__ void res_action_rel(int RH, int WW, uint32_t* Bp, uint32_t* D, int cx
     }
 }
 
+// Tile activity after a round: kActAny = a burning interior cell; the other
+// bits = a burning interior cell within kMaxRound cells of an edge (N, S, W,
+// E) or of both edges at a corner.  Fire moves at most one cell a step, so in
+// a round of kb <= kMaxRound steps a tile's interior can change only if it
+// holds a burning cell or a neighbour holds one within kMaxRound cells of
+// the side or corner they share.
+constexpr uint16_t kActN = 1, kActS = 2, kActW = 4, kActE = 8, kActNW = 16, kActNE = 32, kActSW = 64,
+                   kActSE = 128, kActAny = 256;
+
 // bits of region word w inside the column range [c0, c1) of the region
 __device__ __forceinline__ uint32_t col_bits(int w, int c0, int c1) {
     const int lo = max(c0 - (w << 5), 0), hi = min(c1 - (w << 5), 32) - 1;
@@ -647,8 +677,13 @@ template <int NT, bool FUSED>
 __global__ void __launch_bounds__(NT)
 k_step_tiled(const TileArgs a, const RateConsts Kc) {
     extern __shared__ uint32_t sm[];
-    __shared__ int32_t s_cnt[3][3];     // interior burning, interior burned, region burning
+    // per step: interior burning, interior burn-outs, interior cells doused by
+    // the next step's drop, region burning
+    __shared__ int32_t s_cnt[3][4];
     __shared__ int32_t s_chunk[3];
+    __shared__ int32_t s_d0;
+    __shared__ uint32_t s_act;
+    __shared__ int32_t s_qn[3];
     __shared__ int s_active;
     __shared__ typename std::conditional<FUSED, RateConsts, int>::type sK_store;
     const RateConsts& sK = *reinterpret_cast<const RateConsts*>(&sK_store);
@@ -663,11 +698,14 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     const int TY = min(kTileRows, H - ty0), TX = min(kTileCols, W - tx0);
     const int kb = a.kb;
     if (threadIdx.x == 0) {
+        // the bit of neighbour (dy, dx) that faces this tile
+        constexpr uint16_t facing[3][3] = {{kActSE, kActS, kActSW}, {kActE, kActAny, kActW}, {kActNE, kActN, kActNW}};
         int act = 0;
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
                 const int r = tr + dy, c = tc + dx;
-                if (r >= 0 && r < et.z && c >= 0 && c < et.y) act |= a.act_in[et.x + r * et.y + c];
+                if (r >= 0 && r < et.z && c >= 0 && c < et.y)
+                    act |= (a.act_in[et.x + r * et.y + c] & facing[dy + 1][dx + 1]) != 0;
             }
         s_active = act;
     }
@@ -706,8 +744,25 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     uint32_t* ignw = list + kListCap;
     uint32_t* outw = ignw + 32;
     uint32_t* plist = outw + 32;
+    // chunk activity flags of the two burning buffers (as in the resident step)
+    uint8_t* fl_c = reinterpret_cast<uint8_t*>(D + words + (NT / 32) * kWarpScratch);
+    uint8_t* fl_n = fl_c + kTileFlagBytes;
+    uint32_t* IG = reinterpret_cast<uint32_t*>(fl_c + 2 * kTileFlagBytes);   // ignitions this step
+    uint32_t* OU = IG + kRegionWordsAll;                                      // burn-outs this step
+    uint32_t* Q = OU + kRegionWordsAll;
+    int* wch = reinterpret_cast<int*>(Q + kQCap) + warp * kRegionChunks;     // chunks this warp claimed
+    const int reach = (WW + 1 + 31) >> 5;
     for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
-    if (threadIdx.x < 9) s_cnt[threadIdx.x / 3][threadIdx.x % 3] = 0;
+    for (int i = threadIdx.x; i < words; i += NT) {
+        IG[i] = 0u;
+        OU[i] = 0u;
+    }
+    if (threadIdx.x < 3) s_qn[threadIdx.x] = 0;
+    if (threadIdx.x < 12) s_cnt[threadIdx.x / 4][threadIdx.x % 4] = 0;
+    if (threadIdx.x == 0) {
+        s_d0 = 0;
+        s_act = 0u;
+    }
     if (threadIdx.x < 3) s_chunk[threadIdx.x] = 0;
     ignw[lane] = 0u;
     outw[lane] = 0u;
@@ -750,6 +805,24 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         res_action_rel(RH, WW, B0, D, gcx - ox, gcy - oy, a.R, gcx >= 0 && gcy >= 0);
         __syncthreads();
     }
+    // initial chunk flags and burned interior cells (after the round's first drop)
+    {
+        int nd0 = 0;
+        for (int c = threadIdx.x; c < nchunks; c += NT) {
+            uint32_t any = 0u;
+            const int i1 = min(words, (c + 1) << 5);
+            for (int i = c << 5; i < i1; ++i) {
+                any |= B0[WW + i];
+                const int y = i / WW, w = i - (i / WW) * WW;
+                if (y >= kb && y < kb + TY) nd0 += __popc(D[i] & col_bits(w, 32, 32 + TX));
+            }
+            fl_c[c] = any != 0u;
+            fl_n[c] = 0;
+        }
+        if (nd0) atomicAdd(&s_d0, nd0);
+    }
+    __syncthreads();
+    int32_t dbase = s_d0;
     int32_t t0 = a.t[e];
     const uint32_t ep4 = 4u * (uint32_t)a.episode[e];
     uint32_t* Bc = B0;
@@ -761,7 +834,9 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             s_cnt[(s + 1) % 3][0] = 0;
             s_cnt[(s + 1) % 3][1] = 0;
             s_cnt[(s + 1) % 3][2] = 0;
+            s_cnt[(s + 1) % 3][3] = 0;
             s_chunk[(s + 1) % 3] = 0;
+            s_qn[(s + 1) % 3] = 0;
         }
         bool hasn = false;
         int cxn = 0, cyn = 0;
@@ -772,21 +847,30 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             cxn = gcx - ox;
             cyn = gcy - oy;
         }
-        int my_b = 0, my_d = 0, my_r = 0;
-        uint32_t my_pairs = 0, my_blocks = 0, my_burn = 0;
+        int my_b = 0, my_o = 0, my_x = 0, my_r = 0;
+        uint32_t my_pairs = 0, my_blocks = 0, my_burn = 0, my_chunks = 0;
+        // phase A: warps claim the chunks that can change and queue their work
+        // items (one per burning cell; one per compared pair in the fused
+        // variant, one per candidate cell in the table variant)
         for (;;) {
             int c = 0;
             if (lane == 0) c = atomicAdd(&s_chunk[s % 3], 1);
             c = __shfl_sync(0xffffffffu, c, 0);
             if (c >= nchunks) break;
+            // a chunk with no burning cell within reach, whose write buffer
+            // holds no burning word, cannot change: skip it
+            bool need = fl_n[c] != 0;
+            for (int cc = max(c - reach, 0); cc <= min(c + reach, nchunks - 1) && !need; ++cc)
+                need = fl_c[cc] != 0;
+            if (!need) continue;
+            if (lane == 0) wch[my_chunks] = c;
+            ++my_chunks;
             const int base = c << 5;
             const int i = base + lane;
             uint32_t burn = 0, cand = 0;
             uint32_t sd[8];
-            int y = 0, w = 0;
             if (i < words) {
-                y = i / WW;
-                w = i - y * WW;
+                const int w = i - (i / WW) * WW;
                 const uint32_t* bp = &Bc[WW + i];
                 const bool hl = w > 0, hr = w + 1 < WW;
                 const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
@@ -807,85 +891,161 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
 #pragma unroll
                 for (int d = 0; d < 8; ++d) sd[d] = 0u;
             }
-            const uint32_t act = cand | burn;
-            if (__ballot_sync(0xffffffffu, act != 0u) != 0u) {
-                const int n_act = __popc(act);
-                int incl = n_act;
+            uint32_t np = 0;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                const int excl = incl - n_act;
-                for (int pass = 0; pass < total; pass += kListCap) {
-                    uint32_t rem = act;
-                    int idx = excl;
-                    while (rem != 0u) {
-                        const int j = __ffs(rem) - 1;
-                        rem &= rem - 1u;
-                        if (idx >= pass && idx < pass + kListCap) {
-                            uint32_t item = ((uint32_t)lane << 5) | (uint32_t)j;
-                            if ((cand >> j) & 1u) {
-                                uint32_t dm = 0;
+            for (int d = 0; d < 8; ++d) np += __popc(sd[d] & cand);
+            my_pairs += np;
+            my_blocks += __popc(cand & (sd[0] | sd[1] | sd[2] | sd[3])) + __popc(cand & (sd[4] | sd[5] | sd[6] | sd[7]));
+            my_burn += __popc(burn);
+            const int n_items = __popc(burn) + (int)(FUSED ? np : __popc(cand));
+            int incl = n_items;
 #pragma unroll
-                                for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
-                                item |= (dm << 10) | (1u << 18);
-                            }
-                            list[idx - pass] = item;
-                        }
-                        ++idx;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total == 0) continue;
+            int pos = -1;
+            if (lane == 0) {
+                int old = s_qn[s % 3];
+                while (old + total <= kQCap) {
+                    const int prev = atomicCAS(&s_qn[s % 3], old, old + total);
+                    if (prev == old) {
+                        pos = old;
+                        break;
                     }
-                    __syncwarp();
-                    const int n_pass = min(kListCap, total - pass);
-                    for (int it = lane; it < n_pass; it += 32) {
-                        const uint32_t item = list[it];
-                        const int ol = (int)(item >> 5) & 31;
-                        const int j = (int)item & 31;
-                        const int ii = base + ol;
-                        const int ry = ii / WW;
-                        const int gy = oy + ry, gx = ox + ((ii - ry * WW) << 5) + j;
-                        const uint32_t cell = (uint32_t)(gy * W + gx);
-                        if (item & (1u << 18)) {
-                            const uint32_t dm = (item >> 10) & 0xFFu;
-                            my_pairs += __popc(dm);
-                            my_blocks += ((dm & 0x0Fu) ? 1u : 0u) + ((dm & 0xF0u) ? 1u : 0u);
-                            if (!FUSED && ignites(a, e, off, cell, dm, tt, ep4))
-                                atomicOr(&ignw[ol], 1u << j);
-                        } else {
-                            ++my_burn;
-                            const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
-                            if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&outw[ol], 1u << j);
-                        }
-                    }
-                    if (FUSED) {
-                        for (int it0 = 0; it0 < n_pass; it0 += 32)
-                            fused_pairs(a, sK, list, plist, ignw, it0, n_pass, base, e, off, W, WW, oy, ox, tt,
-                                        ep4, lane);
-                    }
-                    __syncwarp();
+                    old = prev;
                 }
             }
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (pos >= 0) {
+                uint32_t* q = Q + pos + (incl - n_items);
+                const uint32_t hi = (uint32_t)i << 20;
+                for (uint32_t m = burn; m != 0u; m &= m - 1u) *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 15);
+                if (FUSED) {
+#pragma unroll
+                    for (int d = 0; d < 8; ++d)
+                        for (uint32_t m = sd[d] & cand; m != 0u; m &= m - 1u)
+                            *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 15) | (1u << 14) | (uint32_t)d;
+                } else {
+                    for (uint32_t m = cand; m != 0u; m &= m - 1u) {
+                        const int j = __ffs(m) - 1;
+                        uint32_t dm = 0;
+#pragma unroll
+                        for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
+                        *q++ = hi | ((uint32_t)j << 15) | (1u << 14) | dm;
+                    }
+                }
+                continue;
+            }
+            // the queue is full: this warp evaluates the chunk itself
+            uint32_t* ignw_c = IG + base;
+            uint32_t* outw_c = OU + base;
+            const uint32_t act = cand | burn;
+            const int n_act = __popc(act);
+            int inca = n_act;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inca, o);
+                if (lane >= o) inca += v;
+            }
+            const int tot_a = __shfl_sync(0xffffffffu, inca, 31);
+            const int excl = inca - n_act;
+            for (int pass = 0; pass < tot_a; pass += kListCap) {
+                uint32_t rem = act;
+                int idx = excl;
+                while (rem != 0u) {
+                    const int j = __ffs(rem) - 1;
+                    rem &= rem - 1u;
+                    if (idx >= pass && idx < pass + kListCap) {
+                        uint32_t item = ((uint32_t)lane << 5) | (uint32_t)j;
+                        if ((cand >> j) & 1u) {
+                            uint32_t dm = 0;
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
+                            item |= (dm << 10) | (1u << 18);
+                        }
+                        list[idx - pass] = item;
+                    }
+                    ++idx;
+                }
+                __syncwarp();
+                const int n_pass = min(kListCap, tot_a - pass);
+                for (int it = lane; it < n_pass; it += 32) {
+                    const uint32_t item = list[it];
+                    const int ol = (int)(item >> 5) & 31;
+                    const int j = (int)item & 31;
+                    const int ii = base + ol;
+                    const int ry = ii / WW;
+                    const int gy = oy + ry, gx = ox + ((ii - ry * WW) << 5) + j;
+                    const uint32_t cell = (uint32_t)(gy * W + gx);
+                    if (item & (1u << 18)) {
+                        if (!FUSED && ignites(a, e, off, cell, (item >> 10) & 0xFFu, tt, ep4))
+                            atomicOr(&ignw_c[ol], 1u << j);
+                    } else {
+                        const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
+                        if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&outw_c[ol], 1u << j);
+                    }
+                }
+                if (FUSED) {
+                    for (int it0 = 0; it0 < n_pass; it0 += 32)
+                        fused_pairs(a, sK, list, plist, ignw_c, it0, n_pass, base, e, off, W, WW, oy, ox, tt, ep4,
+                                    lane);
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // phase B: every thread of the CTA evaluates queued items
+        {
+            const int qn = min(s_qn[s % 3], kQCap);
+            for (int q = threadIdx.x; q < qn; q += NT) {
+                const uint32_t it = Q[q];
+                const int ii = (int)(it >> 20), j = (int)(it >> 15) & 31;
+                const int ry = ii / WW;
+                const int gy = oy + ry, gx = ox + ((ii - ry * WW) << 5) + j;
+                const uint32_t cell = (uint32_t)(gy * W + gx);
+                if (!(it & (1u << 14))) {
+                    const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
+                    if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&OU[ii], 1u << j);
+                } else if (FUSED) {
+                    if (pair_ignites(a, sK, e, off, W, gy, gx, (int)(it & 7u), tt, ep4)) atomicOr(&IG[ii], 1u << j);
+                } else {
+                    if (ignites(a, e, off, cell, it & 0xFFu, tt, ep4)) atomicOr(&IG[ii], 1u << j);
+                }
+            }
+        }
+        __syncthreads();
+        // phase C: each warp writes back the chunks it claimed
+        for (int k = 0; k < (int)my_chunks; ++k) {
+            const int c = wch[k];
+            const int i = (c << 5) + lane;
+            uint32_t nbw = 0u;
             if (i < words) {
-                const uint32_t ig = ignw[lane], ou = outw[lane];
+                const int y = i / WW, w = i - (i / WW) * WW;
+                const uint32_t burn = Bc[WW + i];
+                const uint32_t ig = IG[i], ou = OU[i];
                 uint32_t nb = (burn & ~ou) | ig;
-                uint32_t nd = D[i] | ou;
                 const uint32_t im = (y >= kb && y < kb + TY) ? col_bits(w, 32, 32 + TX) : 0u;
                 my_r += __popc(nb);
                 my_b += __popc(nb & im);
-                my_d += __popc(nd & im);
+                my_o += __popc(ou & im);
                 const uint32_t m = drop_bits_rel(y, w, cxn, cyn, a.R, hasn);
-                nd |= nb & m;
+                const uint32_t doused = nb & m;
+                my_x += __popc(doused & im);
                 nb &= ~m;
                 Bn[WW + i] = nb;
-                D[i] = nd;
+                D[i] |= ou | doused;
                 C[i] &= ~ig;
-                ignw[lane] = 0u;
-                outw[lane] = 0u;
+                IG[i] = 0u;
+                OU[i] = 0u;
+                nbw = nb;
             }
-            __syncwarp();
+            const uint32_t any_nb = __ballot_sync(0xffffffffu, nbw != 0u);
+            if (lane == 0) fl_n[c] = any_nb != 0u;
         }
-        if (a.counts != nullptr) {
+        if (a.counts != nullptr && my_chunks) {
             my_pairs = __reduce_add_sync(0xffffffffu, my_pairs);
             my_blocks = __reduce_add_sync(0xffffffffu, my_blocks);
             my_burn = __reduce_add_sync(0xffffffffu, my_burn);
@@ -893,21 +1053,26 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
                 atomicAdd(&a.counts[0], (unsigned long long)my_pairs);
                 atomicAdd(&a.counts[1], (unsigned long long)my_blocks);
                 atomicAdd(&a.counts[2], (unsigned long long)my_burn);
+                atomicAdd(&a.counts[3], 32ull * my_chunks);
             }
-            if (threadIdx.x == 0) atomicAdd(&a.counts[3], (unsigned long long)words);
         }
-        my_b = __reduce_add_sync(0xffffffffu, my_b);
-        my_d = __reduce_add_sync(0xffffffffu, my_d);
-        my_r = __reduce_add_sync(0xffffffffu, my_r);
-        if (lane == 0) {
-            atomicAdd(&s_cnt[s % 3][0], my_b);
-            atomicAdd(&s_cnt[s % 3][1], my_d);
-            atomicAdd(&s_cnt[s % 3][2], my_r);
+        if (my_chunks) {
+            my_b = __reduce_add_sync(0xffffffffu, my_b);
+            my_o = __reduce_add_sync(0xffffffffu, my_o);
+            my_x = __reduce_add_sync(0xffffffffu, my_x);
+            my_r = __reduce_add_sync(0xffffffffu, my_r);
+            if (lane == 0) {
+                if (my_b) atomicAdd(&s_cnt[s % 3][0], my_b);
+                if (my_o) atomicAdd(&s_cnt[s % 3][1], my_o);
+                if (my_x) atomicAdd(&s_cnt[s % 3][2], my_x);
+                if (my_r) atomicAdd(&s_cnt[s % 3][3], my_r);
+            }
         }
         __syncthreads();
         fin_b = s_cnt[s % 3][0];
-        fin_d = s_cnt[s % 3][1];
-        const int32_t nr = s_cnt[s % 3][2];
+        fin_d = dbase + s_cnt[s % 3][1];          // burned after the step
+        dbase = fin_d + s_cnt[s % 3][2];          // and after the next drop
+        const int32_t nr = s_cnt[s % 3][3];
         if (threadIdx.x == 0) {
             if (fin_b) atomicAdd(&a.cnt[((int64_t)s * 2) * a.N + e], fin_b);
             if (fin_d) atomicAdd(&a.cnt[((int64_t)s * 2 + 1) * a.N + e], fin_d);
@@ -915,6 +1080,9 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         uint32_t* tmp = Bc;
         Bc = Bn;
         Bn = tmp;
+        uint8_t* ftmp = fl_c;
+        fl_c = fl_n;
+        fl_n = ftmp;
         if (nr == 0) {
             // no fire left in the region: the remaining steps change nothing
             for (int s2 = s + 1 + (int)threadIdx.x; s2 < kb; s2 += NT)
@@ -946,9 +1114,34 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
                 dst[j] = (uint8_t)(((c >> j) & 1u) + ((b >> j) & 1u) * 2u + ((dd >> j) & 1u) * 3u);
         }
     }
+    // where the burning interior cells are, for the next round's activity
+    uint32_t act = 0u;
+    if (fin_b > 0) {
+        const int band = kMaxRound;
+        for (int i = threadIdx.x; i < TY * iwords; i += NT) {
+            const int ry = kb + i / iwords, w = 1 + i % iwords;
+            const uint32_t b = Bc[(ry + 1) * WW + w] & col_bits(w, 32, 32 + TX);
+            if (b == 0u) continue;
+            act |= kActAny;
+            const bool n = ry - kb < band, so = kb + TY - 1 - ry < band;
+            const bool wb = (b & col_bits(w, 32, 32 + band)) != 0u;
+            const bool eb = (b & col_bits(w, max(32, 32 + TX - band), 32 + TX)) != 0u;
+            if (n) act |= kActN;
+            if (so) act |= kActS;
+            if (wb) act |= kActW;
+            if (eb) act |= kActE;
+            if (n && wb) act |= kActNW;
+            if (n && eb) act |= kActNE;
+            if (so && wb) act |= kActSW;
+            if (so && eb) act |= kActSE;
+        }
+        act = __reduce_or_sync(0xffffffffu, act);
+        if (lane == 0 && act != 0u) atomicOr(&s_act, act);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         a.tile_burnt[tix] = fin_d;
-        a.act_out[tix] = fin_b > 0 ? 1 : 0;
+        a.act_out[tix] = (uint16_t)s_act;
         a.synced[tix] = 0;
     }
 }
@@ -1049,7 +1242,7 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
     cudaError_t err;
     if (!c->tiles_valid) {
         // the state changed outside the tiled path: every tile may be active
-        err = cudaMemsetAsync(c->d_tact[c->tact_cur], 1, (size_t)c->n_tiles4, s);
+        err = cudaMemsetAsync(c->d_tact[c->tact_cur], 0xFF, (size_t)c->n_tiles4 * sizeof(uint16_t), s);
         if (err == cudaSuccess) err = cudaMemsetAsync(c->d_tsync, 0, (size_t)c->n_tiles4, s);
         if (err != cudaSuccess) return err;
         c->tiles_valid = true;
@@ -1091,7 +1284,13 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         a.key0 = (uint32_t)(c->seed & 0xffffffffu);
         a.key1 = (uint32_t)(c->seed >> 32);
         a.p_continue = c->P.p_continue;
-        err = fused ? launch_tiled_t<256, true>(c, a, K, s) : launch_tiled_t<256, false>(c, a, K, s);
+        const int nt = c->threads_per_env;
+        if (nt == 128)
+            err = fused ? launch_tiled_t<128, true>(c, a, K, s) : launch_tiled_t<128, false>(c, a, K, s);
+        else if (nt == 512)
+            err = fused ? launch_tiled_t<512, true>(c, a, K, s) : launch_tiled_t<512, false>(c, a, K, s);
+        else
+            err = fused ? launch_tiled_t<256, true>(c, a, K, s) : launch_tiled_t<256, false>(c, a, K, s);
         if (err != cudaSuccess) return err;
         const int64_t o = (int64_t)s0 * c->N;
         k_round_finalize<<<(c->N + 255) / 256, 256, 0, s>>>(c->N, kb, c->d_tcnt, c->d_t, c->t_max,

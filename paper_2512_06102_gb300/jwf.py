@@ -79,6 +79,8 @@ _SIGS = {
     "jwf_step_relaxed_bwd": (ctypes.c_int, [_VP] * 11),
     "jwf_rates_bwd": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 9),
     "jwf_rates_accumulate": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 5),
+    "jwf_relaxed_fwd_steps": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 6),
+    "jwf_relaxed_bwd_steps": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 10),
     "jwf_rates_contract": (ctypes.c_int, [_VP] * 8),
     "jwf_step_relaxed_bwd_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP,
                                                     ctypes.c_float] + [_VP] * 9),
@@ -206,6 +208,7 @@ class Sim:
         self.cells = int(L.jwf_n_cells(h))
         self.offsets = np.array([L.jwf_env_offset(h, e) for e in range(self.N + 1)], np.int64)
         self.params: ParamSet | None = None
+        self.tables_version = 0         # bumped by every call that changes the rate tables
 
     # -- plumbing -----------------------------------------------------------
     def _check(self, st: int, where: str):
@@ -228,6 +231,7 @@ class Sim:
 
     # -- parameters and tables ---------------------------------------------
     def set_params(self, p):
+        self.tables_version += 1
         p = ParamSet.from_any(p)
         mv = np.ascontiguousarray(p.mu_veg, np.float32)
         md = np.ascontiguousarray(p.mu_den, np.float32)
@@ -239,6 +243,7 @@ class Sim:
         self.params = p
 
     def precompute_probs(self, cls, dem, wind_speed, wind_dir, stream=None):
+        self.tables_version += 1
         self._terrain = (cls, dem, wind_speed, wind_dir)
         self._check(lib().jwf_precompute_probs(self._h, _ptr(cls), _ptr(dem), _ptr(wind_speed), _ptr(wind_dir),
                                                _stream(stream)), "jwf_precompute_probs")
@@ -250,6 +255,7 @@ class Sim:
                                           _stream(stream)), "jwf_set_terrain")
 
     def set_probs(self, q, r=None, stream=None):
+        self.tables_version += 1
         self._check(lib().jwf_set_probs(self._h, _ptr(q), _ptr(r), _stream(stream)), "jwf_set_probs")
 
     def probs(self):
@@ -335,6 +341,24 @@ class Sim:
         self._check(lib().jwf_step_relaxed_bwd(self._h, _ptr(pun), _ptr(pburn), _ptr(mask), _ptr(gun_out),
                                                _ptr(gburn_out), _ptr(gun), _ptr(gburn), _ptr(glam), _ptr(gpc),
                                                _stream(stream)), "jwf_step_relaxed_bwd")
+        return gun, gburn
+
+    def relaxed_fwd_steps(self, pun, pburn, pun_out, pburn_out, masks=None, stream=None):
+        """pun_out / pburn_out [n, cells]: row t = state after step t."""
+        n = pun_out.shape[0]
+        self._check(lib().jwf_relaxed_fwd_steps(self._h, int(n), _ptr(pun), _ptr(pburn), _ptr(masks),
+                                                _ptr(pun_out), _ptr(pburn_out), _stream(stream)),
+                    "jwf_relaxed_fwd_steps")
+        return pun_out, pburn_out
+
+    def relaxed_bwd_steps(self, pun, pburn, gun_out, gburn_out, gun, gburn, masks=None, glam=None, gpc=None,
+                          stream=None):
+        """pun / pburn [n, cells]: row t = state before step t; adjoints of
+        the state after step n-1 in, of the state before step 0 out."""
+        n = pun.shape[0]
+        self._check(lib().jwf_relaxed_bwd_steps(self._h, int(n), _ptr(pun), _ptr(pburn), _ptr(masks),
+                                                _ptr(gun_out), _ptr(gburn_out), _ptr(gun), _ptr(gburn),
+                                                _ptr(glam), _ptr(gpc), _stream(stream)), "jwf_relaxed_bwd_steps")
         return gun, gburn
 
     def rates_bwd(self, glam, pburn, cls, dem, wind_speed, wind_dir, gparams, mask=None, stream=None):

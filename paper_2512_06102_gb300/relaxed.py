@@ -66,6 +66,7 @@ class RelaxedRollout(torch.autograd.Function):
         cls, dem, ws, wd = scene
         sim.set_params(theta_to_params(theta, sim.n_classes, cell_size))
         sim.precompute_probs(cls, dem, ws, wd)
+        tables_version = sim.tables_version
         ckpt_every = resolve_ckpt(T, sim.cells, ckpt_every, p_un0.device)
         seg = segment_length(T, ckpt_every)
         pu, pb = p_un0.contiguous(), p_burn0.contiguous()
@@ -75,28 +76,25 @@ class RelaxedRollout(torch.autograd.Function):
             PB = torch.empty_like(PU)
             PU[0].copy_(pu)
             PB[0].copy_(pb)
-            for t in range(T):
-                sim.relaxed_fwd(PU[t], PB[t], None if masks is None else masks[t], PU[t + 1], PB[t + 1])
+            if T > 0:
+                sim.relaxed_fwd_steps(PU[0], PB[0], PU[1:], PB[1:], masks=None if masks is None else masks[:T])
             ctx.ckpts = [(PU, PB)]
             out_u, out_b = PU[T], PB[T]
         else:
             ckpts = []
-            bu, bb = torch.empty_like(pu), torch.empty_like(pb)
-            for t in range(T):
-                if t % seg == 0:
-                    ckpts.append((pu.clone(), pb.clone()))
-                m = None if masks is None else masks[t]
-                sim.relaxed_fwd(pu, pb, m, bu, bb)
-                if t == 0:
-                    pu, pb = bu, bb
-                    bu, bb = torch.empty_like(pu), torch.empty_like(pb)
-                else:
-                    pu, bu = bu, pu
-                    pb, bb = bb, pb
+            bu = torch.empty((seg, sim.cells), dtype=torch.float32, device=pu.device)
+            bb = torch.empty_like(bu)
+            cu, cb = pu.clone(), pb.clone()
+            for a in range(0, T, seg):
+                b = min(a + seg, T)
+                ckpts.append((cu, cb))
+                sim.relaxed_fwd_steps(cu, cb, bu[:b - a], bb[:b - a], masks=None if masks is None else masks[a:b])
+                cu, cb = bu[b - a - 1].clone(), bb[b - a - 1].clone()
             ctx.ckpts = ckpts
-            out_u, out_b = pu, pb
+            out_u, out_b = cu, cb
         ctx.sim, ctx.scene, ctx.T, ctx.masks, ctx.seg = sim, scene, T, masks, seg
         ctx.keep_all = ckpt_every == 0
+        ctx.tables_version = tables_version
         ctx.theta_device = theta.device
         ctx.cell_size = cell_size
         ctx.theta = theta.detach().clone()
@@ -107,8 +105,9 @@ class RelaxedRollout(torch.autograd.Function):
         sim, T, seg, masks = ctx.sim, ctx.T, ctx.seg, ctx.masks
         cls, dem, ws, wd = ctx.scene
         # the context may have been used since the forward: restore its tables
-        sim.set_params(theta_to_params(ctx.theta, sim.n_classes, ctx.cell_size))
-        sim.precompute_probs(cls, dem, ws, wd)
+        if sim.tables_version != ctx.tables_version:
+            sim.set_params(theta_to_params(ctx.theta, sim.n_classes, ctx.cell_size))
+            sim.precompute_probs(cls, dem, ws, wd)
         dev = g_un.device
         cells = sim.cells
         gparams = torch.zeros(sim.grad_size, dtype=torch.float64, device=dev)
@@ -133,23 +132,21 @@ class RelaxedRollout(torch.autograd.Function):
                 su, sb = pu_buf, pb_buf
                 su[0].copy_(ctx.ckpts[si][0])
                 sb[0].copy_(ctx.ckpts[si][1])
-                for t in range(a, b - 1):
-                    m = None if masks is None else masks[t]
-                    sim.relaxed_fwd(su[t - a], sb[t - a], m, su[t - a + 1], sb[t - a + 1])
-            # adjoint steps in reverse; the rate adjoint is accumulated per
-            # CHUNK-step block aligned to absolute step indices
+                if b - a > 1:
+                    sim.relaxed_fwd_steps(su[0], sb[0], su[1:b - a], sb[1:b - a],
+                                          masks=None if masks is None else masks[a:b - 1])
+            # adjoint steps in reverse, one CHUNK-step block (aligned to
+            # absolute step indices) a call; then its rate adjoint
             hi = b
-            for t in reversed(range(a, b)):
-                lo = (t // CHUNK) * CHUNK
-                m = None if masks is None else masks[t]
-                sim.relaxed_bwd(su[t - a], sb[t - a], gu, gb, m, ngu, ngb, glam[t - lo], gpc)
+            while hi > a:
+                lo = max(a, ((hi - 1) // CHUNK) * CHUNK)
+                mk = None if masks is None else masks[lo:hi]
+                sim.relaxed_bwd_steps(su[lo - a:hi - a], sb[lo - a:hi - a], gu, gb, ngu, ngb, masks=mk,
+                                      glam=glam[:hi - lo], gpc=gpc)
                 gu, ngu = ngu, gu
                 gb, ngb = ngb, gb
-                if t == lo:
-                    sim.rates_accumulate(glam[:hi - lo], sb[lo - a:hi - a], gr,
-                                         mask=None if masks is None else masks[lo:hi])
-                    hi = lo
-            assert hi == a
+                sim.rates_accumulate(glam[:hi - lo], sb[lo - a:hi - a], gr, mask=mk)
+                hi = lo
         sim.rates_contract(gr, cls, dem, ws, wd, gparams)
         C = sim.n_classes
         g = torch.empty(6 + 2 * C, dtype=torch.float64, device=dev)

@@ -12,7 +12,8 @@
     masked source burn probability) within 1e-6 relative, and its contraction
     with dr/dtheta within 1e-4 relative of the oracle's autograd; the one-call
     jwf_rates_bwd agrees with the two halves;
-  * checkpointed and non-checkpointed gradients are bit-identical;
+  * checkpointed and non-checkpointed gradients are bit-identical, and the
+    multi-step calls equal the single-step calls bit for bit;
   * the tiled kernels (fused adjoint) and the plain one-thread-per-cell
     kernels (two-pass adjoint) agree to float rounding on a ragged batch;
   * T = 1000 on the 256 x 128^2 differentiation workload with sqrt(T)
@@ -284,6 +285,43 @@ def test_tiled_and_plain_kernels_agree():
     for a, b in zip(out[jwf.RELAXED_TILED][:5], out[jwf.RELAXED_PLAIN][:5]):
         assert torch.allclose(a, b, rtol=1e-6, atol=1e-7 * float(b.abs().max()))
     assert out[jwf.RELAXED_TILED][5].item() == pytest.approx(out[jwf.RELAXED_PLAIN][5].item(), rel=1e-12)
+
+
+def test_multi_step_calls_equal_single_steps():
+    require_gpu()
+    scn = scenarios.make_scenario(40, 72, N=3, seed=9)
+    rng = np.random.default_rng(9)
+    pu, pb = _planes(scn, rng)
+    n, T = pu.size, 5
+    masks = to(((rng.random((T, n)) < 0.05) * 0.8).astype(np.float32))
+    sim = make_sim(scn, keep_rates=True)
+    sim.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    U0, B0 = to(pu.astype(np.float32)), to(pb.astype(np.float32))
+    SU = torch.empty((T, n), device="cuda")
+    SB = torch.empty((T, n), device="cuda")
+    sim.relaxed_fwd_steps(U0, B0, SU, SB, masks=masks)
+    u, b = U0, B0
+    states = [(U0, B0)]
+    for t in range(T):
+        u, b = sim.relaxed_fwd(u, b, masks[t])
+        assert torch.equal(u, SU[t]) and torch.equal(b, SB[t])
+        states.append((u, b))
+    PU = torch.stack([s_[0] for s_ in states[:T]])
+    PB = torch.stack([s_[1] for s_ in states[:T]])
+    au = to(rng.standard_normal(n).astype(np.float32))
+    ab = to(rng.standard_normal(n).astype(np.float32))
+    gu, gb = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+    glam = torch.empty((T, n), device="cuda")
+    gpc = torch.zeros(1, dtype=f64, device="cuda")
+    sim.relaxed_bwd_steps(PU, PB, au, ab, gu, gb, masks=masks, glam=glam, gpc=gpc)
+    gpc1 = torch.zeros(1, dtype=f64, device="cuda")
+    ru, rb = au, ab
+    for t in reversed(range(T)):
+        gl = torch.empty(n, device="cuda")
+        ru, rb = sim.relaxed_bwd(PU[t], PB[t], ru, rb, mask=masks[t], glam=gl, gpc=gpc1)
+        assert torch.equal(gl, glam[t])
+    assert torch.equal(ru, gu) and torch.equal(rb, gb)
+    assert gpc.item() == gpc1.item()
 
 
 def test_full_size_T1000_sampled():
