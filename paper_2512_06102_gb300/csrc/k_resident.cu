@@ -27,6 +27,7 @@
 namespace {
 
 constexpr int kListCap = 256;      // active cells shared out per warp pass
+constexpr int kResQCap = 1024;     // block-wide work items per step (resident step)
 // per warp: item list, ign and out words, pair list (fused variant)
 constexpr int kWarpScratch = kListCap + 64 + 256;
 
@@ -265,13 +266,16 @@ __device__ __forceinline__ void fused_pairs(const Args& a, const RateConsts& K, 
     __syncwarp();
 }
 
+// at most 64 registers a thread: 1024 threads fit an SM
 template <int NT, bool FUSED>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 1024 / NT)
 k_step_resident(const ResArgs a, const RateConsts Kc) {
     extern __shared__ uint32_t sm[];
     __shared__ int32_t s_env;
     __shared__ int32_t s_cnt[3][3];     // burning, new burn-outs, doused (per step)
     __shared__ int32_t s_chunk[3];
+    __shared__ int32_t s_qn[3];         // queued work items (per step)
+    __shared__ int32_t s_ncl[3];        // chunks claimed (per step)
     __shared__ int32_t s_burnt;
     // the rate constants live in shared memory only in the fused variant
     __shared__ typename std::conditional<FUSED, RateConsts, int>::type sK_store;
@@ -308,6 +312,9 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         // chunk activity flags of the two burning buffers
         uint8_t* flag0 = reinterpret_cast<uint8_t*>(D + words + (NT / 32) * kWarpScratch);
         uint8_t* flag1 = flag0 + nchunks;
+        // chunks claimed this step and the block-wide queue of work items
+        int* clist = reinterpret_cast<int*>(flag0 + 2 * ((nchunks + 3) & ~3));
+        uint32_t* Q = reinterpret_cast<uint32_t*>(clist + nchunks);
         const int reach = (WW + 1 + 31) >> 5;                 // chunks a word's neighbours span
         const int64_t off = a.off[e];
         uint8_t* Fe = a.F + off;
@@ -316,10 +323,12 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         // zero both burning planes (the padding rows must read as 0), then load
         for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
         if (threadIdx.x < 9) s_cnt[threadIdx.x / 3][threadIdx.x % 3] = 0;
-        if (threadIdx.x < 3) s_chunk[threadIdx.x] = 0;
+        if (threadIdx.x < 3) {
+            s_chunk[threadIdx.x] = 0;
+            s_qn[threadIdx.x] = 0;
+            s_ncl[threadIdx.x] = 0;
+        }
         if (threadIdx.x == 0) s_burnt = 0;
-        ignw[lane] = 0u;
-        outw[lane] = 0u;
         __syncthreads();
         res_load(Fe, H, W, WW, vec, B0, C, D);
         __syncthreads();
@@ -346,6 +355,8 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 s_cnt[(s + 1) % 3][1] = 0;
                 s_cnt[(s + 1) % 3][2] = 0;
                 s_chunk[(s + 1) % 3] = 0;
+                s_qn[(s + 1) % 3] = 0;
+                s_ncl[(s + 1) % 3] = 0;
             }
             // the next step's drop is applied while the new planes are written
             int cxn = -1, cyn = -1;
@@ -355,6 +366,8 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
             }
             int my_b = 0, my_o = 0, my_x = 0;
             uint32_t my_pairs = 0, my_blocks = 0, my_burn = 0, my_chunks = 0;
+            // phase A: warps claim the chunks that can change, clear their
+            // words of the write buffer, and queue their work items
             for (;;) {
                 int c = 0;
                 if (lane == 0) c = atomicAdd(&s_chunk[s % 3], 1);
@@ -367,14 +380,13 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                     need = fl_c[cc] != 0;
                 if (!need) continue;
                 ++my_chunks;
+                if (lane == 0) clist[atomicAdd(&s_ncl[s % 3], 1)] = c;
                 const int base = c << 5;
                 const int i = base + lane;
                 uint32_t burn = 0, cand = 0;
                 uint32_t sd[8];
-                int y = 0, w = 0;
                 if (i < words) {
-                    y = i / WW;
-                    w = i - y * WW;
+                    const int w = i - (i / WW) * WW;
                     const uint32_t* bp = &Bc[WW + i];             // row y + 1 of the padded plane
                     const bool hl = w > 0, hr = w + 1 < WW;
                     const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
@@ -392,92 +404,171 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                     const uint32_t any = sd[0] | sd[1] | sd[2] | sd[3] | sd[4] | sd[5] | sd[6] | sd[7];
                     cand = C[i] & any;
                     burn = bc;
+                    Bn[WW + i] = 0u;                  // collects this step's ignitions
                 } else {
 #pragma unroll
                     for (int d = 0; d < 8; ++d) sd[d] = 0u;
                 }
-                const uint32_t act = cand | burn;
-                if (__ballot_sync(0xffffffffu, act != 0u) != 0u) {
-                    // share out the active cells of these 32 words across the warp
-                    const int n_act = __popc(act);
-                    int incl = n_act;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += v;
-                    }
-                    const int total = __shfl_sync(0xffffffffu, incl, 31);
-                    const int excl = incl - n_act;
-                    for (int pass = 0; pass < total; pass += kListCap) {
-                        uint32_t rem = act;
-                        int idx = excl;
-                        while (rem != 0u) {
-                            const int j = __ffs(rem) - 1;
-                            rem &= rem - 1u;
-                            if (idx >= pass && idx < pass + kListCap) {
-                                uint32_t item = ((uint32_t)lane << 5) | (uint32_t)j;
-                                if ((cand >> j) & 1u) {
-                                    uint32_t dm = 0;
-#pragma unroll
-                                    for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
-                                    item |= (dm << 10) | (1u << 18);
-                                }
-                                list[idx - pass] = item;
-                            }
-                            ++idx;
-                        }
-                        __syncwarp();
-                        const int n_pass = min(kListCap, total - pass);
-                        for (int it = lane; it < n_pass; it += 32) {
-                            const uint32_t item = list[it];
-                            const int ol = (int)(item >> 5) & 31;    // owner lane
-                            const int j = (int)item & 31;
-                            const int ii = base + ol;
-                            const int yy = ii / WW;
-                            const int xx = ((ii - yy * WW) << 5) + j;
-                            const uint32_t cell = (uint32_t)(yy * W + xx);
-                            if (item & (1u << 18)) {
-                                const uint32_t dm = (item >> 10) & 0xFFu;
-                                my_pairs += __popc(dm);
-                                my_blocks += ((dm & 0x0Fu) ? 1u : 0u) + ((dm & 0xF0u) ? 1u : 0u);
-                                if (!FUSED && ignites(a, e, off, cell, dm, tt, ep4))
-                                    atomicOr(&ignw[ol], 1u << j);
-                            } else {
-                                ++my_burn;
-                                const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
-                                if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&outw[ol], 1u << j);
-                            }
-                        }
-                        if (FUSED) {
-                            for (int it0 = 0; it0 < n_pass; it0 += 32)
-                                fused_pairs(a, sK, list, plist, ignw, it0, n_pass, base, e, off, W, WW, 0, 0, tt,
-                                            ep4, lane);
-                        }
-                        __syncwarp();
-                    }
-                }
-                uint32_t nb = 0u;
-                if (i < words) {
-                    const uint32_t ig = ignw[lane], ou = outw[lane];
-                    nb = (burn & ~ou) | ig;
-                    my_b += __popc(nb);
-                    my_o += __popc(ou);
-                    const uint32_t m = drop_bits(y, w, W, cxn, cyn, a.R);
-                    const uint32_t doused = nb & m;
-                    my_x += __popc(doused);
-                    nb &= ~m;
-                    Bn[WW + i] = nb;
-                    D[i] |= ou | doused;
-                    C[i] &= ~ig;
-                    ignw[lane] = 0u;
-                    outw[lane] = 0u;
-                }
-                const uint32_t any_nb = __ballot_sync(0xffffffffu, nb != 0u);
-                if (lane == 0) fl_n[c] = any_nb != 0u;
                 __syncwarp();
+                uint32_t np = 0;
+#pragma unroll
+                for (int d = 0; d < 8; ++d) np += __popc(sd[d] & cand);
+                my_pairs += np;
+                my_blocks += __popc(cand & (sd[0] | sd[1] | sd[2] | sd[3])) +
+                             __popc(cand & (sd[4] | sd[5] | sd[6] | sd[7]));
+                my_burn += __popc(burn);
+                const int n_items = __popc(burn) + (int)(FUSED ? np : __popc(cand));
+                int incl = n_items;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                if (total == 0) continue;
+                int pos = -1;
+                if (lane == 0) {
+                    int old = s_qn[s % 3];
+                    while (old + total <= kResQCap) {
+                        const int prev = atomicCAS(&s_qn[s % 3], old, old + total);
+                        if (prev == old) {
+                            pos = old;
+                            break;
+                        }
+                        old = prev;
+                    }
+                }
+                pos = __shfl_sync(0xffffffffu, pos, 0);
+                if (pos >= 0) {
+                    uint32_t* q = Q + pos + (incl - n_items);
+                    const uint32_t hi = (uint32_t)i << 18;
+                    for (uint32_t m = burn; m != 0u; m &= m - 1u) *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 13);
+                    if (FUSED) {
+#pragma unroll
+                        for (int d = 0; d < 8; ++d)
+                            for (uint32_t m = sd[d] & cand; m != 0u; m &= m - 1u)
+                                *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 13) | (1u << 12) | (uint32_t)d;
+                    } else {
+                        for (uint32_t m = cand; m != 0u; m &= m - 1u) {
+                            const int j = __ffs(m) - 1;
+                            uint32_t dm = 0;
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
+                            *q++ = hi | ((uint32_t)j << 13) | (1u << 12) | dm;
+                        }
+                    }
+                    continue;
+                }
+                // the queue is full: this warp evaluates the chunk itself
+                // (ignitions into the cleared write-buffer words, burn-outs
+                // into the burned plane)
+                uint32_t* ignw_c = Bn + WW + base;
+                uint32_t* outw_c = D + base;
+                const uint32_t act = cand | burn;
+                const int n_act = __popc(act);
+                int inca = n_act;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, inca, o);
+                    if (lane >= o) inca += v;
+                }
+                const int tot_a = __shfl_sync(0xffffffffu, inca, 31);
+                const int excl = inca - n_act;
+                for (int pass = 0; pass < tot_a; pass += kListCap) {
+                    uint32_t rem = act;
+                    int idx = excl;
+                    while (rem != 0u) {
+                        const int j = __ffs(rem) - 1;
+                        rem &= rem - 1u;
+                        if (idx >= pass && idx < pass + kListCap) {
+                            uint32_t item = ((uint32_t)lane << 5) | (uint32_t)j;
+                            if ((cand >> j) & 1u) {
+                                uint32_t dm = 0;
+#pragma unroll
+                                for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
+                                item |= (dm << 10) | (1u << 18);
+                            }
+                            list[idx - pass] = item;
+                        }
+                        ++idx;
+                    }
+                    __syncwarp();
+                    const int n_pass = min(kListCap, tot_a - pass);
+                    for (int it = lane; it < n_pass; it += 32) {
+                        const uint32_t item = list[it];
+                        const int ol = (int)(item >> 5) & 31;
+                        const int j = (int)item & 31;
+                        const int ii = base + ol;
+                        const int yy = ii / WW;
+                        const int xx = ((ii - yy * WW) << 5) + j;
+                        const uint32_t cell = (uint32_t)(yy * W + xx);
+                        if (item & (1u << 18)) {
+                            if (!FUSED && ignites(a, e, off, cell, (item >> 10) & 0xFFu, tt, ep4))
+                                atomicOr(&ignw_c[ol], 1u << j);
+                        } else {
+                            const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
+                            if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&outw_c[ol], 1u << j);
+                        }
+                    }
+                    if (FUSED) {
+                        for (int it0 = 0; it0 < n_pass; it0 += 32)
+                            fused_pairs(a, sK, list, plist, ignw_c, it0, n_pass, base, e, off, W, WW, 0, 0, tt,
+                                        ep4, lane);
+                    }
+                    __syncwarp();
+                }
             }
-            // counts of this step (before the next drop), one barrier
-            if (a.counts != nullptr) {
+            __syncthreads();
+            // phase B: every thread of the CTA evaluates queued items
+            {
+                const int qn = min(s_qn[s % 3], kResQCap);
+                for (int q = threadIdx.x; q < qn; q += NT) {
+                    const uint32_t it = Q[q];
+                    const int ii = (int)(it >> 18), j = (int)(it >> 13) & 31;
+                    const int yy = ii / WW;
+                    const int xx = ((ii - yy * WW) << 5) + j;
+                    const uint32_t cell = (uint32_t)(yy * W + xx);
+                    if (!(it & (1u << 12))) {
+                        const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
+                        if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&D[ii], 1u << j);
+                    } else if (FUSED) {
+                        if (pair_ignites(a, sK, e, off, W, yy, xx, (int)(it & 7u), tt, ep4))
+                            atomicOr(&Bn[WW + ii], 1u << j);
+                    } else {
+                        if (ignites(a, e, off, cell, it & 0xFFu, tt, ep4)) atomicOr(&Bn[WW + ii], 1u << j);
+                    }
+                }
+            }
+            __syncthreads();
+            // phase C: the claimed chunks are written back, dealt to the warps
+            {
+                const int ncl = s_ncl[s % 3];
+                for (int k = warp; k < ncl; k += NT / 32) {
+                    const int c = clist[k];
+                    const int i = (c << 5) + lane;
+                    uint32_t nb = 0u;
+                    if (i < words) {
+                        const int y = i / WW, w = i - (i / WW) * WW;
+                        const uint32_t burn = Bc[WW + i];
+                        const uint32_t ig = Bn[WW + i];
+                        const uint32_t ou = D[i] & burn;          // burning cells that burned out
+                        nb = (burn & ~ou) | ig;
+                        my_b += __popc(nb);
+                        my_o += __popc(ou);
+                        const uint32_t m = drop_bits(y, w, W, cxn, cyn, a.R);
+                        const uint32_t doused = nb & m;
+                        my_x += __popc(doused);
+                        nb &= ~m;
+                        Bn[WW + i] = nb;
+                        D[i] |= doused;
+                        C[i] &= ~ig;
+                    }
+                    const uint32_t any_nb = __ballot_sync(0xffffffffu, nb != 0u);
+                    if (lane == 0) fl_n[c] = any_nb != 0u;
+                }
+            }
+            // counts of this step (before the next drop)
+            if (a.counts != nullptr && my_chunks) {
                 my_pairs = __reduce_add_sync(0xffffffffu, my_pairs);
                 my_blocks = __reduce_add_sync(0xffffffffu, my_blocks);
                 my_burn = __reduce_add_sync(0xffffffffu, my_burn);
@@ -485,8 +576,8 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                     atomicAdd(&a.counts[0], (unsigned long long)my_pairs);
                     atomicAdd(&a.counts[1], (unsigned long long)my_blocks);
                     atomicAdd(&a.counts[2], (unsigned long long)my_burn);
+                    atomicAdd(&a.counts[3], 32ull * my_chunks);
                 }
-                if (lane == 0 && my_chunks) atomicAdd(&a.counts[3], 32ull * my_chunks);
             }
             my_b = __reduce_add_sync(0xffffffffu, my_b);
             my_o = __reduce_add_sync(0xffffffffu, my_o);
@@ -1306,8 +1397,11 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
 
 size_t jwf_resident_smem(int32_t H, int32_t W, int threads) {
     const int nwarps = threads / 32;
+    // queued work items address words with 14 bits
+    if ((int64_t)H * ((W + 31) / 32) >= (int64_t)1 << 14) return (size_t)1 << 40;
     const int64_t nchunks = ((int64_t)H * ((W + 31) / 32) + 31) / 32;
-    const int64_t flag_words = (2 * nchunks + 3) / 4;
+    // two chunk-flag byte arrays, the claimed-chunk list and the work queue
+    const int64_t flag_words = 2 * ((nchunks + 3) / 4) + nchunks + kResQCap;
     return (size_t)(res_plane_words(H, W) + nwarps * kWarpScratch + flag_words) * sizeof(uint32_t);
 }
 
