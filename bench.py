@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-rollout", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--profile", choices=["resident", "relaxed", "tiled"], default=None,
+                    help="run one small case of a kernel family once (for ncu captures); prints no bench line")
     return ap.parse_args()
 
 
@@ -706,8 +708,62 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(case: str):
+    """Small cases of the workloads for ncu captures (inputs still larger than
+    L2, a few GB on the device at most): 'resident' = 1024 grids of 128^2, one
+    200-step episode with drops on the fused resident kernel; 'relaxed' = 256
+    grids of 128^2, one tiled relaxed forward step, one adjoint step and one
+    8-step rate-adjoint accumulation; 'tiled' = 2 grids of 4096^2, 800 steps with
+    drops on the fused tiled kernel (256 threads a tile, 16 steps a round)."""
+    import torch
+
+    from paper_2512_06102_gb300 import build, jwf, scenarios
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    if case in ("resident", "tiled"):
+        N, S, K = (1024, SIDE, EPISODE) if case == "resident" else (2, BIG_SIDE, 800)
+        scn = scenarios.make_scenario(S, S, N=N, seed=0)
+        drops = scenarios.drops(K, scn.H, scn.W, seed=0)
+        sim = jwf.Sim(S, S, n_envs=N, n_classes=scenarios.N_CLASSES, seed=0)
+        sim.set_params(scn.params)
+        sim.set_terrain(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+        if case == "resident":
+            sim.set_kernel(jwf.KERNEL_FUSED)
+        else:
+            sim.set_kernel(jwf.KERNEL_TILED_FUSED, 256)
+            sim.set_round_steps(16)
+        sim.load_state(to(scn.F0))
+        out = sim.step(K, to(drops))
+        torch.cuda.synchronize()
+        print(f"profile case {case}: burned at the end {int(out[1][-1].sum())}")
+    else:
+        scn = scenarios.make_scenario(SIDE, SIDE, N=REL_ENVS, seed=100)
+        sim = jwf.Sim(SIDE, SIDE, n_envs=REL_ENVS, n_classes=scenarios.N_CLASSES, keep_rates=True)
+        sim.set_params(scn.params)
+        sim.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+        pb0 = (to(scn.F0) == 2).float()
+        pu0 = 1.0 - pb0
+        g = torch.Generator(device=dev).manual_seed(3)
+        au = torch.randn(pu0.shape, device=dev, generator=g)
+        ab = torch.randn(pu0.shape, device=dev, generator=g)
+        glam = torch.empty((8, sim.cells), device=dev)
+        gpc = torch.zeros(1, dtype=torch.float64, device=dev)
+        ou, ob = sim.relaxed_fwd(pu0, pb0)
+        for t in range(8):
+            sim.relaxed_bwd(pu0, pb0, au, ab, None, None, None, glam[t], gpc)
+        gr = torch.zeros((sim.cells, 8), device=dev)
+        sim.rates_accumulate(glam, torch.stack([pb0] * 8), gr)
+        torch.cuda.synchronize()
+        print(f"profile case relaxed: {float(ou.sum()):.3f} {float(gr.abs().sum()):.3f}")
+
+
 def main():
     args = parse()
+    if args.profile is not None:
+        run_profile(args.profile)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
