@@ -334,10 +334,21 @@ def run_ours(args):
     t_table = timed(table_episode)
     sim.set_kernel(jwf.KERNEL_PLAIN)
     t_plain = timed(table_episode)
+    # the same episode with the wind changing every step (a [200][N] series;
+    # the fused kernel evaluates each step's rates, no table to rebuild)
+    gw = torch.Generator(device=dev).manual_seed(11)
+    ws_ser = torch.rand((EPISODE, N_ENVS), device=dev, generator=gw) * 10.0
+    wd_ser = torch.rand((EPISODE, N_ENVS), device=dev, generator=gw) * (2.0 * np.pi)
+    sim.set_kernel(jwf.KERNEL_FUSED)
+    sim.set_wind_series(ws_ser, wd_ser)
+    episode()
+    t_series = timed(episode)
+    sim.set_wind_series(None)
     comparators = {"table_resident_ms_per_step": round(t_table * 1e3, 3),
                    "plain_one_launch_per_step_ms_per_step": round(t_plain * 1e3, 3),
                    "speedup_vs_plain": round(t_plain / (t_max / args.steps), 2),
-                   "speedup_vs_table_resident": round(t_table / (t_max / args.steps), 2)}
+                   "speedup_vs_table_resident": round(t_table / (t_max / args.steps), 2),
+                   "wind_series_ms_per_step": round(t_series * 1e3, 3)}
     sim.close()
     del sim
 

@@ -151,6 +151,19 @@ JWF_API jwf_status jwf_precompute_probs(jwf_ctx* ctx, const uint8_t* d_class, co
 JWF_API jwf_status jwf_set_terrain(jwf_ctx* ctx, const uint8_t* d_class, const float* d_dem,
                                    const float* d_wind_speed, const float* d_wind_dir, void* stream);
 
+/* Wind as a time series (Section 3 indexes wind speed and direction by the
+ * step; Section 4 lets weather change over a run).  d_wind_speed and
+ * d_wind_dir are float [n_steps][N] on the device, borrowed (they must stay
+ * valid while the series is set: the wind part of Eqs. 1-2 is recomputed from
+ * them when the parameters change).  A step of an env at episode step t uses
+ * row min(t, n_steps - 1), so the series restarts with every episode.  Only
+ * the fused kernels (JWF_KERNEL_FUSED, JWF_KERNEL_TILED_FUSED, and AUTO with
+ * terrain set) evaluate rates per step; jwf_step with a table kernel returns
+ * JWF_EUNSUPPORTED while a series is set.  n_steps = 0 returns to the static
+ * wind of jwf_set_terrain.  Allocates device memory when the series grows. */
+JWF_API jwf_status jwf_set_wind_series(jwf_ctx* ctx, int32_t n_steps, const float* d_wind_speed,
+                                       const float* d_wind_dir, void* stream);
+
 /* Replace the tables with caller data: d_q float [cells][8] (required),
  * d_r float [cells][8] (may be NULL; requires JWF_KEEP_RATES otherwise).
  * Device-to-device copies on the stream. */

@@ -47,7 +47,7 @@ void free_all(jwf_ctx* c) {
                     c->d_F0, c->d_q, c->d_r, c->d_t, c->d_episode, c->d_cnt, c->d_flag,
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
-                    c->d_tcnt, c->d_rtiles, c->d_adj};
+                    c->d_tcnt, c->d_rtiles, c->d_adj, c->d_wser};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -286,6 +286,7 @@ jwf_status jwf_set_params(jwf_ctx* ctx, const jwf_params* p) {
     ctx->P = P;
     ctx->have_params = true;
     ctx->wexp_stale = true;
+    ctx->wser_stale = ctx->wser_n > 0;
     return JWF_OK;
 }
 
@@ -341,6 +342,41 @@ jwf_status jwf_set_terrain(jwf_ctx* ctx, const uint8_t* d_class, const float* d_
     ctx->t_wd = d_wind_dir;
     ctx->have_terrain = true;
     ctx->wexp_stale = false;
+    return JWF_OK;
+}
+
+jwf_status jwf_set_wind_series(jwf_ctx* ctx, int32_t n_steps, const float* d_wind_speed,
+                               const float* d_wind_dir, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (n_steps < 0) return fail(ctx, JWF_EINVAL, "jwf_set_wind_series: n_steps < 0");
+    if (n_steps == 0) {
+        ctx->wser_n = 0;
+        return JWF_OK;
+    }
+    if (d_wind_speed == nullptr || d_wind_dir == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_set_wind_series: null pointer");
+    if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_set_wind_series: no parameters set");
+    const int64_t need = (int64_t)n_steps * ctx->N * 8;
+    if (need > ctx->wser_cap) {
+        float2* p = nullptr;
+        const cudaError_t err = cudaMalloc(&p, (size_t)need * sizeof(float2));
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, err == cudaErrorMemoryAllocation ? JWF_ENOMEM : JWF_ECUDA,
+                        "jwf_set_wind_series: allocation failed");
+        }
+        if (ctx->d_wser != nullptr) {
+            cudaStreamSynchronize(S(stream));
+            cudaFree(ctx->d_wser);
+        }
+        ctx->d_wser = p;
+        ctx->wser_cap = need;
+    }
+    ctx->wser_n = n_steps;
+    ctx->s_ws = d_wind_speed;
+    ctx->s_wd = d_wind_dir;
+    JWF_CUDA_TRY(ctx, jwf_launch_wind_series(ctx, S(stream)), "jwf_set_wind_series");
+    ctx->wser_stale = false;
     return JWF_OK;
 }
 
@@ -414,6 +450,12 @@ jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_
         if (fused) return fail(ctx, JWF_EUNSUPPORTED, "jwf_step: auto-reset on large grids needs the table");
         tiled = false;
         plain = true;
+    }
+    if (ctx->wser_n > 0 && !fused)
+        return fail(ctx, JWF_EUNSUPPORTED, "jwf_step: a wind series needs a fused kernel (rates from the terrain)");
+    if (fused && ctx->wser_n > 0 && ctx->wser_stale) {
+        JWF_CUDA_TRY(ctx, jwf_launch_wind_series(ctx, S(stream)), "jwf_step");
+        ctx->wser_stale = false;
     }
     cudaError_t err;
     if (fused && ctx->wexp_stale) {

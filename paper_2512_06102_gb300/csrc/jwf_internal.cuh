@@ -154,6 +154,14 @@ struct jwf_ctx {
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[JWF_MAX_GROUPS] = {};
     bool wexp_stale = true;              // parameters changed since d_wexp was built
+    // wind time series (fused kernels): [wser_n][N][8] wind exponents of the
+    // series' steps, from borrowed [wser_n][N] speed and direction arrays
+    float2* d_wser = nullptr;
+    int64_t wser_cap = 0;                // float2 entries allocated
+    int32_t wser_n = 0;                  // steps in the series (0: static wind)
+    const float* s_ws = nullptr;
+    const float* s_wd = nullptr;
+    bool wser_stale = false;
 
     JwfDevParams P{};
     bool have_params = false, have_table = false, have_rates = false, have_state = false;
@@ -169,6 +177,7 @@ struct jwf_ctx {
 // Launchers (host functions; each returns cudaGetLastError() of its launch).
 // ---------------------------------------------------------------------------
 cudaError_t jwf_launch_wind_exponent(const jwf_ctx* c, const float* ws, const float* wd, cudaStream_t s);
+cudaError_t jwf_launch_wind_series(jwf_ctx* c, cudaStream_t s);
 cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
                                   const float* ws, const float* wd, cudaStream_t s);
 cudaError_t jwf_launch_rates_accumulate(const jwf_ctx* c, int32_t n_steps, const float* glam,

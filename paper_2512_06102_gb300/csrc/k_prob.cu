@@ -448,6 +448,16 @@ cudaError_t jwf_launch_wind_exponent(const jwf_ctx* c, const float* ws, const fl
     return cudaGetLastError();
 }
 
+cudaError_t jwf_launch_wind_series(jwf_ctx* c, cudaStream_t s) {
+    // the series is [steps][N]: the same kernel over steps x N "envs"
+    const int64_t n = (int64_t)c->wser_n * c->N;
+    if (n == 0) return cudaSuccess;
+    k_wind_exponent<<<(unsigned)((n * 8 + 255) / 256), 256, 0, s>>>((int32_t)n, c->s_ws, c->s_wd,
+                                                                   (double)c->P.alpha_w1, (double)c->P.alpha_w2,
+                                                                   c->d_wser);
+    return cudaGetLastError();
+}
+
 cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
                                   const float* ws, const float* wd, cudaStream_t s) {
     RateConsts K;

@@ -43,7 +43,8 @@ struct ResArgs {
     const float* q;             // table variant
     const uint8_t* cls;         // fused variant: landcover, elevation, wind exponent
     const float* dem;
-    const float2* wexp;         // [N][8] (hi, lo)
+    const float2* wexp;         // [N][8] (hi, lo), or [wser_n][N][8] for a wind series
+    int32_t wser_n;             // steps of the wind series (0: static wind)
     const int32_t* drops;       // [k][N][2] or null
     int32_t* t;
     int32_t* episode;
@@ -219,7 +220,9 @@ __device__ __forceinline__ bool pair_ignites(const Args& a, const RateConsts& K,
     const int64_t u = off + (int64_t)(yy - jwf_dr(d)) * W + (xx - jwf_dx(d));
     const int cv = a.cls[v], cu = a.cls[u];
     const float zv = a.dem[v], zu = a.dem[u];
-    const float2 w2 = a.wexp[e * 8 + d];
+    // a wind series is indexed by the step within the episode (held at its last entry)
+    const int ts = a.wser_n > 0 ? min((int)tt, a.wser_n - 1) : 0;
+    const float2 w2 = a.wexp[((int64_t)ts * a.N + e) * 8 + d];
     const uint4 u4 = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + (uint32_t)(d >> 2)), a.key0, a.key1);
     const uint32_t uw = (d & 3) == 0 ? u4.x : (d & 3) == 1 ? u4.y : (d & 3) == 2 ? u4.z : u4.w;
     const float r = rate_of(K.G[cv][cu], zv, zu, {w2.x, w2.y}, d, K);
@@ -695,6 +698,7 @@ struct TileArgs {
     const uint8_t* cls;
     const float* dem;
     const float2* wexp;
+    int32_t wser_n;
     const int32_t* drops;        // [kb][N][2] of this round, or null
     const int32_t* t;            // step counters at the start of the round
     const int32_t* episode;
@@ -1360,7 +1364,8 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         a.q = c->d_q;
         a.cls = c->t_cls;
         a.dem = c->t_dem;
-        a.wexp = c->d_wexp;
+        a.wexp = c->wser_n > 0 ? c->d_wser : c->d_wexp;
+        a.wser_n = c->wser_n;
         a.drops = drops ? drops + (int64_t)s0 * c->N * 2 : nullptr;
         a.t = c->d_t;
         a.episode = c->d_episode;
@@ -1426,7 +1431,8 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
     a.q = c->d_q;
     a.cls = c->t_cls;
     a.dem = c->t_dem;
-    a.wexp = c->d_wexp;
+    a.wexp = c->wser_n > 0 ? c->d_wser : c->d_wexp;
+    a.wser_n = c->wser_n;
     a.drops = drops;
     a.t = c->d_t;
     a.episode = c->d_episode;

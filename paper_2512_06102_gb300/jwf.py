@@ -70,6 +70,7 @@ _SIGS = {
     "jwf_step": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP]),
     "jwf_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int32]),
     "jwf_set_relaxed_kernel": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "jwf_set_wind_series": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP]),
     "jwf_set_pair_counter": (ctypes.c_int, [_VP, _VP]),
     "jwf_size_classes": (ctypes.c_int32, [_VP, _VP]),
     "jwf_set_class_threads": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
@@ -253,6 +254,16 @@ class Sim:
         self._terrain = (cls, dem, wind_speed, wind_dir)     # keep the buffers alive
         self._check(lib().jwf_set_terrain(self._h, _ptr(cls), _ptr(dem), _ptr(wind_speed), _ptr(wind_dir),
                                           _stream(stream)), "jwf_set_terrain")
+
+    def set_wind_series(self, wind_speed=None, wind_dir=None, stream=None):
+        """Per-step wind, float [steps, N] each (None: back to static wind)."""
+        if wind_speed is None:
+            self._wser = None
+            self._check(lib().jwf_set_wind_series(self._h, 0, None, None, _stream(stream)), "jwf_set_wind_series")
+            return
+        self._wser = (wind_speed, wind_dir)     # keep the borrowed buffers alive
+        self._check(lib().jwf_set_wind_series(self._h, int(wind_speed.shape[0]), _ptr(wind_speed), _ptr(wind_dir),
+                                              _stream(stream)), "jwf_set_wind_series")
 
     def set_probs(self, q, r=None, stream=None):
         self.tables_version += 1
