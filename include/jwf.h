@@ -211,6 +211,27 @@ JWF_API jwf_status jwf_apply_action(jwf_ctx* ctx, const uint8_t* d_mask, void* s
 JWF_API jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
                     int32_t* d_burnt, uint8_t* d_done, void* stream);
 
+/* jwf_step that also records the state after every step: d_history is uint8
+ * [k][cells] on the device (row s = the state after step s, after an
+ * auto-reset the restarted state; caller-owned).  The trajectory is the one
+ * jwf_step produces.  The tiled kernels run one step per launch while
+ * recording.  Errors as jwf_step; JWF_EINVAL when d_history is NULL. */
+JWF_API jwf_status jwf_step_record(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
+                                   int32_t* d_burnt, uint8_t* d_done, uint8_t* d_history, void* stream);
+
+/* Replace the Philox key (the seed of jwf_create) for the following steps,
+ * e.g. to draw a new sample of the same episode. */
+JWF_API jwf_status jwf_set_seed(jwf_ctx* ctx, uint64_t seed);
+
+/* Discrete states (uint8 [n][cells]) to relaxed planes (float [n][cells]
+ * each): p_un = 1 for no-fuel and can-burn cells, p_burn = 1 for burning
+ * cells, 0 otherwise (p_bd = 1 for burned cells is implicit).  With these
+ * planes one relaxed step (Eqs. 5-10) is the expectation of the stochastic
+ * step from the same state, which makes them the linearisation points of a
+ * straight-through backward along a sampled trajectory. */
+JWF_API jwf_status jwf_state_planes(jwf_ctx* ctx, int32_t n, const uint8_t* d_states, float* d_pun,
+                                    float* d_pburn, void* stream);
+
 /* Kernel choice for jwf_step (default JWF_KERNEL_AUTO: resident when every
  * env fits shared memory, else tiled, else (auto-reset) plain).  All kernels
  * give identical results for the same probabilities. */

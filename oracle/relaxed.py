@@ -62,3 +62,29 @@ def calibration_loss(p_un_T: torch.Tensor, target: torch.Tensor, pool: int = 4,
     bce = torch.nn.functional.binary_cross_entropy(pred, target)
     mse = ((avg_pool(pred, pool) - avg_pool(target, pool)) ** 2).mean()
     return bce + w_mse * mse
+
+
+def straight_through_grad(states, r_of_theta, theta, a_un, a_burn):
+    """Reference gradient of the straight-through rollout: the adjoint of the
+    relaxed step (Eqs. 5-10) chained backward along a sampled discrete
+    trajectory, each step linearised at the hard planes of the state before
+    it (p_un = [no fuel or can burn], p_burn = [burning]).
+
+    states: list of T int arrays [N, H, W] (the state before each step);
+    r_of_theta(th) -> rates [N, H, W, 8] (FP64, differentiable in th);
+    theta: FP64 parameter vector whose entry 5 is p_continue; a_un, a_burn:
+    adjoints of the final planes.  Returns dL/dtheta."""
+    a_u = torch.as_tensor(a_un, dtype=torch.float64)
+    a_b = torch.as_tensor(a_burn, dtype=torch.float64)
+    g = torch.zeros_like(theta, dtype=torch.float64)
+    for x in reversed(states):
+        x = torch.as_tensor(x)
+        pu = (x <= 1).to(torch.float64).requires_grad_(True)
+        pb = (x == 2).to(torch.float64).requires_grad_(True)
+        th = theta.detach().clone().requires_grad_(True)
+        ou, ob = relaxed_step(pu, pb, r_of_theta(th), th[5])
+        L = (a_u * ou).sum() + (a_b * ob).sum()
+        gu, gb, gt = torch.autograd.grad(L, [pu, pb, th])
+        g = g + gt
+        a_u, a_b = gu, gb
+    return g

@@ -429,6 +429,16 @@ jwf_status jwf_apply_action(jwf_ctx* ctx, const uint8_t* d_mask, void* stream) {
     return JWF_OK;
 }
 
+jwf_status jwf_step_record(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
+                           int32_t* d_burnt, uint8_t* d_done, uint8_t* d_history, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_history == nullptr) return fail(ctx, JWF_EINVAL, "jwf_step_record: d_history is null");
+    ctx->hist = d_history;
+    const jwf_status st = jwf_step(ctx, k, d_drops, d_burning, d_burnt, d_done, stream);
+    ctx->hist = nullptr;
+    return st;
+}
+
 jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
                     int32_t* d_burnt, uint8_t* d_done, void* stream) {
     if (ctx == nullptr) return JWF_EINVAL;
@@ -472,6 +482,24 @@ jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_
             err = jwf_launch_step_resident(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
     }
     if (err != cudaSuccess) return cuda_fail(ctx, err, "jwf_step");
+    return JWF_OK;
+}
+
+jwf_status jwf_set_seed(jwf_ctx* ctx, uint64_t seed) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    ctx->seed = seed;
+    return JWF_OK;
+}
+
+jwf_status jwf_state_planes(jwf_ctx* ctx, int32_t n, const uint8_t* d_states, float* d_pun, float* d_pburn,
+                            void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (n < 0) return fail(ctx, JWF_EINVAL, "jwf_state_planes: n < 0");
+    if (d_states == nullptr || d_pun == nullptr || d_pburn == nullptr)
+        return fail(ctx, JWF_EINVAL, "jwf_state_planes: null pointer");
+    if (n == 0) return JWF_OK;
+    JWF_CUDA_TRY(ctx, jwf_launch_state_planes((int64_t)n * ctx->cells, d_states, d_pun, d_pburn, S(stream)),
+                 "jwf_state_planes");
     return JWF_OK;
 }
 

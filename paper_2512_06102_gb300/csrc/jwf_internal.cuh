@@ -162,6 +162,7 @@ struct jwf_ctx {
     const float* s_ws = nullptr;
     const float* s_wd = nullptr;
     bool wser_stale = false;
+    uint8_t* hist = nullptr;             // during a recording jwf_step: [k][cells] states after each step
 
     JwfDevParams P{};
     bool have_params = false, have_table = false, have_rates = false, have_state = false;
@@ -178,6 +179,7 @@ struct jwf_ctx {
 // ---------------------------------------------------------------------------
 cudaError_t jwf_launch_wind_exponent(const jwf_ctx* c, const float* ws, const float* wd, cudaStream_t s);
 cudaError_t jwf_launch_wind_series(jwf_ctx* c, cudaStream_t s);
+cudaError_t jwf_launch_state_planes(int64_t n, const uint8_t* states, float* pun, float* pburn, cudaStream_t s);
 cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
                                   const float* ws, const float* wd, cudaStream_t s);
 cudaError_t jwf_launch_rates_accumulate(const jwf_ctx* c, int32_t n_steps, const float* glam,

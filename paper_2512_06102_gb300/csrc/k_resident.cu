@@ -52,6 +52,8 @@ struct ResArgs {
     int32_t* out_burnt;
     uint8_t* out_done;
     uint32_t* queue;            // [0] cursor, [1] CTAs finished
+    uint8_t* history;           // [k][cells] state after each step, or null
+    int64_t cells;              // cells of the context (stride of history)
     unsigned long long* counts; // optional [4]: pairs compared, candidate Philox blocks,
                                 // burning-cell draws, bit-plane word-steps scanned
     int32_t k;
@@ -147,8 +149,10 @@ __device__ __forceinline__ uint32_t drop_bits(int y, int w, int W, int cx, int c
     return span << lo;
 }
 
-// Apply a drop to the planes (burning under it -> burned), all threads.
-__device__ void res_action(int H, int W, int WW, uint32_t* Bp, uint32_t* D, int cx, int cy, int R) {
+// Apply a drop to the planes (burning under it -> burned), all threads; adds
+// the number of doused cells to *count when count is not null.
+__device__ void res_action(int H, int W, int WW, uint32_t* Bp, uint32_t* D, int cx, int cy, int R,
+                           int* count = nullptr) {
     if (cx < 0 || cy < 0) return;
     const int y0 = max(cy - R, 0), y1 = min(cy + R, H - 1);
     if (y0 > y1) return;
@@ -162,6 +166,7 @@ __device__ void res_action(int H, int W, int WW, uint32_t* Bp, uint32_t* D, int 
         const uint32_t doused = *bp & m;
         *bp &= ~m;
         D[y * WW + w] |= doused;
+        if (count != nullptr && doused != 0u) atomicAdd(count, __popc(doused));
     }
 }
 
@@ -280,6 +285,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
     __shared__ int32_t s_qn[3];         // queued work items (per step)
     __shared__ int32_t s_ncl[3];        // chunks claimed (per step)
     __shared__ int32_t s_burnt;
+    __shared__ int32_t s_dous;          // cells doused by a drop applied at a step's start
     // the rate constants live in shared memory only in the fused variant
     __shared__ typename std::conditional<FUSED, RateConsts, int>::type sK_store;
     const RateConsts& sK = *reinterpret_cast<const RateConsts*>(&sK_store);
@@ -350,9 +356,26 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         uint32_t* Bc = B0;
         uint32_t* Bn = B1;
         int32_t last_burnt = 0;
+        int hist_done = 0;          // history rows written
+        const bool rec = a.history != nullptr;
         for (int s = 0; s < a.k; ++s) {
             const uint32_t tt = (uint32_t)t;
             const uint32_t ep4 = 4u * (uint32_t)ep;
+            if (rec && s > 0) {
+                // record the state after step s - 1, then apply step s's drop
+                // (when recording it is not folded into the previous write-back)
+                const int64_t ho = (int64_t)(s - 1) * a.cells;
+                res_store(a.history + ho + off, H, W, WW, vec && (ho & 15) == 0, Bc, C, D);
+                hist_done = s;
+                if (threadIdx.x == 0) s_dous = 0;
+                __syncthreads();
+                if (a.drops != nullptr) {
+                    res_action(H, W, WW, Bc, D, a.drops[((int64_t)s * a.N + e) * 2],
+                               a.drops[((int64_t)s * a.N + e) * 2 + 1], a.R, &s_dous);
+                    __syncthreads();
+                    burnt_now += s_dous;
+                }
+            }
             if (threadIdx.x == 0) {
                 s_cnt[(s + 1) % 3][0] = 0;
                 s_cnt[(s + 1) % 3][1] = 0;
@@ -363,7 +386,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
             }
             // the next step's drop is applied while the new planes are written
             int cxn = -1, cyn = -1;
-            if (a.drops != nullptr && s + 1 < a.k) {
+            if (a.drops != nullptr && s + 1 < a.k && !rec) {
                 cxn = a.drops[((int64_t)(s + 1) * a.N + e) * 2];
                 cyn = a.drops[((int64_t)(s + 1) * a.N + e) * 2 + 1];
             }
@@ -642,6 +665,13 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         }
         __syncthreads();
         res_store(Fe, H, W, WW, vec, Bc, C, D);
+        if (a.history != nullptr) {
+            // the last step's state, and the unchanged state of the steps after the fire went out
+            for (int j = hist_done; j < a.k; ++j) {
+                const int64_t ho = (int64_t)j * a.cells;
+                res_store(a.history + ho + off, H, W, WW, vec && (ho & 15) == 0, Bc, C, D);
+            }
+        }
         if (threadIdx.x == 0) {
             a.t[e] = t;
             a.episode[e] = ep;
@@ -1347,7 +1377,8 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         jwf_rate_consts(c, &K);
     else
         K = RateConsts{};
-    const int32_t rs = (c->round_steps >= 1 && c->round_steps <= kMaxRound) ? c->round_steps : kMaxRound;
+    int32_t rs = (c->round_steps >= 1 && c->round_steps <= kMaxRound) ? c->round_steps : kMaxRound;
+    if (c->hist != nullptr) rs = 1;     // recording: the state after every step
     for (int32_t s0 = 0; s0 < k; s0 += rs) {
         const int32_t kb = (k - s0) < rs ? (k - s0) : rs;
         err = cudaMemsetAsync(c->d_tcnt, 0, (size_t)kb * 2 * c->N * sizeof(int32_t), s);
@@ -1396,6 +1427,11 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         if (err != cudaSuccess) return err;
         c->cur ^= 1;
         c->tact_cur ^= 1;
+        if (c->hist != nullptr) {
+            err = cudaMemcpyAsync(c->hist + (int64_t)s0 * c->cells, c->d_state[c->cur], (size_t)c->cells,
+                                  cudaMemcpyDeviceToDevice, s);
+            if (err != cudaSuccess) return err;
+        }
     }
     return cudaSuccess;
 }
@@ -1447,6 +1483,8 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
     a.key0 = (uint32_t)(c->seed & 0xffffffffu);
     a.key1 = (uint32_t)(c->seed >> 32);
     a.p_continue = c->P.p_continue;
+    a.history = c->hist;
+    a.cells = c->cells;
     RateConsts K;
     if (fused)
         jwf_rate_consts(c, &K);

@@ -226,8 +226,30 @@ cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, i
             k_reset<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(c->d_tiles, c->d_H, c->d_W, c->d_off,
                                                                c->d_flag, c->d_F0, c->d_state[c->cur]);
         }
-        const cudaError_t err = cudaGetLastError();
+        cudaError_t err = cudaGetLastError();
+        if (err == cudaSuccess && c->hist != nullptr)
+            err = cudaMemcpyAsync(c->hist + (int64_t)st * c->cells, c->d_state[c->cur], (size_t)c->cells,
+                                  cudaMemcpyDeviceToDevice, s);
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
+}
+
+// Discrete states -> relaxed planes: p_un = [no fuel or can burn], p_burn =
+// [burning] (p_bd = [burned] is implicit), e.g. for a straight-through
+// backward along a sampled trajectory.
+__global__ void k_state_planes(int64_t n, const uint8_t* __restrict__ st, float* __restrict__ pun,
+                               float* __restrict__ pburn) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t v = st[i];
+        pun[i] = v <= 1 ? 1.0f : 0.0f;
+        pburn[i] = v == 2 ? 1.0f : 0.0f;
+    }
+}
+
+cudaError_t jwf_launch_state_planes(int64_t n, const uint8_t* states, float* pun, float* pburn, cudaStream_t s) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    k_state_planes<<<(unsigned)blocks, 256, 0, s>>>(n, states, pun, pburn);
+    return cudaGetLastError();
 }

@@ -71,6 +71,9 @@ _SIGS = {
     "jwf_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int32]),
     "jwf_set_relaxed_kernel": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "jwf_set_wind_series": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP]),
+    "jwf_step_record": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 6),
+    "jwf_set_seed": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "jwf_state_planes": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP]),
     "jwf_set_pair_counter": (ctypes.c_int, [_VP, _VP]),
     "jwf_size_classes": (ctypes.c_int32, [_VP, _VP]),
     "jwf_set_class_threads": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
@@ -309,8 +312,10 @@ class Sim:
         candidate Philox blocks, remain-burning draws, words scanned), or None."""
         self._check(lib().jwf_set_pair_counter(self._h, _ptr(counter)), "jwf_set_pair_counter")
 
-    def step(self, k: int = 1, drops=None, burning=None, burnt=None, done=None, stream=None):
-        """Advance k steps; returns the (burning, burnt, done) tensors [k, N]."""
+    def step(self, k: int = 1, drops=None, burning=None, burnt=None, done=None, stream=None, history=None):
+        """Advance k steps; returns the (burning, burnt, done) tensors [k, N].
+        history: optional uint8 [k, cells] device tensor that receives the
+        state after every step (jwf_step_record)."""
         dev = torch.device("cuda", torch.cuda.current_device())
         if burning is None:
             burning = torch.empty((k, self.N), dtype=torch.int32, device=dev)
@@ -318,9 +323,29 @@ class Sim:
             burnt = torch.empty((k, self.N), dtype=torch.int32, device=dev)
         if done is None:
             done = torch.empty((k, self.N), dtype=torch.uint8, device=dev)
-        self._check(lib().jwf_step(self._h, int(k), _ptr(drops), _ptr(burning), _ptr(burnt), _ptr(done),
-                                   _stream(stream)), "jwf_step")
+        if history is None:
+            self._check(lib().jwf_step(self._h, int(k), _ptr(drops), _ptr(burning), _ptr(burnt), _ptr(done),
+                                       _stream(stream)), "jwf_step")
+        else:
+            if tuple(history.shape) != (k, self.cells) or history.dtype != torch.uint8:
+                raise ValueError("history must be uint8 [k, cells]")
+            self._check(lib().jwf_step_record(self._h, int(k), _ptr(drops), _ptr(burning), _ptr(burnt), _ptr(done),
+                                              _ptr(history), _stream(stream)), "jwf_step_record")
         return burning, burnt, done
+
+    def set_seed(self, seed: int):
+        self._check(lib().jwf_set_seed(self._h, ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF)), "jwf_set_seed")
+
+    def state_planes(self, states, pun=None, pburn=None, stream=None):
+        """uint8 [n, cells] states -> float (p_un, p_burn) planes [n, cells]."""
+        if pun is None:
+            pun = torch.empty(states.shape, dtype=torch.float32, device=states.device)
+        if pburn is None:
+            pburn = torch.empty(states.shape, dtype=torch.float32, device=states.device)
+        n = states.shape[0] if states.dim() == 2 else 1
+        self._check(lib().jwf_state_planes(self._h, int(n), _ptr(states), _ptr(pun), _ptr(pburn), _stream(stream)),
+                    "jwf_state_planes")
+        return pun, pburn
 
     def state_views(self):
         """Borrowed views (state uint8 [cells], t int32 [N], episode int32 [N])."""

@@ -1,4 +1,5 @@
-"""Differentiable relaxed rollout (Section 3, Eqs. 5-10) on libjwf.
+"""Differentiable relaxed rollout (Section 3, Eqs. 5-10) on libjwf, and the
+straight-through rollout (stochastic forward, relaxed backward).
 
 `RelaxedRollout.apply(theta, p_un0, p_burn0, sim, scene, T, masks, ckpt_every)`
 runs T relaxed steps with libjwf's forward kernel and returns (p_un_T,
@@ -158,6 +159,70 @@ class RelaxedRollout(torch.autograd.Function):
 
 def rollout(theta, p_un0, p_burn0, sim, scene, T, masks=None, ckpt_every=None, cell_size=30.0):
     return RelaxedRollout.apply(theta, p_un0, p_burn0, sim, scene, T, masks, ckpt_every, cell_size)
+
+
+class StraightThroughRollout(torch.autograd.Function):
+    """Straight-through rollout: the forward runs T steps of the stochastic
+    update (Section 3) from the discrete states F0 and returns the hard planes
+    (p_un_T, p_burn_T) of the sampled last state; the backward is the adjoint
+    of the relaxed step (Eqs. 5-10) evaluated along the sampled trajectory
+    (libjwf's adjoint kernels on jwf_state_planes of the recorded states),
+    which gives gradients with respect to theta (the rates and p_continue).
+    The sample depends on the context's seed (Sim.set_seed).
+
+    With build_tables the context's tables are rebuilt from theta and the
+    scene (the context needs JWF_KEEP_RATES); otherwise the caller's tables
+    (jwf_set_probs with rates) are used as they are, and theta must match them
+    for the gradient to mean anything."""
+
+    @staticmethod
+    def forward(ctx, theta, sim: jwf.Sim, scene, F0, T: int, build_tables: bool = True, cell_size: float = 30.0):
+        cls, dem, ws, wd = scene
+        if build_tables:
+            sim.set_params(theta_to_params(theta, sim.n_classes, cell_size))
+            sim.precompute_probs(cls, dem, ws, wd)
+        hist = torch.empty((T, sim.cells), dtype=torch.uint8, device=F0.device)
+        sim.load_state(F0)
+        sim.step(T, None, history=hist)
+        pu, pb = sim.state_planes(hist[T - 1:T])
+        ctx.sim, ctx.scene, ctx.T, ctx.hist, ctx.F0 = sim, scene, T, hist, F0
+        ctx.theta_device = theta.device
+        return pu[0], pb[0]
+
+    @staticmethod
+    def backward(ctx, g_un, g_burn):
+        sim, T = ctx.sim, ctx.T
+        cls, dem, ws, wd = ctx.scene
+        dev = ctx.F0.device
+        cells = sim.cells
+        states = torch.cat([ctx.F0.reshape(1, -1), ctx.hist[:T - 1]], 0)      # state before each step
+        PU, PB = sim.state_planes(states)
+        gparams = torch.zeros(sim.grad_size, dtype=torch.float64, device=dev)
+        gpc = torch.zeros(1, dtype=torch.float64, device=dev)
+        gu = (g_un if g_un is not None else torch.zeros(cells, device=dev)).contiguous().clone()
+        gb = (g_burn if g_burn is not None else torch.zeros(cells, device=dev)).contiguous().clone()
+        ngu, ngb = torch.empty_like(gu), torch.empty_like(gb)
+        glam = torch.empty((CHUNK, cells), dtype=torch.float32, device=dev)
+        gr = torch.zeros((cells, 8), dtype=torch.float32, device=dev)
+        hi = T
+        while hi > 0:
+            lo = ((hi - 1) // CHUNK) * CHUNK
+            sim.relaxed_bwd_steps(PU[lo:hi], PB[lo:hi], gu, gb, ngu, ngb, glam=glam[:hi - lo], gpc=gpc)
+            gu, ngu = ngu, gu
+            gb, ngb = ngb, gb
+            sim.rates_accumulate(glam[:hi - lo], PB[lo:hi], gr)
+            hi = lo
+        sim.rates_contract(gr, cls, dem, ws, wd, gparams)
+        C = sim.n_classes
+        g = torch.empty(6 + 2 * C, dtype=torch.float64, device=dev)
+        g[0:5] = gparams[0:5]
+        g[5] = gpc[0]
+        g[6:] = gparams[5:]
+        return (g.to(ctx.theta_device), None, None, None, None, None, None)
+
+
+def straight_through(theta, sim, scene, F0, T, build_tables=True, cell_size=30.0):
+    return StraightThroughRollout.apply(theta, sim, scene, F0, T, build_tables, cell_size)
 
 
 def calibration_loss(p_un_T: torch.Tensor, target: torch.Tensor, H: int, W: int, pool: int = 4,
