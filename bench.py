@@ -40,6 +40,7 @@ N_ENVS, SIDE, EPISODE = 4096, 128, 200
 REL_ENVS, REL_T = 256, 100
 RAG_ENVS, RAG_T, RAG_TMAX = 10000, 500, 200
 BIG_ENVS, BIG_SIDE, BIG_T = 8, 4096, 1000
+TANK_ENVS, TANK_SIDE, TANK_T = 16384, 20, 500
 METRIC = "CA cell-updates/s at 4096x128^2 (200-step episode with tanker drops)"
 CPU_SAMPLE_ENVS = 48
 # lane-operation model of the step (instruction counts of the work the model
@@ -61,6 +62,7 @@ def parse():
     ap.add_argument("--no-relaxed", action="store_true")
     ap.add_argument("--no-rollout", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-tanker", action="store_true")
     ap.add_argument("--profile", choices=["resident", "relaxed", "tiled"], default=None,
                     help="run one small case of a kernel family once (for ncu captures); prints no bench line")
     return ap.parse_args()
@@ -361,6 +363,9 @@ def run_ours(args):
     big = None
     if not args.no_large:
         big = bench_large(args, D, dev, rank)
+    tank = None
+    if not args.no_tanker:
+        tank = bench_tanker(args, D, dev, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -387,6 +392,8 @@ def run_ours(args):
         line["rollout"] = rag
     if big is not None:
         line["large"] = big
+    if tank is not None:
+        line["tanker"] = tank
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -584,6 +591,63 @@ def bench_large(args, D, dev, rank):
                                         "word_steps": words}},
             "comparators": {"plain_one_launch_per_step_ms_per_1000": round(t_plain200 * 5e3, 1),
                             "speedup_vs_plain": round(t_plain200 * 5 / best, 2)}}
+
+
+def bench_tanker(args, D, dev, rank):
+    """The air-tanker agent scenario of Section 4: 16,384 grids of 20 x 20, one
+    agent each (move + valve, 10 units of water, 5 x 5 egocentric window),
+    500 agent steps with random actions and auto-reset (random agent position
+    and ignition every episode, episode limit 100), as one CUDA graph; eager
+    steps and the plain one-launch-per-step kernel as comparators."""
+    import torch
+
+    from paper_2512_06102_gb300 import jwf, scenarios, tanker
+
+    scn = scenarios.make_scenario(TANK_SIDE, TANK_SIDE, N=TANK_ENVS, seed=300 + rank)
+    F0 = scn.F0.copy()
+    F0[F0 == 2] = 1
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    acts = torch.randint(0, 10, (TANK_T, TANK_ENVS), dtype=torch.int32, device=dev,
+                         generator=torch.Generator(device=dev).manual_seed(5))
+    stream = torch.cuda.current_stream()
+
+    def run(kernel, graph):
+        sim = jwf.Sim(TANK_SIDE, TANK_SIDE, n_envs=TANK_ENVS, n_classes=scenarios.N_CLASSES, seed=rank,
+                      auto_reset=True, t_max=100)
+        sim.set_params(scn.params)
+        sim.set_terrain(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+        if kernel == jwf.KERNEL_PLAIN:
+            sim.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+        sim.set_kernel(kernel)
+        env = tanker.TankerEnv(sim, to(F0), water0=10, obs_k=5, burn_penalty=0.01, random_fire=True)
+        env.reset()
+        g = tanker.GraphTankerRollout(env, acts, capture=graph)
+        best = float("inf")
+        for _ in range(max(1, args.warmup) + 2):
+            env.reset()
+            torch.cuda.synchronize()
+            D.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rw = g.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, D.max(e0.elapsed_time(e1) / 1e3))
+        ret = float(rw.sum().item()) / TANK_ENVS
+        episodes = int(g.dones.sum().item())
+        sim.close()
+        return best, ret, episodes
+
+    t_graph, ret, episodes = run(jwf.KERNEL_FUSED, True)
+    t_eager, _, _ = run(jwf.KERNEL_FUSED, False)
+    t_plain, _, _ = run(jwf.KERNEL_PLAIN, True)
+    return {"metric": "agent env-steps/s, 16384 x 20^2 tanker scenario, 500 steps, auto-reset (one CUDA graph)",
+            "value": D.world * TANK_ENVS * TANK_T / t_graph, "unit": "env-steps/s",
+            "ms_per_rollout": round(t_graph * 1e3, 3), "launches_per_step": 3,
+            "episodes_finished": episodes, "mean_return_random_policy": round(ret, 3),
+            "comparators": {"eager_ms": round(t_eager * 1e3, 3), "plain_kernel_graph_ms": round(t_plain * 1e3, 3),
+                            "speedup_vs_eager": round(t_eager / t_graph, 2),
+                            "speedup_vs_plain": round(t_plain / t_graph, 2)}}
 
 
 def bench_rollout(args, D, dev, rank):

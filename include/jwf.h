@@ -285,6 +285,39 @@ JWF_API jwf_status jwf_set_pair_counter(jwf_ctx* ctx, unsigned long long* d_coun
  * counters t and episode numbers (valid until the next call on ctx). */
 JWF_API jwf_status jwf_get_state(jwf_ctx* ctx, uint8_t** d_state, int32_t** d_t, int32_t** d_episode);
 
+/* ---- air-tanker agent environment (Section 4) ---------------------------- */
+
+/* An agent per env moves over the grid and controls a valve that drops a
+ * limited amount of water (water turns burning cells into burned cells);
+ * it observes an egocentric window of the fire state; each step is penalised
+ * per burning cell and an extinguished fire earns +10.  The paper states
+ * these ingredients, not their details; this library's readings:
+ *   d_agent: int32 [N][3] = (x, y, water) per env, device, caller-owned;
+ *   action a in [0, 10): move = a % 5 (0 stay, 1 north = row - 1, 2 east =
+ *     column + 1, 3 south, 4 west; clamped to the grid); the valve is open
+ *     when a >= 5; other values count as 0;
+ *   an open valve with water > 0 drops water on the drop footprint (radius
+ *     drop_radius of jwf_config) centred on the agent's new cell and uses
+ *     one unit; the drop is this step's action (applied before the spread);
+ *   reward = -burn_penalty * (burning cells after the step) + (10 if none);
+ *   observation: uint8 [N][obs_k][obs_k] (obs_k odd, <= 63), the states
+ *     centred on the agent, 255 outside the grid (d_obs may be NULL);
+ *   restart (jwf_agent_reset, and after a step that an auto-reset context
+ *     restarted): Philox4x32-10 with the context's key and counter (0, 0,
+ *     env, 4 * episode + 3): x = floor(u(w0) * W), y = floor(u(w1) * H),
+ *     water = water0; with random_fire the first can-burn cell at or after
+ *     cell floor(u(w2) * H * W) (row-major, wrapping) starts burning.
+ * jwf_agent_step = move/valve, one jwf_step (k = 1, any kernel; use
+ * JWF_AUTO_RESET for continuing episodes), reward, restarts, observation;
+ * d_actions int32 [N], d_reward float [N] and d_done uint8 [N] (both may be
+ * NULL).  Errors: JWF_EINVAL for null d_agent/d_actions, water0 < 0 or a bad
+ * obs_k; otherwise as jwf_step. */
+JWF_API jwf_status jwf_agent_reset(jwf_ctx* ctx, int32_t* d_agent, int32_t water0, int32_t random_fire,
+                                   int32_t obs_k, uint8_t* d_obs, void* stream);
+JWF_API jwf_status jwf_agent_step(jwf_ctx* ctx, const int32_t* d_actions, int32_t* d_agent, int32_t water0,
+                                  int32_t random_fire, float burn_penalty, float* d_reward, uint8_t* d_done,
+                                  int32_t obs_k, uint8_t* d_obs, void* stream);
+
 /* ---- relaxed (raw-probabilities) update, Eqs. 5-10 ----------------------- */
 
 /* Kernels of the relaxed step.  JWF_RELAXED_TILED (default): persistent CTAs

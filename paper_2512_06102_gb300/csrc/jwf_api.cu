@@ -47,7 +47,8 @@ void free_all(jwf_ctx* c) {
                     c->d_F0, c->d_q, c->d_r, c->d_t, c->d_episode, c->d_cnt, c->d_flag,
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
-                    c->d_tcnt, c->d_rtiles, c->d_adj, c->d_wser};
+                    c->d_tcnt, c->d_rtiles, c->d_adj, c->d_wser, c->d_agent_drops, c->d_agent_cnt,
+                    c->d_agent_done};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -191,6 +192,9 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_gr, (size_t)c->cells * 8);
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_adj, (size_t)c->cells * 2);
     if (err == cudaSuccess) err = dev_alloc(&c->d_rtiles, rtiles.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_agent_drops, 2 * (size_t)N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_agent_cnt, (size_t)N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_agent_done, (size_t)N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_t, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_episode, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_cnt, 2 * (size_t)N);
@@ -482,6 +486,49 @@ jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_
             err = jwf_launch_step_resident(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
     }
     if (err != cudaSuccess) return cuda_fail(ctx, err, "jwf_step");
+    return JWF_OK;
+}
+
+namespace {
+jwf_status agent_args(jwf_ctx* ctx, const char* who, int32_t* d_agent, int32_t water0, int32_t obs_k, uint8_t* d_obs) {
+    if (d_agent == nullptr) return fail(ctx, JWF_EINVAL, who);
+    if (water0 < 0) return fail(ctx, JWF_EINVAL, who);
+    if (d_obs != nullptr && (obs_k < 1 || obs_k > 63 || obs_k % 2 == 0)) return fail(ctx, JWF_EINVAL, who);
+    return JWF_OK;
+}
+}  // namespace
+
+jwf_status jwf_agent_reset(jwf_ctx* ctx, int32_t* d_agent, int32_t water0, int32_t random_fire, int32_t obs_k,
+                           uint8_t* d_obs, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    const jwf_status st = agent_args(ctx, "jwf_agent_reset: bad argument", d_agent, water0, obs_k, d_obs);
+    if (st != JWF_OK) return st;
+    if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_agent_reset: no state loaded");
+    JWF_CUDA_TRY(ctx, jwf_launch_agent_post(ctx, 1, d_agent, water0, random_fire ? 1 : 0, 0.0f, nullptr, obs_k,
+                                            d_obs, S(stream)),
+                 "jwf_agent_reset");
+    ctx->tiles_valid = false;
+    return JWF_OK;
+}
+
+jwf_status jwf_agent_step(jwf_ctx* ctx, const int32_t* d_actions, int32_t* d_agent, int32_t water0,
+                          int32_t random_fire, float burn_penalty, float* d_reward, uint8_t* d_done, int32_t obs_k,
+                          uint8_t* d_obs, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_actions == nullptr) return fail(ctx, JWF_EINVAL, "jwf_agent_step: d_actions is null");
+    const jwf_status st = agent_args(ctx, "jwf_agent_step: bad argument", d_agent, water0, obs_k, d_obs);
+    if (st != JWF_OK) return st;
+    JWF_CUDA_TRY(ctx, jwf_launch_agent_act(ctx, d_actions, d_agent, S(stream)), "jwf_agent_step");
+    const jwf_status ss = jwf_step(ctx, 1, ctx->d_agent_drops, ctx->d_agent_cnt, nullptr, ctx->d_agent_done, stream);
+    if (ss != JWF_OK) return ss;
+    JWF_CUDA_TRY(ctx, jwf_launch_agent_post(ctx, 0, d_agent, water0, random_fire ? 1 : 0, burn_penalty, d_reward,
+                                            obs_k, d_obs, S(stream)),
+                 "jwf_agent_step");
+    if (d_done != nullptr)
+        JWF_CUDA_TRY(ctx, cudaMemcpyAsync(d_done, ctx->d_agent_done, (size_t)ctx->N, cudaMemcpyDeviceToDevice,
+                                          S(stream)),
+                     "jwf_agent_step");
+    ctx->tiles_valid = false;
     return JWF_OK;
 }
 

@@ -163,6 +163,9 @@ struct jwf_ctx {
     const float* s_wd = nullptr;
     bool wser_stale = false;
     uint8_t* hist = nullptr;             // during a recording jwf_step: [k][cells] states after each step
+    int32_t* d_agent_drops = nullptr;    // [N][2] drop centres of an agent step
+    int32_t* d_agent_cnt = nullptr;      // [N] burning cells after an agent step
+    uint8_t* d_agent_done = nullptr;     // [N] done flags of an agent step
 
     JwfDevParams P{};
     bool have_params = false, have_table = false, have_rates = false, have_state = false;
@@ -179,6 +182,9 @@ struct jwf_ctx {
 // ---------------------------------------------------------------------------
 cudaError_t jwf_launch_wind_exponent(const jwf_ctx* c, const float* ws, const float* wd, cudaStream_t s);
 cudaError_t jwf_launch_wind_series(jwf_ctx* c, cudaStream_t s);
+cudaError_t jwf_launch_agent_act(const jwf_ctx* c, const int32_t* actions, int32_t* agent, cudaStream_t s);
+cudaError_t jwf_launch_agent_post(const jwf_ctx* c, int mode, int32_t* agent, int32_t water0, int random_fire,
+                                  float burn_penalty, float* reward, int32_t obs_k, uint8_t* obs, cudaStream_t s);
 cudaError_t jwf_launch_state_planes(int64_t n, const uint8_t* states, float* pun, float* pburn, cudaStream_t s);
 cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
                                   const float* ws, const float* wd, cudaStream_t s);

@@ -73,6 +73,9 @@ _SIGS = {
     "jwf_set_wind_series": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP]),
     "jwf_step_record": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 6),
     "jwf_set_seed": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "jwf_agent_reset": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
+    "jwf_agent_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _VP, _VP,
+                                      ctypes.c_int32, _VP, _VP]),
     "jwf_state_planes": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP]),
     "jwf_set_pair_counter": (ctypes.c_int, [_VP, _VP]),
     "jwf_size_classes": (ctypes.c_int32, [_VP, _VP]),
@@ -332,6 +335,16 @@ class Sim:
             self._check(lib().jwf_step_record(self._h, int(k), _ptr(drops), _ptr(burning), _ptr(burnt), _ptr(done),
                                               _ptr(history), _stream(stream)), "jwf_step_record")
         return burning, burnt, done
+
+    def agent_reset(self, agent, water0: int, random_fire: bool = True, obs_k: int = 5, obs=None, stream=None):
+        self._check(lib().jwf_agent_reset(self._h, _ptr(agent), int(water0), int(bool(random_fire)), int(obs_k),
+                                          _ptr(obs), _stream(stream)), "jwf_agent_reset")
+
+    def agent_step(self, actions, agent, water0: int, random_fire: bool = True, burn_penalty: float = 0.01,
+                   reward=None, done=None, obs_k: int = 5, obs=None, stream=None):
+        self._check(lib().jwf_agent_step(self._h, _ptr(actions), _ptr(agent), int(water0), int(bool(random_fire)),
+                                         ctypes.c_float(burn_penalty), _ptr(reward), _ptr(done), int(obs_k),
+                                         _ptr(obs), _stream(stream)), "jwf_agent_step")
 
     def set_seed(self, seed: int):
         self._check(lib().jwf_set_seed(self._h, ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF)), "jwf_set_seed")
