@@ -175,11 +175,12 @@ k_relaxed_bwd_b(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
 // Tiled variant: 2-D tiles of kRH x kRW cells, staged in shared memory by
 // asynchronous copies.  Each warp covers 32 consecutive cells of a row, so the
 // rate rows (32 B a cell) stream in 1 KB runs.  The adjoint recomputes lam on
-// the tile and a one-cell halo, keeps glam and the rate rows of that region in
-// shared memory (rates transposed to [d][cell] so that the gather reads
-// consecutive words), and gathers dL/dp_burn from there: one kernel, no glam
-// round trip, each rate row read once (plus the halo's).  Sums run over
-// d = 0..7 in the same order as the plain kernels.
+// the tile and a one-cell halo, keeps the products glam(v) r(v, d) of that
+// region in shared memory ([d][cell], so that the gather reads consecutive
+// words), and gathers dL/dp_burn from there: one kernel, no glam round trip,
+// each rate row read once (plus the halo's).  Sums run over d = 0..7 in the
+// order of the plain kernels (the gather adds rounded products where the
+// plain kernel fuses multiply and add).
 constexpr int kRH = JWF_RT_ROWS, kRW = JWF_RT_COLS;
 
 
@@ -295,8 +296,7 @@ struct BwdStage {
 };
 struct BwdSmem {
     BwdStage st;
-    float rt[8][kEN];       // rates transposed for the gather
-    float gl[kEN];
+    float P[8][kEN];        // glam(v) r(v, d), [d][cell] so that the gather reads consecutive words
     double red[kBT / 32];
 };
 size_t bwd_smem_bytes() { return sizeof(BwdSmem); }
@@ -391,9 +391,8 @@ k_relaxed_bwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32
                     if (pbv != 0.f) acc += (double)(ab * pbv);
                 }
             }
-            S.gl[i] = g;
 #pragma unroll
-            for (int d = 0; d < 8; ++d) S.rt[d][i] = rv[d];
+            for (int d = 0; d < 8; ++d) S.P[d][i] = g * rv[d];
         }
         __syncthreads();
         // dL/dp_burn(u) = (1 - m(u)) (p_continue a_b(u) + sum_d glam(u + Delta_d) r[u + Delta_d][d])
@@ -405,11 +404,7 @@ k_relaxed_bwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32
             const float abu = b.ab[ei];
             float g = p_continue != 0.f ? p_continue * abu : 0.f;
 #pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const int li = (ty + 1 + jwf_dr(d)) * kEW + (tx + 1 + jwf_dx(d));
-                const float rv = S.rt[d][li], gl = S.gl[li];
-                if (rv != 0.f && gl != 0.f) g += gl * rv;
-            }
+            for (int d = 0; d < 8; ++d) g += S.P[d][(ty + 1 + jwf_dr(d)) * kEW + (tx + 1 + jwf_dx(d))];
             if (mask != nullptr) {
                 const float keep = 1.0f - b.m[(ty + 2) * kPW + tx + 2];
                 g = keep != 0.f ? g * keep : 0.f;
