@@ -694,7 +694,7 @@ def bench_tanker(args, D, dev, rank):
     t_plain, _, _ = run(jwf.KERNEL_PLAIN, True)
     return {"metric": "agent env-steps/s, 16384 x 20^2 tanker scenario, 500 steps, auto-reset (one CUDA graph)",
             "value": D.world * TANK_ENVS * TANK_T / t_graph, "unit": "env-steps/s",
-            "ms_per_rollout": round(t_graph * 1e3, 3), "launches_per_step": 3,
+            "ms_per_rollout": round(t_graph * 1e3, 3), "launches_per_step": 1,
             "episodes_finished": episodes, "mean_return_random_policy": round(ret, 3),
             "comparators": {"eager_ms": round(t_eager * 1e3, 3), "plain_kernel_graph_ms": round(t_plain * 1e3, 3),
                             "speedup_vs_eager": round(t_eager / t_graph, 2),

@@ -308,7 +308,9 @@ JWF_API jwf_status jwf_get_state(jwf_ctx* ctx, uint8_t** d_state, int32_t** d_t,
  *     water = water0; with random_fire the first can-burn cell at or after
  *     cell floor(u(w2) * H * W) (row-major, wrapping) starts burning.
  * jwf_agent_step = move/valve, one jwf_step (k = 1, any kernel; use
- * JWF_AUTO_RESET for continuing episodes), reward, restarts, observation;
+ * JWF_AUTO_RESET for continuing episodes), reward, restarts, observation
+ * (when every grid is at most 32 x 32 and the kernel is AUTO, RESIDENT or
+ * FUSED, all of it in one launch with one warp per grid; same results);
  * d_actions int32 [N], d_reward float [N] and d_done uint8 [N] (both may be
  * NULL).  Errors: JWF_EINVAL for null d_agent/d_actions, water0 < 0 or a bad
  * obs_k; otherwise as jwf_step. */

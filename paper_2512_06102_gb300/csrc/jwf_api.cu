@@ -518,6 +518,30 @@ jwf_status jwf_agent_step(jwf_ctx* ctx, const int32_t* d_actions, int32_t* d_age
     if (d_actions == nullptr) return fail(ctx, JWF_EINVAL, "jwf_agent_step: d_actions is null");
     const jwf_status st = agent_args(ctx, "jwf_agent_step: bad argument", d_agent, water0, obs_k, d_obs);
     if (st != JWF_OK) return st;
+    const jwf_kernel kn = ctx->kernel;
+    if (ctx->maxH <= 32 && ctx->maxW <= 32 && ctx->have_state &&
+        (kn == JWF_KERNEL_AUTO || kn == JWF_KERNEL_RESIDENT || kn == JWF_KERNEL_FUSED)) {
+        // grids of at most 32 x 32: the whole agent step in one warp-per-env launch
+        const bool fused = kn == JWF_KERNEL_FUSED;
+        if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_agent_step: no parameters set");
+        if (fused && !ctx->have_terrain) return fail(ctx, JWF_ESTATE, "jwf_agent_step: fused step needs terrain");
+        if (!fused && !ctx->have_table) return fail(ctx, JWF_ESTATE, "jwf_agent_step: no probability table");
+        if (ctx->wser_n > 0 && !fused)
+            return fail(ctx, JWF_EUNSUPPORTED, "jwf_agent_step: a wind series needs the fused kernel");
+        if (fused && ctx->wser_n > 0 && ctx->wser_stale) {
+            JWF_CUDA_TRY(ctx, jwf_launch_wind_series(ctx, S(stream)), "jwf_agent_step");
+            ctx->wser_stale = false;
+        }
+        if (fused && ctx->wexp_stale) {
+            JWF_CUDA_TRY(ctx, jwf_launch_wind_exponent(ctx, ctx->t_ws, ctx->t_wd, S(stream)), "jwf_agent_step");
+            ctx->wexp_stale = false;
+        }
+        JWF_CUDA_TRY(ctx, jwf_launch_agent_warp(ctx, fused, d_actions, d_agent, water0, random_fire ? 1 : 0,
+                                                burn_penalty, d_reward, d_done, obs_k, d_obs, S(stream)),
+                     "jwf_agent_step");
+        ctx->tiles_valid = false;
+        return JWF_OK;
+    }
     JWF_CUDA_TRY(ctx, jwf_launch_agent_act(ctx, d_actions, d_agent, S(stream)), "jwf_agent_step");
     const jwf_status ss = jwf_step(ctx, 1, ctx->d_agent_drops, ctx->d_agent_cnt, nullptr, ctx->d_agent_done, stream);
     if (ss != JWF_OK) return ss;

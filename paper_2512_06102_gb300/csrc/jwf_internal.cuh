@@ -185,6 +185,9 @@ cudaError_t jwf_launch_wind_series(jwf_ctx* c, cudaStream_t s);
 cudaError_t jwf_launch_agent_act(const jwf_ctx* c, const int32_t* actions, int32_t* agent, cudaStream_t s);
 cudaError_t jwf_launch_agent_post(const jwf_ctx* c, int mode, int32_t* agent, int32_t water0, int random_fire,
                                   float burn_penalty, float* reward, int32_t obs_k, uint8_t* obs, cudaStream_t s);
+cudaError_t jwf_launch_agent_warp(const jwf_ctx* c, bool fused, const int32_t* actions, int32_t* agent,
+                                  int32_t water0, int random_fire, float burn_penalty, float* reward, uint8_t* done,
+                                  int32_t obs_k, uint8_t* obs, cudaStream_t s);
 cudaError_t jwf_launch_state_planes(int64_t n, const uint8_t* states, float* pun, float* pburn, cudaStream_t s);
 cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
                                   const float* ws, const float* wd, cudaStream_t s);

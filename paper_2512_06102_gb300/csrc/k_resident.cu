@@ -23,6 +23,7 @@
 
 #include "jwf_internal.cuh"
 #include "rate_model.cuh"
+#include "step_common.cuh"
 
 namespace {
 
@@ -187,51 +188,6 @@ __device__ void res_init_flags(const uint32_t* Bp, const uint32_t* D, int WW, in
         fl_other[c] = other;
     }
     atomicAdd(burnt, nd);
-}
-
-// Table variant: does can-burn cell `cell` ignite this step?  dm: bit d set
-// when its source in direction d burns.  Draws: slot 0 words -> d 0..3, slot 1
-// words -> d 4..7; success iff u < q.  Any success ignites, so the second half
-// is skipped once the first has succeeded.
-template <class Args>
-__device__ __forceinline__ bool ignites(const Args& a, int e, int64_t off, uint32_t cell, uint32_t dm,
-                                        uint32_t tt, uint32_t ep4) {
-    const float4* q4 = reinterpret_cast<const float4*>(a.q + (off + cell) * 8);
-    bool ign = false;
-    if (dm & 0x0Fu) {
-        const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4), a.key0, a.key1);
-        const float4 qa = __ldg(q4);
-        ign |= ((dm & 1u) && jwf_u24(u.x) < qa.x) || ((dm & 2u) && jwf_u24(u.y) < qa.y) ||
-               ((dm & 4u) && jwf_u24(u.z) < qa.z) || ((dm & 8u) && jwf_u24(u.w) < qa.w);
-    }
-    if (!ign && (dm & 0xF0u)) {
-        const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 1u), a.key0, a.key1);
-        const float4 qb = __ldg(q4 + 1);
-        ign |= ((dm & 16u) && jwf_u24(u.x) < qb.x) || ((dm & 32u) && jwf_u24(u.y) < qb.y) ||
-               ((dm & 64u) && jwf_u24(u.z) < qb.z) || ((dm & 128u) && jwf_u24(u.w) < qb.w);
-    }
-    return ign;
-}
-
-// Fused variant, one (target, source) pair: does the burning source in
-// direction d ignite can-burn cell (yy, xx) of env e this step?  The rate of
-// Eqs. 1-4 is evaluated on the spot (rate_model.cuh, as the table kernel does)
-// and compared with the Philox word of that direction.
-template <class Args>
-__device__ __forceinline__ bool pair_ignites(const Args& a, const RateConsts& K, int e, int64_t off, int W, int yy,
-                                             int xx, int d, uint32_t tt, uint32_t ep4) {
-    const uint32_t cell = (uint32_t)(yy * W + xx);
-    const int64_t v = off + cell;
-    const int64_t u = off + (int64_t)(yy - jwf_dr(d)) * W + (xx - jwf_dx(d));
-    const int cv = a.cls[v], cu = a.cls[u];
-    const float zv = a.dem[v], zu = a.dem[u];
-    // a wind series is indexed by the step within the episode (held at its last entry)
-    const int ts = a.wser_n > 0 ? min((int)tt, a.wser_n - 1) : 0;
-    const float2 w2 = a.wexp[((int64_t)ts * a.N + e) * 8 + d];
-    const uint4 u4 = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + (uint32_t)(d >> 2)), a.key0, a.key1);
-    const uint32_t uw = (d & 3) == 0 ? u4.x : (d & 3) == 1 ? u4.y : (d & 3) == 2 ? u4.z : u4.w;
-    const float r = rate_of(K.G[cv][cu], zv, zu, {w2.x, w2.y}, d, K);
-    return jwf_u24(uw) < prob_of(r);
 }
 
 // Fused variant: the candidate cells of list[it0 .. it0+32) are flattened

@@ -3,9 +3,10 @@
 With the oracle's FP32 table and the same seed, every step's observation,
 reward, done flag, agent state and grid state equal the oracle's, over
 episodes that restart (auto-reset, random agent position and ignition), for
-random actions on 20 x 20 grids; the fused kernel (rates from the terrain)
-gives the same trajectory as the table kernel; a CUDA-graph rollout gives the
-same rewards as eager steps.
+random actions, on 20 x 20 grids (one warp per grid, and the three-launch
+path) and on 40 x 36 grids; the fused kernel (rates from the terrain) gives
+the same trajectory as the table kernel; a CUDA-graph rollout gives the same
+rewards as eager steps.
 """
 import numpy as np
 import pytest
@@ -36,12 +37,15 @@ def _gpu_env(scn, F0, kernel, q=None, seed=17):
     return sim, tanker.TankerEnv(sim, to(F0), water0=6, obs_k=5, burn_penalty=0.02, random_fire=True)
 
 
-def test_tanker_matches_oracle():
+@pytest.mark.parametrize("shape,kernel", [((S, S), jwf.KERNEL_RESIDENT),     # one warp per grid
+                                          ((S, S), jwf.KERNEL_PLAIN),        # act + step + post launches
+                                          ((40, 36), jwf.KERNEL_RESIDENT)])  # larger than a warp's grid
+def test_tanker_matches_oracle(shape, kernel):
     require_gpu()
-    scn = scenarios.make_scenario(S, S, N=N, seed=51)
+    scn = scenarios.make_scenario(shape[0], shape[1], N=N, seed=51)
     F0 = _fire_free(scn)
     q32 = oracle_tables(scn)[0]
-    sim, env = _gpu_env(scn, F0, jwf.KERNEL_RESIDENT, q32)
+    sim, env = _gpu_env(scn, F0, kernel, q32)
     ora = oagent.TankerOracle(scn.H, scn.W, F0, q32, scn.params.p_continue, seed=17, t_max=60, water0=6, obs_k=5,
                               burn_penalty=0.02, random_fire=True)
     np.testing.assert_array_equal(env.reset().cpu().numpy(), ora.reset())
