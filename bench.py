@@ -549,8 +549,8 @@ def bench_relaxed(args, D, dev, rank):
             "path_frac": round((fwd_b + bwd_b + acc_b) * rate / D.world / 1e9 / hbm, 4),
             "roofline": {"bound": "hbm", "achieved": round(ach_b, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(ach_b / hbm, 4), "peak_source": peak_kind,
-                         "traffic": kernel_traffic("k_relaxed_bwd_tiled", "paper_2512_06102_gb300/csrc/k_relaxed.cu"),
-                         "kernel": "k_relaxed_bwd_tiled", "kernel_us": round(k_tiled["bwd"] * 1e6, 2),
+                         "traffic": kernel_traffic("k_relaxed_bwd_sweep", "paper_2512_06102_gb300/csrc/k_relaxed.cu"),
+                         "kernel": "k_relaxed_bwd_sweep", "kernel_us": round(k_tiled["bwd"] * 1e6, 2),
                          "bytes_model": "60 B/cell-step (32 B rates, 8 B state, 8 B adjoint in, 8 B adjoint "
                                         "out, 4 B glam)"},
             "roofline_fwd": {"bound": "hbm", "achieved": round(ach_f, 1), "peak": hbm, "unit": "GB/s",

@@ -322,15 +322,18 @@ JWF_API jwf_status jwf_agent_step(jwf_ctx* ctx, const int32_t* d_actions, int32_
 
 /* ---- relaxed (raw-probabilities) update, Eqs. 5-10 ----------------------- */
 
-/* Kernels of the relaxed step.  JWF_RELAXED_TILED (default): persistent CTAs
- * walk 2-D tiles of 16 x 64 cells staged in shared memory by asynchronous
- * copies (the forward two tiles deep); the adjoint is one kernel that
- * recomputes lam on a one-cell halo and gathers dL/dp_burn from shared
- * memory.  Rates whose source lies outside the grid are multiplied by zero
- * (they must be finite; jwf_precompute_probs writes 0 there).
- * JWF_RELAXED_PLAIN: one thread per cell; the adjoint is two kernels (lam
- * adjoint, then the transpose gather) with a round trip of glam through
- * memory.  Both evaluate the same sums in the same order. */
+/* Kernels of the relaxed step.  JWF_RELAXED_TILED (default): the forward
+ * walks 16 x 64-cell tiles staged in shared memory by asynchronous copies
+ * (persistent CTAs, two tiles deep); the adjoint is one kernel in which each
+ * warp sweeps a strip of 30 columns down the rows (a halo column on each
+ * side), keeping the p_burn window, lam, glam and the per-source
+ * accumulators of dL/dp_burn in registers and streaming its rows through a
+ * shared-memory ring filled by asynchronous copies.  JWF_RELAXED_PLAIN: one
+ * thread per cell; the adjoint is two kernels (lam adjoint, then the
+ * transpose gather) with a round trip of glam through memory.  lam is summed
+ * in the same order by both; the gather's order differs (rounding only).
+ * Rates whose source lies outside the grid are multiplied by zero (they must
+ * be finite; jwf_precompute_probs writes 0 there). */
 enum jwf_relaxed_kernel { JWF_RELAXED_TILED = 0, JWF_RELAXED_PLAIN = 1 };
 JWF_API jwf_status jwf_set_relaxed_kernel(jwf_ctx* ctx, int32_t kernel);
 

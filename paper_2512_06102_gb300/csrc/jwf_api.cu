@@ -48,7 +48,7 @@ void free_all(jwf_ctx* c) {
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
                     c->d_tcnt, c->d_rtiles, c->d_adj, c->d_wser, c->d_agent_drops, c->d_agent_cnt,
-                    c->d_agent_done};
+                    c->d_agent_done, c->d_stiles};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -147,6 +147,11 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
         for (int y = 0; y < c->H[e]; y += JWF_RT_ROWS)
             for (int x = 0; x < c->W[e]; x += JWF_RT_COLS) rtiles.push_back(make_int4(e, y, x, 0));
     c->n_rtiles = (int64_t)rtiles.size();
+    std::vector<int4> stiles;
+    for (int32_t e = 0; e < N; ++e)
+        for (int y = 0; y < c->H[e]; y += JWF_SW_ROWS)
+            for (int x = 0; x < c->W[e]; x += JWF_SW_COLS) stiles.push_back(make_int4(e, y, x, 0));
+    c->n_stiles = (int64_t)stiles.size();
     // processing order: size class (by the longer side) descending, then
     // cells descending; each class is one resident launch
     auto size_class = [&](int32_t e) {
@@ -192,6 +197,7 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_gr, (size_t)c->cells * 8);
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_adj, (size_t)c->cells * 2);
     if (err == cudaSuccess) err = dev_alloc(&c->d_rtiles, rtiles.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_stiles, stiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_agent_drops, 2 * (size_t)N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_agent_cnt, (size_t)N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_agent_done, (size_t)N);
@@ -218,6 +224,8 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = cudaMemset(c->d_tburnt, 0, tiles4.size() * sizeof(int32_t));
     if (err == cudaSuccess)
         err = cudaMemcpy(c->d_rtiles, rtiles.data(), rtiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(c->d_stiles, stiles.data(), stiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_H, c->H.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_W, c->W.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_off, c->off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);

@@ -77,6 +77,10 @@ struct JwfDevParams {
 // The tiled relaxed kernels walk 2-D tiles of JWF_RT_ROWS x JWF_RT_COLS cells.
 #define JWF_RT_ROWS 16
 #define JWF_RT_COLS 64
+// The relaxed adjoint sweeps strips of JWF_SW_COLS output columns (one warp,
+// a halo column on each side) down JWF_SW_ROWS rows.
+#define JWF_SW_COLS 30
+#define JWF_SW_ROWS 16
 
 // A size class of envs run by one resident launch: envs order[start ..
 // start + count), the largest shape in it, and its block size (0: by size).
@@ -140,6 +144,8 @@ struct jwf_ctx {
     int64_t n_tiles4 = 0;
     int4* d_rtiles = nullptr;            // (env, first row, first column) per relaxed 2-D tile
     int64_t n_rtiles = 0;
+    int4* d_stiles = nullptr;            // (env, first row, first column) per adjoint sweep strip
+    int64_t n_stiles = 0;
     int relaxed_kernel = 0;              // 0: tiled (fused adjoint), 1: plain (two-pass adjoint)
     uint16_t* d_tact[2] = {nullptr, nullptr};
     int tact_cur = 0;

@@ -172,15 +172,11 @@ k_relaxed_bwd_b(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
 }
 
 // ---------------------------------------------------------------------------
-// Tiled variant: 2-D tiles of kRH x kRW cells, staged in shared memory by
-// asynchronous copies.  Each warp covers 32 consecutive cells of a row, so the
-// rate rows (32 B a cell) stream in 1 KB runs.  The adjoint recomputes lam on
-// the tile and a one-cell halo, keeps the products glam(v) r(v, d) of that
-// region in shared memory ([d][cell], so that the gather reads consecutive
-// words), and gathers dL/dp_burn from there: one kernel, no glam round trip,
-// each rate row read once (plus the halo's).  Sums run over d = 0..7 in the
-// order of the plain kernels (the gather adds rounded products where the
-// plain kernel fuses multiply and add).
+// Tiled variant: the forward walks 2-D tiles of kRH x kRW cells staged in
+// shared memory by asynchronous copies; each warp covers 32 consecutive cells
+// of a row, so the rate rows (32 B a cell) stream in 1 KB runs.  The adjoint
+// is a column sweep (below): one kernel, no glam round trip, each rate row
+// read once.
 constexpr int kRH = JWF_RT_ROWS, kRW = JWF_RT_COLS;
 
 
@@ -280,147 +276,226 @@ k_relaxed_fwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32
     }
 }
 
-// Adjoint: two persistent CTAs per SM walk the tiles; per tile a CTA stages
-// in shared memory (asynchronous copies) the rate rows, p_un and the incoming
-// adjoints of the tile and a one-cell halo, and p_burn and the mask of a
-// two-cell halo (zero outside the grid, so that a source or target outside
-// the grid contributes nothing and the sums need no bounds tests).  One CTA
-// computes while the other one's copies are in flight.
-constexpr int kBT = 512;                                   // threads of the adjoint CTA
-constexpr int kEW = kRW + 2, kEH = kRH + 2, kEN = kEH * kEW;  // tile + 1: glam and rates
-constexpr int kPW = kRW + 4, kPH = kRH + 4, kPN = kPH * kPW;  // tile + 2: pb
-struct BwdStage {
-    float r[kEN * 8];       // rate rows, [cell][d] as in memory
-    float pu[kEN], au[kEN], ab[kEN];
-    float pb[kPN], m[kPN];  // p_burn and mask; pb becomes (1 - m) p_burn
-};
-struct BwdSmem {
-    BwdStage st;
-    float P[8][kEN];        // glam(v) r(v, d), [d][cell] so that the gather reads consecutive words
-    double red[kBT / 32];
-};
-size_t bwd_smem_bytes() { return sizeof(BwdSmem); }
+// Column-sweep adjoint.  A warp owns a strip of JWF_SW_COLS output columns
+// (lane L is column x0 - 1 + L: lanes 0 and 31 are halo columns) and walks
+// down rows y0 - 1 .. y1, one target row per iteration, all in registers:
+// the masked p_burn of rows y - 1, y, y + 1 (neighbour columns by shuffles;
+// the halo lanes also keep their outer column), lam and glam of the row, the
+// eight products glam(v) r(v, d), which go to the accumulators of their
+// source cells u = v - Delta_d (rows y - 1, y, y + 1 of this lane's column,
+// or of the neighbouring lane's through shuffles).  After row y the
+// accumulator of row y - 1 is complete and dL/dp_burn of that row is
+// written.  Every load is a coalesced row segment; next row's loads are
+// issued before this row is computed.  lam sums d = 0..7 like the other
+// kernels; the gather adds the products in a fixed order of its own.
+constexpr int kSweepWarps = 4;
 
-__device__ __forceinline__ void bwd_stage(BwdStage& b, const int4* __restrict__ tiles, int64_t ti,
-                                          const int32_t* __restrict__ Hs, const int32_t* __restrict__ Ws,
-                                          const int64_t* __restrict__ offs, const float* __restrict__ r,
-                                          const float* __restrict__ pun, const float* __restrict__ pburn,
-                                          const float* __restrict__ mask, const float* __restrict__ gun_out,
-                                          const float* __restrict__ gburn_out) {
-    const int4 tl = tiles[ti];
-    const int e = tl.x, y0 = tl.y, x0 = tl.z;
-    const int H = Hs[e], W = Ws[e];
-    const int64_t off = offs[e];
-    for (int i = threadIdx.x; i < kEN; i += kBT) {
-        const int y = y0 - 1 + i / kEW, x = x0 - 1 + i % kEW;
-        if (y < 0 || y >= H || x < 0 || x >= W) continue;
-        const int64_t v = off + (int64_t)y * W + x;
-        jwf_cp_async16(&b.r[i * 8], r + v * 8);
-        jwf_cp_async16(&b.r[i * 8 + 4], r + v * 8 + 4);
-        jwf_cp_async4(&b.pu[i], pun + v);
-        jwf_cp_async4(&b.au[i], gun_out + v);
-        jwf_cp_async4(&b.ab[i], gburn_out + v);
-    }
-    for (int i = threadIdx.x; i < kPN; i += kBT) {
-        const int y = y0 - 2 + i / kPW, x = x0 - 2 + i % kPW;
-        if (y < 0 || y >= H || x < 0 || x >= W) {
-            b.pb[i] = 0.f;
-            b.m[i] = 0.f;
-            continue;
-        }
-        const int64_t v = off + (int64_t)y * W + x;
-        jwf_cp_async4(&b.pb[i], pburn + v);
-        if (mask != nullptr)
-            jwf_cp_async4(&b.m[i], mask + v);
-        else
-            b.m[i] = 0.f;
-    }
+// masked p_burn and the mask at (y, x), zero outside the grid
+__device__ __forceinline__ float2 sweep_pb(const float* __restrict__ pburn, const float* __restrict__ mask,
+                                           int64_t off, int y, int x, int H, int W) {
+    if (y < 0 || y >= H || x < 0 || x >= W) return make_float2(0.f, 0.f);
+    const int64_t i = off + (int64_t)y * W + x;
+    const float m = mask != nullptr ? mask[i] : 0.f;
+    const float p = pburn[i];
+    return make_float2(mask != nullptr ? p * (1.0f - m) : p, m);
 }
 
-__global__ void __launch_bounds__(kBT)
-k_relaxed_bwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32_t* __restrict__ Hs,
+// Each lane streams its column through a private ring of kSwDepth rows in
+// shared memory, filled by asynchronous copies kSwDepth - 1 rows ahead (no
+// lane reads another lane's slots, so only the copy groups need waiting for).
+constexpr int kSwDepth = 4;
+// one ring slot = one row of the strip, field by field across the lanes (a
+// lane's accesses fall on distinct banks)
+struct __align__(16) SwSlot {
+    float4 ra[32], rb[32];      // rate row of (y, x)
+    float pu[32], au[32], ab[32];   // p_un and the incoming adjoints at (y, x)
+    float pbn[32], mn[32];      // p_burn and mask at (y + 2, x)
+    float pbo[32], mo[32];      // ... and at (y + 2, outer column) for the halo lanes
+};
+
+__device__ __forceinline__ void sweep_issue(SwSlot& sl, int lane, const float* __restrict__ r,
+                                            const float* __restrict__ pun, const float* __restrict__ pburn,
+                                            const float* __restrict__ mask, const float* __restrict__ gun_out,
+                                            const float* __restrict__ gburn_out, int64_t off, int y, int x, int xo,
+                                            bool edge, int H, int W) {
+    if (y >= 0 && y < H && x >= 0 && x < W) {
+        const int64_t v = off + (int64_t)y * W + x;
+        jwf_cp_async16(reinterpret_cast<float*>(&sl.ra[lane]), r + v * 8);
+        jwf_cp_async16(reinterpret_cast<float*>(&sl.rb[lane]), r + v * 8 + 4);
+        jwf_cp_async4(&sl.pu[lane], pun + v);
+        jwf_cp_async4(&sl.au[lane], gun_out + v);
+        jwf_cp_async4(&sl.ab[lane], gburn_out + v);
+    } else {
+        sl.ra[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sl.rb[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sl.pu[lane] = 0.f;
+        sl.au[lane] = 0.f;
+        sl.ab[lane] = 0.f;
+    }
+    const int y2 = y + 2;
+    if (y2 >= 0 && y2 < H && x >= 0 && x < W) {
+        const int64_t v2 = off + (int64_t)y2 * W + x;
+        jwf_cp_async4(&sl.pbn[lane], pburn + v2);
+        if (mask != nullptr) jwf_cp_async4(&sl.mn[lane], mask + v2);
+        else sl.mn[lane] = 0.f;
+    } else {
+        sl.pbn[lane] = 0.f;
+        sl.mn[lane] = 0.f;
+    }
+    if (edge && y2 >= 0 && y2 < H && xo >= 0 && xo < W) {
+        const int64_t vo = off + (int64_t)y2 * W + xo;
+        jwf_cp_async4(&sl.pbo[lane], pburn + vo);
+        if (mask != nullptr) jwf_cp_async4(&sl.mo[lane], mask + vo);
+        else sl.mo[lane] = 0.f;
+    } else {
+        sl.pbo[lane] = 0.f;
+        sl.mo[lane] = 0.f;
+    }
+    jwf_cp_async_commit();
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__global__ void __launch_bounds__(kSweepWarps * 32)
+k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32_t* __restrict__ Hs,
                     const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs,
                     const float* __restrict__ r, const float* __restrict__ pun,
                     const float* __restrict__ pburn, const float* __restrict__ mask,
                     const float* __restrict__ gun_out, const float* __restrict__ gburn_out, float p_continue,
                     float* __restrict__ gun, float* __restrict__ gburn, float* __restrict__ glam,
                     double* __restrict__ partials, uint32_t* __restrict__ counter, double* __restrict__ gpc) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    BwdSmem& S = *reinterpret_cast<BwdSmem*>(smem_raw);
+    __shared__ double red[kSweepWarps];
     __shared__ bool am_last;
+    __shared__ SwSlot ring[kSweepWarps][kSwDepth];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double acc = 0.0;
-    BwdStage& b = S.st;
-    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x) {
-        bwd_stage(b, tiles, ti, Hs, Ws, offs, r, pun, pburn, mask, gun_out, gburn_out);
-        jwf_cp_async_commit();
-        const int4 tl = tiles[ti];
-        const int e = tl.x, y0 = tl.y, x0 = tl.z;
+    for (int64_t it = (int64_t)blockIdx.x * kSweepWarps + warp; it < n_items; it += (int64_t)gridDim.x * kSweepWarps) {
+        const int4 w = items[it];
+        const int e = w.x, y0 = w.y, x0 = w.z;
         const int H = Hs[e], W = Ws[e];
         const int64_t off = offs[e];
-        jwf_cp_async_wait_all();
-        __syncthreads();
-        if (mask != nullptr) {
-            for (int i = threadIdx.x; i < kPN; i += kBT) b.pb[i] = b.pb[i] * (1.0f - b.m[i]);
-            __syncthreads();
+        const int y1 = min(y0 + JWF_SW_ROWS, H);
+        const int x = x0 - 1 + lane;
+        const bool out_col = lane >= 1 && lane <= JWF_SW_COLS && x < W;
+        // outer column of the halo lanes (their neighbour outside the warp)
+        const int xo = lane == 0 ? x - 1 : x + 1;
+        const bool edge = lane == 0 || lane == 31;
+        // p_burn windows: rows y - 1, y, y + 1 of the target row y
+        float2 pa = sweep_pb(pburn, mask, off, y0 - 2, x, H, W);
+        float2 pb = sweep_pb(pburn, mask, off, y0 - 1, x, H, W);
+        float2 pc = sweep_pb(pburn, mask, off, y0, x, H, W);
+        float oa = 0.f, ob = 0.f, oc = 0.f;
+        if (edge) {
+            oa = sweep_pb(pburn, mask, off, y0 - 2, xo, H, W).x;
+            ob = sweep_pb(pburn, mask, off, y0 - 1, xo, H, W).x;
+            oc = sweep_pb(pburn, mask, off, y0, xo, H, W).x;
         }
-        // glam (and, inside the tile, dL/dp_un) on the tile and its halo
-        for (int i = threadIdx.x; i < kEN; i += kBT) {
-            const int ly = i / kEW, lx = i - (i / kEW) * kEW;
-            const int y = y0 - 1 + ly, x = x0 - 1 + lx;
-            float rv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float g = 0.f;
-            if (y >= 0 && y < H && x >= 0 && x < W) {
-                const float4 ra = *reinterpret_cast<const float4*>(&b.r[i * 8]);
-                const float4 rb = *reinterpret_cast<const float4*>(&b.r[i * 8 + 4]);
-                rv[0] = ra.x; rv[1] = ra.y; rv[2] = ra.z; rv[3] = ra.w;
-                rv[4] = rb.x; rv[5] = rb.y; rv[6] = rb.z; rv[7] = rb.w;
-                const float pu = b.pu[i], au = b.au[i], ab = b.ab[i];
-                float lam = 0.f;
+        const int yb = y0 - 1;                            // first target row
+        for (int k = 0; k < kSwDepth - 1; ++k)
+            sweep_issue(ring[warp][k], lane, r, pun, pburn, mask, gun_out, gburn_out, off, yb + k, x, xo, edge, H, W);
+        float g_prev = 0.f, g_cur = 0.f, g_next = 0.f;   // accumulators of rows y - 1, y, y + 1
+        float ab_prev = 0.f, m_prev = 0.f;                // a_b and mask of row y - 1
+        for (int y = yb; y <= y1; ++y) {
+            const int k = y - yb;
+            sweep_issue(ring[warp][(k + kSwDepth - 1) % kSwDepth], lane, r, pun, pburn, mask, gun_out, gburn_out, off,
+                        y + kSwDepth - 1, x, xo, edge, H, W);
+            cp_async_wait_n<kSwDepth - 1>();
+            const SwSlot& sl = ring[warp][k % kSwDepth];
+            struct {
+                float4 ra, rb;
+                float pu, au, ab;
+            } cur = {sl.ra[lane], sl.rb[lane], sl.pu[lane], sl.au[lane], sl.ab[lane]};
+            const float pbn = sl.pbn[lane], mn = sl.mn[lane];
+            const float2 pn = make_float2(mask != nullptr ? pbn * (1.0f - mn) : pbn, mn);
+            const float on = mask != nullptr ? sl.pbo[lane] * (1.0f - sl.mo[lane]) : sl.pbo[lane];
+            // neighbour columns of the window
+            float la = __shfl_up_sync(FULL, pa.x, 1), lb = __shfl_up_sync(FULL, pb.x, 1),
+                  lc = __shfl_up_sync(FULL, pc.x, 1);
+            float ra_ = __shfl_down_sync(FULL, pa.x, 1), rb_ = __shfl_down_sync(FULL, pb.x, 1),
+                  rc_ = __shfl_down_sync(FULL, pc.x, 1);
+            if (lane == 0) {
+                la = oa;
+                lb = ob;
+                lc = oc;
+            }
+            if (lane == 31) {
+                ra_ = oa;
+                rb_ = ob;
+                rc_ = oc;
+            }
+            const float rv[8] = {cur.ra.x, cur.ra.y, cur.ra.z, cur.ra.w, cur.rb.x, cur.rb.y, cur.rb.z, cur.rb.w};
+            // sources of directions 0..7: (y, x-1), (y+1, x-1), (y+1, x), (y+1, x+1), (y, x+1), (y-1, x+1),
+            // (y-1, x), (y-1, x-1)
+            const float src[8] = {lb, lc, pc.x, rc_, rb_, ra_, pa.x, la};
+            float lam = 0.f;
 #pragma unroll
-                for (int d = 0; d < 8; ++d) lam += b.pb[(ly + 1 - jwf_dr(d)) * kPW + (lx + 1 - jwf_dx(d))] * rv[d];
+            for (int d = 0; d < 8; ++d) lam += src[d] * rv[d];
+            const bool valid = y >= 0 && y < H && x >= 0 && x < W;
+            float g = 0.f;
+            if (valid) {
                 const float em = expf(-lam);
                 const float p_ign = -expm1f(-lam);
-                const float nb = ab - au;
-                const float pe = pu * em;
+                const float nb = cur.ab - cur.au;
+                const float pe = cur.pu * em;
                 g = pe != 0.f ? sat(nb * pe) : 0.f;
-                if (ly >= 1 && ly <= kRH && lx >= 1 && lx <= kRW) {
+                if (out_col && y >= y0 && y < y1) {
                     const int64_t v = off + (int64_t)y * W + x;
-                    gun[v] = sat(p_ign != 0.f ? au + nb * p_ign : au);
+                    gun[v] = sat(p_ign != 0.f ? cur.au + nb * p_ign : cur.au);
                     glam[v] = g;
-                    const float pbv = b.pb[(ly + 1) * kPW + lx + 1];
-                    if (pbv != 0.f) acc += (double)(ab * pbv);
+                    if (pb.x != 0.f) acc += (double)(cur.ab * pb.x);
                 }
             }
+            float P[8];
 #pragma unroll
-            for (int d = 0; d < 8; ++d) S.P[d][i] = g * rv[d];
-        }
-        __syncthreads();
-        // dL/dp_burn(u) = (1 - m(u)) (p_continue a_b(u) + sum_d glam(u + Delta_d) r[u + Delta_d][d])
-        for (int j = threadIdx.x; j < kRH * kRW; j += kBT) {
-            const int ty = j / kRW, tx = j - (j / kRW) * kRW;
-            const int y = y0 + ty, x = x0 + tx;
-            if (y >= H || x >= W) continue;
-            const int ei = (ty + 1) * kEW + tx + 1;
-            const float abu = b.ab[ei];
-            float g = p_continue != 0.f ? p_continue * abu : 0.f;
-#pragma unroll
-            for (int d = 0; d < 8; ++d) g += S.P[d][(ty + 1 + jwf_dr(d)) * kEW + (tx + 1 + jwf_dx(d))];
-            if (mask != nullptr) {
-                const float keep = 1.0f - b.m[(ty + 2) * kPW + tx + 2];
-                g = keep != 0.f ? g * keep : 0.f;
+            for (int d = 0; d < 8; ++d) P[d] = g * rv[d];
+            // products to the source cells: own column (d = 2 -> row y+1, d = 6 -> row y-1); the column
+            // to the left gets d = 0, 1, 7 (rows y, y+1, y-1) from its right neighbour, the column to the
+            // right gets d = 3, 4, 5 (rows y+1, y, y-1) from its left neighbour
+            const float fr0 = __shfl_down_sync(FULL, P[0], 1), fr1 = __shfl_down_sync(FULL, P[1], 1),
+                        fr7 = __shfl_down_sync(FULL, P[7], 1);
+            const float fl3 = __shfl_up_sync(FULL, P[3], 1), fl4 = __shfl_up_sync(FULL, P[4], 1),
+                        fl5 = __shfl_up_sync(FULL, P[5], 1);
+            g_prev += P[6];
+            g_prev += fr7;
+            g_prev += fl5;
+            g_cur += fr0;
+            g_cur += fl4;
+            g_next += P[2];
+            g_next += fr1;
+            g_next += fl3;
+            // row y - 1 is complete
+            if (out_col && y - 1 >= y0 && y - 1 < y1) {
+                float gb = p_continue != 0.f ? p_continue * ab_prev + g_prev : g_prev;
+                if (mask != nullptr) {
+                    const float keep = 1.0f - m_prev;
+                    gb = keep != 0.f ? gb * keep : 0.f;
+                }
+                gburn[off + (int64_t)(y - 1) * W + x] = sat(gb);
             }
-            gburn[off + (int64_t)y * W + x] = sat(g);
+            g_prev = g_cur;
+            g_cur = g_next;
+            g_next = 0.f;
+            ab_prev = cur.ab;
+            m_prev = pb.y;
+            pa = pb;
+            pb = pc;
+            pc = pn;
+            oa = ob;
+            ob = oc;
+            oc = on;
         }
-        __syncthreads();
+        jwf_cp_async_wait_all();      // the rows fetched past the strip's end land before the ring is reused
     }
     if (gpc == nullptr) return;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (lane == 0) red[warp] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int w = 0; w < kBT / 32; ++w) s += S.red[w];
+        for (int i = 0; i < kSweepWarps; ++i) s += red[i];
         partials[blockIdx.x] = s;
         __threadfence();
         am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
@@ -431,17 +506,16 @@ k_relaxed_bwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32
     double s = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&partials[b]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = s;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) red[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        for (int w = 0; w < kBT / 32; ++w) tot += S.red[w];
+        for (int i = 0; i < kSweepWarps; ++i) tot += red[i];
         *gpc += tot;
         *counter = 0u;
     }
 }
-
 }  // namespace
 
 cudaError_t jwf_launch_relaxed_fwd(const jwf_ctx* c, const float* pun, const float* pburn,
@@ -487,24 +561,25 @@ cudaError_t jwf_launch_relaxed_bwd(jwf_ctx* c, const float* pun, const float* pb
                                                                    mask, gburn_out, glam, c->P.p_continue,
                                                                    gburn);
     } else {
-        // two persistent CTAs per SM
-        static int smem_set[64] = {};
-        const size_t smem = bwd_smem_bytes();
+        // column sweeps, grid-stride over the strips with as many CTAs as fit
+        // the GPU at once (a fixed grid also keeps the per-CTA partial sums of
+        // dL/dp_continue deterministic)
+        static int per_sm[64] = {};
         if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
-        if (!smem_set[c->device]) {
+        if (per_sm[c->device] == 0) {
+            int b = 0;
             const cudaError_t err =
-                cudaFuncSetAttribute(k_relaxed_bwd_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_bwd_sweep, kSweepWarps * 32, 0);
             if (err != cudaSuccess) return err;
-            smem_set[c->device] = 1;
+            per_sm[c->device] = b > 0 ? b : 1;
         }
-        int64_t grid = (int64_t)c->num_sms * 2;
-        if (grid > c->n_rtiles) grid = c->n_rtiles;
+        int64_t grid = (c->n_stiles + kSweepWarps - 1) / kSweepWarps;
+        if (grid > (int64_t)c->num_sms * per_sm[c->device]) grid = (int64_t)c->num_sms * per_sm[c->device];
         if (grid > c->partial_cap) grid = c->partial_cap;
         if (grid < 1) grid = 1;
-        k_relaxed_bwd_tiled<<<(unsigned)grid, kBT, smem, s>>>(c->d_rtiles, c->n_rtiles, c->d_H, c->d_W, c->d_off,
-                                                            c->d_r, pun, pburn, mask, gun_out, gburn_out,
-                                                            c->P.p_continue, gun, gburn, glam, c->d_partials,
-                                                            c->d_red_counter, gpc);
+        k_relaxed_bwd_sweep<<<(unsigned)grid, kSweepWarps * 32, 0, s>>>(
+            c->d_stiles, c->n_stiles, c->d_H, c->d_W, c->d_off, c->d_r, pun, pburn, mask, gun_out, gburn_out,
+            c->P.p_continue, gun, gburn, glam, c->d_partials, c->d_red_counter, gpc);
     }
     return cudaGetLastError();
 }
