@@ -12,8 +12,9 @@
 //   dL/dp_burn(u) = (1 - m(u)) (p_continue a_b(u) + sum_d glam(u + Delta_d) r[u + Delta_d][d])
 //   dL/dp_continue = sum_v a_b(v) pb(v)
 // HBM-bound stencils: the forward moves 8 B of state in, 32 B of rates and
-// 8 B of state out per cell; the adjoint is split in two passes (glam, then
-// the transpose gather) so that no cell recomputes a neighbour's lam.
+// 8 B of state out per cell.  The plain kernels split the adjoint in two
+// passes (glam, then the transpose gather) so that no cell recomputes a
+// neighbour's lam; the tiled set does it in one column sweep.
 //
 // The adjoint of a cell that the fire has not reached grows by about
 // sum_d r per step (a spark there would spread), so it can leave the float
