@@ -3,14 +3,16 @@
 
 One step = one full episode of the batched workload: 4096 grids of 128 x 128
 cells (30 m; 11-class fBm landcover, fBm DEM 0-2000 m, per-grid wind, 1-3
-fires), reset to the initial fires, the probability table built (Eqs. 1-4),
-then 200 discrete steps (Section 3 stochastic update) with one random 3 x 3
-tanker drop per grid per step and per-step burning/burned counts and done
-flags.  Metric: cell-updates/s (grids x cells x steps / time).
+fires), reset to the initial fires, the per-grid wind part of Eqs. 1-4, then
+200 discrete steps (Section 3 stochastic update, the rates of Eqs. 1-4
+evaluated inside the step) with one random 3 x 3 tanker drop per grid per
+step and per-step burning/burned counts and done flags.  Metric:
+cell-updates/s (grids x cells x steps / time).
 
 The same JSON line also reports the relaxed path (Eqs. 5-10): a forward and
-backward pass (sqrt(T) checkpoints) of 256 grids of 128 x 128 over T = 100
-steps, as fwd+bwd cell-steps/s.
+backward pass of 256 grids of 128 x 128 over T = 100 steps (every state kept;
+also with sqrt(T) checkpoints), as fwd+bwd cell-steps/s, and the other
+workloads (ragged rollout, large maps, the air-tanker scenario).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -256,13 +258,17 @@ def run_ours(args):
     value = world * units / t_max
 
     # end to end through the public API with host buffers: inputs copied in
-    # from pinned memory and the per-step counts read back, every step
+    # from pinned memory and the per-step counts read back, every step.  The
+    # initial fires travel 2-bit packed (jwf_load_state_packed), a quarter of
+    # the byte-per-cell array.
+    P0_d = jwf.pack_states(F0_d)
     host = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
             for k, a in (("cls", scn.cls), ("dem", scn.dem), ("ws", scn.wind_speed), ("wd", scn.wind_dir),
-                         ("F0", scn.F0), ("drops", drops))}
+                         ("drops", drops))}
+    host["P0"] = P0_d.cpu().pin_memory()
     out_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
              for k, v in (("burning", burning), ("burnt", burnt), ("done", done))}
-    dev_in = {"cls": cls_d, "dem": dem_d, "ws": ws_d, "wd": wd_d, "F0": F0_d, "drops": drops_d}
+    dev_in = {"cls": cls_d, "dem": dem_d, "ws": ws_d, "wd": wd_d, "P0": P0_d, "drops": drops_d}
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = sum(v.numel() * v.element_size() for v in out_h.values())
 
@@ -294,7 +300,7 @@ def run_ours(args):
                     ev_in[nb].record(s_copy)
             s_main.wait_event(ev_in[b])
             d = sets[b]
-            sim.load_state(d["F0"])
+            sim.load_state_packed(d["P0"])
             sim.set_terrain(d["cls"], d["dem"], d["ws"], d["wd"])
             ob = outs[b]
             sim.step(EPISODE, d["drops"], ob[0], ob[1], ob[2])
@@ -421,6 +427,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scn, drops)
+        cpu["parallel"] = cpu_parallel(scn, drops)
+        cpu["relaxed"] = cpu_relaxed()
+        cpu["large"] = cpu_large()
 
     line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
@@ -429,7 +438,7 @@ def run_ours(args):
             "config": {"workload": f"batched: {N_ENVS} grids x {SIDE}x{SIDE}, {EPISODE}-step episode, 3x3 drop/step",
                        "global_batch": N_ENVS * world, "grid": [SIDE, SIDE], "steps_per_episode": EPISODE,
                        "parallelism": f"replicas x{world} (independent grid shards)",
-                       "l2": "inputs larger than L2 (2.15 GB probability table rebuilt and read every step)"},
+                       "l2": "inputs larger than L2 (landcover + DEM 335 MB and the 67 MB states read every episode)"},
             "env_steps_per_s": world * N_ENVS * EPISODE * args.steps / t_max,
             "roofline": roof,
             "comparators": comparators,
@@ -801,6 +810,104 @@ def cpu_baseline(scn, drops, n_envs=CPU_SAMPLE_ENVS, reps=1):
             "kind": "oracle",
             "sample": f"{n_envs} of the {N_ENVS} grids x {EPISODE} steps ({reps} rep), FP64 table + C step, "
                       f"{dt:.1f} s"}
+
+
+def _oracle_shard(payload):
+    """One worker of the env-parallel oracle timing (a spawned process): the
+    FP64 table and C rollout of its own grids; returns its wall time."""
+    import torch
+    torch.set_num_threads(1)
+    from oracle import discrete, prob
+    cls, dem, ws, wd, F0, drops, params, p_continue, env_ids = payload
+    t0 = time.perf_counter()
+    q = [prob.table_f32(cls[i][None], dem[i][None], ws[i:i + 1], wd[i:i + 1], params, 30.0)[0].reshape(-1, 8)
+         for i in range(len(env_ids))]
+    n = len(env_ids)
+    ro = discrete.Rollout(np.full(n, SIDE), np.full(n, SIDE), F0.reshape(-1), np.concatenate(q), p_continue,
+                          seed=1000, env_ids=np.asarray(env_ids, np.int32))
+    ro.step(EPISODE, np.ascontiguousarray(drops))
+    return time.perf_counter() - t0
+
+
+def cpu_parallel(scn, drops, per_core=CPU_SAMPLE_ENVS // 4):
+    """The oracle env-parallel: one spawned process per host core, each on its
+    own grids of the batch; rate = all grids' cell-updates / the slowest
+    worker's time (process start-up excluded)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    n = min(cores * per_core, N_ENVS)
+    p = scn.params.as_dict()
+    jobs = []
+    for w in range(cores):
+        env_ids = list(range(w * per_core, min((w + 1) * per_core, n)))
+        if not env_ids:
+            break
+        e0, e1 = env_ids[0], env_ids[-1] + 1
+        jobs.append((np.stack([scn.env(e, scn.cls) for e in env_ids]), np.stack([scn.env(e, scn.dem) for e in env_ids]),
+                     scn.wind_speed[e0:e1], scn.wind_dir[e0:e1], np.stack([scn.env(e, scn.F0) for e in env_ids]),
+                     drops[:, e0:e1], p, scn.params.p_continue, env_ids))
+    from concurrent.futures import ProcessPoolExecutor
+    try:
+        with ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+            times = list(ex.map(_oracle_shard, jobs))
+    except Exception as exc:        # a worker that could not start: report, do not fail the bench
+        return {"unavailable": f"env-parallel oracle failed: {type(exc).__name__}: {exc}"[:200]}
+    dt = max(times)
+    return {"value": n * SIDE * SIDE * EPISODE / dt, "unit": "cell-updates/s", "cores": len(jobs),
+            "kind": "oracle",
+            "sample": f"{n} of the {N_ENVS} grids x {EPISODE} steps, {per_core} grids per process, "
+                      f"slowest process {dt:.1f} s"}
+
+
+def cpu_relaxed(n=8):
+    """The FP64 relaxed oracle (PyTorch CPU, one thread): rates of Eqs. 1-4
+    from the parameters under autograd, T = 100 relaxed steps (Eqs. 5-10),
+    backward to every parameter; fwd+bwd cell-steps/s."""
+    import torch
+
+    from oracle import prob
+    from oracle import relaxed as orx
+    from paper_2512_06102_gb300 import scenarios
+    torch.set_num_threads(1)
+    scn = scenarios.make_scenario(SIDE, SIDE, N=n, seed=2)
+    f64 = torch.float64
+    p = scn.params
+    th = [torch.tensor(float(x), dtype=f64, requires_grad=True)
+          for x in (p.p_base, p.alpha_w1, p.alpha_w2, p.alpha_s, p.alpha_gamma, p.p_continue)]
+    mv = torch.tensor(np.asarray(p.mu_veg, np.float64), requires_grad=True)
+    md = torch.tensor(np.asarray(p.mu_den, np.float64), requires_grad=True)
+    cls = torch.as_tensor(scn.cls).long().reshape(n, SIDE, SIDE)
+    dem = torch.as_tensor(scn.dem).double().reshape(n, SIDE, SIDE)
+    F0 = torch.as_tensor(scn.F0).reshape(n, SIDE, SIDE)
+    t0 = time.perf_counter()
+    r = prob.rates(cls, dem, torch.as_tensor(scn.wind_speed).double(), torch.as_tensor(scn.wind_dir).double(),
+                   th[0], th[1], th[2], th[3], th[4], mv, md, p.cell_size)
+    ou, ob = orx.relaxed_rollout((F0 <= 1).double(), (F0 == 2).double(), r, th[5], REL_T)
+    (0.5 * ou.sum() + ob.sum()).backward()
+    dt = time.perf_counter() - t0
+    return {"value": n * SIDE * SIDE * REL_T / dt, "unit": "fwd+bwd cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} grids of {SIDE}x{SIDE}, T = {REL_T}, FP64 autograd, {dt:.1f} s"}
+
+
+def cpu_large(side=1024, steps=50):
+    """The oracle on one large grid (the dense C sweep costs the same per cell
+    at any size, so a {side}^2 grid of the same generator stands for the
+    4096^2 ones): FP64 table + 50 steps with drops."""
+    import torch
+
+    from oracle import discrete, prob
+    from paper_2512_06102_gb300 import scenarios
+    torch.set_num_threads(1)
+    scn = scenarios.make_scenario(side, side, N=1, seed=0)
+    dr = scenarios.drops(steps, scn.H, scn.W, seed=0)
+    t0 = time.perf_counter()
+    q32 = prob.table_f32(scn.env(0, scn.cls)[None], scn.env(0, scn.dem)[None], scn.wind_speed[:1],
+                         scn.wind_dir[:1], scn.params.as_dict(), scn.params.cell_size)[0]
+    ro = discrete.Rollout(scn.H, scn.W, scn.F0, q32.reshape(-1, 8), scn.params.p_continue, seed=1000)
+    ro.step(steps, np.ascontiguousarray(dr))
+    dt = time.perf_counter() - t0
+    return {"value": side * side * steps / dt, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 grid of {side}x{side} x {steps} steps with drops (FP64 table + C step), {dt:.1f} s"}
 
 
 def run_reference(args):

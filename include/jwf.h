@@ -179,6 +179,30 @@ JWF_API jwf_status jwf_get_probs(jwf_ctx* ctx, float** d_q, float** d_r);
  * every env; t = 0 and episode = 0 for all envs. */
 JWF_API jwf_status jwf_load_state(jwf_ctx* ctx, const uint8_t* d_F0, void* stream);
 
+/* 2-bit packed states.  A state 0..3 takes two bits: cell i of an array
+ * (for the context, the cells of all envs in order, row-major within an
+ * env) sits in bits 2(i mod 4) and 2(i mod 4) + 1 of byte i / 4, so a packed
+ * array of n states takes ceil(n / 4) bytes, a quarter of the byte-per-cell
+ * layout (the host-to-device copy of a batch's initial fires, a recorded
+ * trajectory).  jwf_packed_size(n) is ceil(n / 4) rounded up to a multiple of
+ * 16: the row stride of a packed history and the size to allocate. */
+JWF_API int64_t jwf_packed_size(int64_t n_cells);
+
+/* Pack n uint8 states (device, only their low two bits are kept) into
+ * d_packed (device, ceil(n / 4) bytes written), or unpack them back.
+ * Buffers are caller-owned and must not overlap.  Asynchronous on stream.
+ * Errors: JWF_EINVAL (n < 0, null pointer with n > 0), JWF_ECUDA. */
+JWF_API jwf_status jwf_pack_states(int64_t n_cells, const uint8_t* d_states, uint8_t* d_packed, void* stream);
+JWF_API jwf_status jwf_unpack_states(int64_t n_cells, const uint8_t* d_packed, uint8_t* d_states, void* stream);
+
+/* jwf_load_state from 2-bit packed initial states (device, ceil(cells / 4)
+ * bytes).  The context keeps one byte a cell internally. */
+JWF_API jwf_status jwf_load_state_packed(jwf_ctx* ctx, const uint8_t* d_P0, void* stream);
+
+/* The current state of every env, 2-bit packed into d_packed (device,
+ * caller-owned, ceil(cells / 4) bytes).  Errors: JWF_ESTATE (no state). */
+JWF_API jwf_status jwf_get_state_packed(jwf_ctx* ctx, uint8_t* d_packed, void* stream);
+
 /* Restart the envs selected by d_env_mask (uint8 [N], nonzero = restart; NULL
  * = all): state := initial state, t := 0, episode += 1 (a fresh random
  * stream).  Section 4: episodes restart from randomised initial fires. */
@@ -218,6 +242,15 @@ JWF_API jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int
  * recording.  Errors as jwf_step; JWF_EINVAL when d_history is NULL. */
 JWF_API jwf_status jwf_step_record(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
                                    int32_t* d_burnt, uint8_t* d_done, uint8_t* d_history, void* stream);
+
+/* jwf_step_record with 2-bit packed rows: d_history is [k] rows of
+ * jwf_packed_size(cells) bytes (device, caller-owned), row s = the packed
+ * state after step s; a quarter of the memory of the byte-per-cell history
+ * (e.g. 200 steps of 4096 grids of 128 x 128: 3.4 GB instead of 13.4 GB).
+ * The resident kernels write the rows from their bit planes; the others pack
+ * the state after each step.  Errors as jwf_step_record. */
+JWF_API jwf_status jwf_step_record_packed(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
+                                          int32_t* d_burnt, uint8_t* d_done, uint8_t* d_history, void* stream);
 
 /* Replace the Philox key (the seed of jwf_create) for the following steps,
  * e.g. to draw a new sample of the same episode. */
@@ -272,6 +305,14 @@ JWF_API jwf_status jwf_set_class_threads(jwf_ctx* ctx, int32_t size_class, int32
 /* Steps per launch of the tiled kernel (1..16, default 16; the halo, and so
  * the redundant work per tile, grows with it). */
 JWF_API jwf_status jwf_set_round_steps(jwf_ctx* ctx, int32_t steps);
+
+/* Scheduling hint for the resident kernels: within each size class, envs are
+ * taken from the work queue in descending h_priority (host float [N], read
+ * during the call; e.g. the expected number of steps an env's fire lasts) so
+ * that long envs start first and do not finish last.  NULL restores the
+ * default order (cells descending).  Results do not depend on the order.
+ * Synchronous (waits for work already queued on the device). */
+JWF_API jwf_status jwf_set_env_priority(jwf_ctx* ctx, const float* h_priority);
 
 /* Instrumentation: while d_counts (four uint64 on the device, owned by the
  * caller) is set, the resident step kernels add to them the work they did:

@@ -173,3 +173,22 @@ class Rollout:
     def env_state(self, e: int) -> np.ndarray:
         n = int(self.H[e]) * int(self.W[e])
         return self.F[self.off[e]:self.off[e] + n].reshape(int(self.H[e]), int(self.W[e]))
+
+
+def pack_states(F: np.ndarray) -> np.ndarray:
+    """2-bit packed storage of states 0..3: cell i of the flattened array goes
+    to bits 2(i mod 4) and 2(i mod 4) + 1 of byte i // 4 (ceil(n / 4) bytes).
+    A storage format of this library, not part of the method."""
+    f = np.asarray(F, np.uint8).reshape(-1)
+    out = np.zeros((f.size + 3) // 4, np.uint8)
+    for j in range(4):
+        part = f[j::4].astype(np.uint16) & 3
+        out[:part.size] |= (part << (2 * j)).astype(np.uint8)
+    return out
+
+
+def unpack_states(P: np.ndarray, n: int) -> np.ndarray:
+    """Inverse of pack_states: the first n states of a packed byte array."""
+    p = np.asarray(P, np.uint8).reshape(-1)
+    i = np.arange(n)
+    return ((p[i // 4] >> (2 * (i % 4))) & 3).astype(np.uint8)

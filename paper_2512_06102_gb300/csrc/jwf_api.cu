@@ -130,6 +130,9 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
         for (int64_t s = 0; s < n; s += JWF_TILE) tiles.push_back(make_int2(e, (int)s));
     }
     c->cells = c->off[N];
+    c->packed_aligned = true;
+    for (int32_t e = 0; e < N; ++e)
+        if ((c->off[e] & 31) != 0 || (c->W[e] & 31) != 0) c->packed_aligned = false;
     c->n_tiles = (int64_t)tiles.size();
     // tiles of the tiled path: (env, tile row, tile column) and per-env layout
     std::vector<int4> tiles4, env_tiles(N);
@@ -424,6 +427,36 @@ jwf_status jwf_load_state(jwf_ctx* ctx, const uint8_t* d_F0, void* stream) {
     return JWF_OK;
 }
 
+jwf_status jwf_load_state_packed(jwf_ctx* ctx, const uint8_t* d_P0, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_P0 == nullptr) return fail(ctx, JWF_EINVAL, "jwf_load_state_packed: null pointer");
+    ctx->tiles_valid = false;
+    JWF_CUDA_TRY(ctx, jwf_launch_load_packed(ctx, d_P0, S(stream)), "jwf_load_state_packed");
+    ctx->have_state = true;
+    return JWF_OK;
+}
+
+jwf_status jwf_get_state_packed(jwf_ctx* ctx, uint8_t* d_packed, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_packed == nullptr) return fail(ctx, JWF_EINVAL, "jwf_get_state_packed: null pointer");
+    if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_get_state_packed: no state loaded");
+    JWF_CUDA_TRY(ctx, jwf_launch_pack(ctx->cells, ctx->d_state[ctx->cur], d_packed, S(stream)),
+                 "jwf_get_state_packed");
+    return JWF_OK;
+}
+
+int64_t jwf_packed_size(int64_t n_cells) { return n_cells < 0 ? -1 : jwf_packed_bytes(n_cells); }
+
+jwf_status jwf_pack_states(int64_t n_cells, const uint8_t* d_states, uint8_t* d_packed, void* stream) {
+    if (n_cells < 0 || (n_cells > 0 && (d_states == nullptr || d_packed == nullptr))) return JWF_EINVAL;
+    return jwf_launch_pack(n_cells, d_states, d_packed, S(stream)) == cudaSuccess ? JWF_OK : JWF_ECUDA;
+}
+
+jwf_status jwf_unpack_states(int64_t n_cells, const uint8_t* d_packed, uint8_t* d_states, void* stream) {
+    if (n_cells < 0 || (n_cells > 0 && (d_states == nullptr || d_packed == nullptr))) return JWF_EINVAL;
+    return jwf_launch_unpack(n_cells, d_packed, d_states, S(stream)) == cudaSuccess ? JWF_OK : JWF_ECUDA;
+}
+
 jwf_status jwf_reset(jwf_ctx* ctx, const uint8_t* d_env_mask, void* stream) {
     if (ctx == nullptr) return JWF_EINVAL;
     if (!ctx->have_state) return fail(ctx, JWF_ESTATE, "jwf_reset: no state loaded");
@@ -446,8 +479,21 @@ jwf_status jwf_step_record(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int3
     if (ctx == nullptr) return JWF_EINVAL;
     if (d_history == nullptr) return fail(ctx, JWF_EINVAL, "jwf_step_record: d_history is null");
     ctx->hist = d_history;
+    ctx->hist_packed = false;
     const jwf_status st = jwf_step(ctx, k, d_drops, d_burning, d_burnt, d_done, stream);
     ctx->hist = nullptr;
+    return st;
+}
+
+jwf_status jwf_step_record_packed(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
+                                  int32_t* d_burnt, uint8_t* d_done, uint8_t* d_history, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_history == nullptr) return fail(ctx, JWF_EINVAL, "jwf_step_record_packed: d_history is null");
+    ctx->hist = d_history;
+    ctx->hist_packed = true;
+    const jwf_status st = jwf_step(ctx, k, d_drops, d_burning, d_burnt, d_done, stream);
+    ctx->hist = nullptr;
+    ctx->hist_packed = false;
     return st;
 }
 
@@ -604,6 +650,28 @@ jwf_status jwf_set_class_threads(jwf_ctx* ctx, int32_t size_class, int32_t threa
         return fail(ctx, JWF_EINVAL, "jwf_set_class_threads: threads must be 0, 32, 64, 128 or 256");
     for (JwfGroup& G : ctx->groups)
         if (G.size_class == size_class) G.threads = threads;
+    return JWF_OK;
+}
+
+jwf_status jwf_set_env_priority(jwf_ctx* ctx, const float* h_priority) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    std::vector<int32_t> order(ctx->N);
+    JWF_CUDA_TRY(ctx, cudaMemcpy(order.data(), ctx->d_order, ctx->N * sizeof(int32_t), cudaMemcpyDeviceToHost),
+                 "jwf_set_env_priority");
+    for (const JwfGroup& G : ctx->groups) {
+        auto b = order.begin() + G.start, e = b + G.count;
+        if (h_priority == nullptr) {
+            // back to the creation order: cells descending, then env index
+            std::stable_sort(b, e, [&](int32_t x, int32_t y) { return x < y; });
+            std::stable_sort(b, e, [&](int32_t x, int32_t y) {
+                return (int64_t)ctx->H[x] * ctx->W[x] > (int64_t)ctx->H[y] * ctx->W[y];
+            });
+        } else {
+            std::stable_sort(b, e, [&](int32_t x, int32_t y) { return h_priority[x] > h_priority[y]; });
+        }
+    }
+    JWF_CUDA_TRY(ctx, cudaMemcpy(ctx->d_order, order.data(), ctx->N * sizeof(int32_t), cudaMemcpyHostToDevice),
+                 "jwf_set_env_priority");
     return JWF_OK;
 }
 

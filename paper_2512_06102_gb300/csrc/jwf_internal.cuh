@@ -169,6 +169,8 @@ struct jwf_ctx {
     const float* s_wd = nullptr;
     bool wser_stale = false;
     uint8_t* hist = nullptr;             // during a recording jwf_step: [k][cells] states after each step
+    bool hist_packed = false;            // hist rows are 2-bit packed, jwf_packed_bytes(cells) apart
+    bool packed_aligned = false;         // every env starts on a 32-cell boundary and has W % 32 == 0
     int32_t* d_agent_drops = nullptr;    // [N][2] drop centres of an agent step
     int32_t* d_agent_cnt = nullptr;      // [N] burning cells after an agent step
     uint8_t* d_agent_done = nullptr;     // [N] done flags of an agent step
@@ -207,6 +209,15 @@ cudaError_t jwf_launch_rates_bwd(jwf_ctx* c, int32_t n_steps, const float* glam,
                                  double* gparams, cudaStream_t s);
 
 cudaError_t jwf_launch_load(jwf_ctx* c, const uint8_t* F0, cudaStream_t s);
+// 2-bit packed states: cell i sits in bits 2(i mod 4), 2(i mod 4) + 1 of byte
+// i / 4.  A packed row of `cells` states takes jwf_packed_bytes(cells) bytes
+// (rounded up to 16 so that consecutive rows stay 16-byte aligned).
+inline int64_t jwf_packed_bytes(int64_t cells) { return ((cells + 3) / 4 + 15) / 16 * 16; }
+cudaError_t jwf_launch_pack(int64_t n, const uint8_t* states, uint8_t* packed, cudaStream_t s);
+cudaError_t jwf_launch_unpack(int64_t n, const uint8_t* packed, uint8_t* states, cudaStream_t s);
+cudaError_t jwf_launch_load_packed(jwf_ctx* c, const uint8_t* P0, cudaStream_t s);
+// record the current state as history row `row` (u8 copy or packed)
+cudaError_t jwf_record_row(jwf_ctx* c, int64_t row, cudaStream_t s);
 cudaError_t jwf_launch_reset(jwf_ctx* c, const uint8_t* env_mask, cudaStream_t s);
 cudaError_t jwf_launch_action(jwf_ctx* c, const uint8_t* mask, cudaStream_t s);
 cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,

@@ -53,8 +53,11 @@ struct ResArgs {
     int32_t* out_burnt;
     uint8_t* out_done;
     uint32_t* queue;            // [0] cursor, [1] CTAs finished
-    uint8_t* history;           // [k][cells] state after each step, or null
-    int64_t cells;              // cells of the context (stride of history)
+    uint8_t* history;           // [k] rows: the state after each step, or null
+    int64_t cells;              // cells of the context
+    int64_t hist_stride;        // bytes between history rows
+    int32_t hist_packed;        // rows are 2-bit packed (else one byte a cell)
+    int32_t packed_aligned;     // every env starts on a 32-cell boundary and W % 32 == 0
     unsigned long long* counts; // optional [4]: pairs compared, candidate Philox blocks,
                                 // burning-cell draws, bit-plane word-steps scanned
     int32_t k;
@@ -137,6 +140,59 @@ __device__ void res_store(uint8_t* __restrict__ Fe, int H, int W, int WW, bool v
                 dst[j] = (uint8_t)(((c >> j) & 1u) + ((b >> j) & 1u) * 2u + ((dd >> j) & 1u) * 3u);
         }
     }
+}
+
+// bit j of v -> bit 2j of the result
+__device__ __forceinline__ uint64_t spread_bits(uint32_t v) {
+    uint64_t x = v;
+    x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+    x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+    x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    return (x | (x << 1)) & 0x5555555555555555ull;
+}
+
+// The env's state as 2-bit codes into a packed row P (cell g of the context
+// at bits 2g, 2g + 1 of the row; the env's first cell is g = off).  With
+// `aligned` every word of 32 cells owns 8 whole bytes (plain stores);
+// otherwise words share bytes with their neighbours and OR their bits into a
+// row the caller zeroed.
+__device__ void res_store2(uint32_t* __restrict__ P, int64_t off, int H, int W, int WW, bool aligned,
+                           const uint32_t* Bp, const uint32_t* C, const uint32_t* D) {
+    const int words = H * WW;
+    for (int i = threadIdx.x; i < words; i += blockDim.x) {
+        const int y = i / WW, w = i - (i / WW) * WW;
+        const int x0 = w << 5;
+        const int n = min(32, W - x0);
+        const uint32_t m = n == 32 ? 0xffffffffu : ((1u << n) - 1u);
+        const uint32_t b = Bp[(y + 1) * WW + w], dd = D[i];
+        // code = 1 can burn, 2 burning, 3 burned: low bit C|D, high bit B|D
+        const uint64_t code = spread_bits((C[i] | dd) & m) | (spread_bits((b | dd) & m) << 1);
+        const int64_t g0 = off + (int64_t)y * W + x0;
+        if (aligned) {
+            reinterpret_cast<uint2*>(P)[g0 >> 5] = make_uint2((uint32_t)code, (uint32_t)(code >> 32));
+        } else {
+            const int64_t bit = 2 * g0;
+            uint32_t* q = P + (bit >> 5);
+            const int o = (int)(bit & 31);
+            const uint32_t w0 = (uint32_t)(code << o);
+            const uint32_t w1 = o ? (uint32_t)(code >> (32 - o)) : (uint32_t)(code >> 32);
+            const uint32_t w2 = o ? (uint32_t)(code >> (64 - o)) : 0u;
+            if (w0) atomicOr(q, w0);
+            if (w1) atomicOr(q + 1, w1);
+            if (w2) atomicOr(q + 2, w2);
+        }
+    }
+}
+
+// history row `row` of the env: one byte a cell, or 2-bit packed
+__device__ __forceinline__ void res_record(const ResArgs& a, int64_t row, int64_t off, int H, int W, int WW,
+                                           bool vec, const uint32_t* Bp, const uint32_t* C, const uint32_t* D) {
+    const int64_t ho = row * a.hist_stride;
+    if (a.hist_packed)
+        res_store2(reinterpret_cast<uint32_t*>(a.history + ho), off, H, W, WW, a.packed_aligned != 0, Bp, C, D);
+    else
+        res_store(a.history + ho + off, H, W, WW, vec && (ho & 15) == 0, Bp, C, D);
 }
 
 // Bits of word w (cells 32w .. 32w+31) of row y covered by a drop of radius R
@@ -320,8 +376,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
             if (rec && s > 0) {
                 // record the state after step s - 1, then apply step s's drop
                 // (when recording it is not folded into the previous write-back)
-                const int64_t ho = (int64_t)(s - 1) * a.cells;
-                res_store(a.history + ho + off, H, W, WW, vec && (ho & 15) == 0, Bc, C, D);
+                res_record(a, s - 1, off, H, W, WW, vec, Bc, C, D);
                 hist_done = s;
                 if (threadIdx.x == 0) s_dous = 0;
                 __syncthreads();
@@ -623,10 +678,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         res_store(Fe, H, W, WW, vec, Bc, C, D);
         if (a.history != nullptr) {
             // the last step's state, and the unchanged state of the steps after the fire went out
-            for (int j = hist_done; j < a.k; ++j) {
-                const int64_t ho = (int64_t)j * a.cells;
-                res_store(a.history + ho + off, H, W, WW, vec && (ho & 15) == 0, Bc, C, D);
-            }
+            for (int j = hist_done; j < a.k; ++j) res_record(a, j, off, H, W, WW, vec, Bc, C, D);
         }
         if (threadIdx.x == 0) {
             a.t[e] = t;
@@ -1384,8 +1436,7 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         c->cur ^= 1;
         c->tact_cur ^= 1;
         if (c->hist != nullptr) {
-            err = cudaMemcpyAsync(c->hist + (int64_t)s0 * c->cells, c->d_state[c->cur], (size_t)c->cells,
-                                  cudaMemcpyDeviceToDevice, s);
+            err = jwf_record_row(c, s0, s);
             if (err != cudaSuccess) return err;
         }
     }
@@ -1441,6 +1492,14 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
     a.p_continue = c->P.p_continue;
     a.history = c->hist;
     a.cells = c->cells;
+    a.hist_packed = c->hist_packed ? 1 : 0;
+    a.hist_stride = c->hist_packed ? jwf_packed_bytes(c->cells) : c->cells;
+    a.packed_aligned = c->packed_aligned ? 1 : 0;
+    if (c->hist != nullptr && c->hist_packed && !c->packed_aligned) {
+        // rows are assembled by OR from words that share bytes
+        const cudaError_t e0 = cudaMemsetAsync(c->hist, 0, (size_t)k * (size_t)a.hist_stride, s);
+        if (e0 != cudaSuccess) return e0;
+    }
     RateConsts K;
     if (fused)
         jwf_rate_consts(c, &K);

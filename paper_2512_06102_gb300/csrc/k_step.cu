@@ -57,6 +57,78 @@ __global__ void k_load(const int64_t cells, const uint8_t* __restrict__ F0, uint
     }
 }
 
+// ---------------------------------------------------------------------------
+// 2-bit packed states: cell i in bits 2(i mod 4), 2(i mod 4) + 1 of byte i/4
+// ---------------------------------------------------------------------------
+// four states in the bytes of v -> their 8 packed bits
+__device__ __forceinline__ uint32_t pack4(uint32_t v) {
+    uint32_t x = v & 0x03030303u;
+    x = (x | (x >> 6)) & 0x000f000fu;
+    return (x | (x >> 12)) & 0xffu;
+}
+
+// 8 packed bits -> four states in the bytes of the result
+__device__ __forceinline__ uint32_t unpack4(uint32_t p) {
+    uint32_t x = p & 0xffu;
+    x = (x | (x << 12)) & 0x000f000fu;
+    return (x | (x << 6)) & 0x03030303u;
+}
+
+// n states -> ceil(n / 4) packed bytes (only the low two bits of a state are
+// kept); 16 states a thread when F is 16-byte and P 4-byte aligned
+__global__ void k_pack(const int64_t n, const uint8_t* __restrict__ F, uint8_t* __restrict__ P) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(F) & 15u) | (reinterpret_cast<uintptr_t>(P) & 3u)) == 0;
+    const int64_t n16 = vec ? (n >> 4) : 0;
+    for (int64_t i = i0; i < n16; i += stride) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(F) + i);
+        reinterpret_cast<uint32_t*>(P)[i] = pack4(v.x) | (pack4(v.y) << 8) | (pack4(v.z) << 16) | (pack4(v.w) << 24);
+    }
+    const int64_t nb = (n + 3) >> 2;
+    for (int64_t b = n16 * 4 + i0; b < nb; b += stride) {
+        uint32_t x = 0;
+        for (int j = 0; j < 4; ++j) {
+            const int64_t c = 4 * b + j;
+            if (c < n) x |= (uint32_t)(F[c] & 3u) << (2 * j);
+        }
+        P[b] = (uint8_t)x;
+    }
+}
+
+// ceil(n / 4) packed bytes -> n states in F (and F2 when not null); with t and
+// ep not null also the start of a run (t = episode = 0 for the N envs)
+__global__ void k_unpack(const int64_t n, const uint8_t* __restrict__ P, uint8_t* __restrict__ F,
+                         uint8_t* __restrict__ F2, int32_t* __restrict__ t, int32_t* __restrict__ ep, int32_t N) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uintptr_t al = (reinterpret_cast<uintptr_t>(F) & 15u) | (reinterpret_cast<uintptr_t>(F2) & 15u) |
+                         (reinterpret_cast<uintptr_t>(P) & 3u);
+    const int64_t n16 = al == 0 ? (n >> 4) : 0;
+    for (int64_t i = i0; i < n16; i += stride) {
+        const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(P) + i);
+        const uint4 v = make_uint4(unpack4(w), unpack4(w >> 8), unpack4(w >> 16), unpack4(w >> 24));
+        reinterpret_cast<uint4*>(F)[i] = v;
+        if (F2 != nullptr) reinterpret_cast<uint4*>(F2)[i] = v;
+    }
+    for (int64_t c = n16 * 16 + i0; c < n; c += stride) {
+        const uint8_t v = (uint8_t)((P[c >> 2] >> (2 * (c & 3))) & 3u);
+        F[c] = v;
+        if (F2 != nullptr) F2[c] = v;
+    }
+    if (t != nullptr)
+        for (int64_t j = i0; j < N; j += stride) {
+            t[j] = 0;
+            ep[j] = 0;
+        }
+}
+
+unsigned pack_blocks(int64_t work) {
+    int64_t b = (work + 255) / 256;
+    if (b < 1) b = 1;
+    return (unsigned)(b > 152 * 16 ? 152 * 16 : b);
+}
+
 __global__ void k_reset(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
                         const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs,
                         const uint8_t* __restrict__ env_mask, const uint8_t* __restrict__ F0,
@@ -194,6 +266,33 @@ cudaError_t jwf_launch_load(jwf_ctx* c, const uint8_t* F0, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t jwf_launch_pack(int64_t n, const uint8_t* states, uint8_t* packed, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_pack<<<pack_blocks((n + 15) / 16), 256, 0, s>>>(n, states, packed);
+    return cudaGetLastError();
+}
+
+cudaError_t jwf_launch_unpack(int64_t n, const uint8_t* packed, uint8_t* states, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_unpack<<<pack_blocks((n + 15) / 16), 256, 0, s>>>(n, packed, states, nullptr, nullptr, nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t jwf_launch_load_packed(jwf_ctx* c, const uint8_t* P0, cudaStream_t s) {
+    const int64_t w = (c->cells + 15) / 16;
+    c->cur = 0;
+    k_unpack<<<pack_blocks(w > c->N ? w : c->N), 256, 0, s>>>(c->cells, P0, c->d_state[0], c->d_F0, c->d_t,
+                                                              c->d_episode, c->N);
+    return cudaGetLastError();
+}
+
+cudaError_t jwf_record_row(jwf_ctx* c, int64_t row, cudaStream_t s) {
+    if (c->hist_packed)
+        return jwf_launch_pack(c->cells, c->d_state[c->cur], c->hist + row * jwf_packed_bytes(c->cells), s);
+    return cudaMemcpyAsync(c->hist + row * c->cells, c->d_state[c->cur], (size_t)c->cells,
+                           cudaMemcpyDeviceToDevice, s);
+}
+
 cudaError_t jwf_launch_reset(jwf_ctx* c, const uint8_t* env_mask, cudaStream_t s) {
     k_reset<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(c->d_tiles, c->d_H, c->d_W, c->d_off, env_mask,
                                                        c->d_F0, c->d_state[c->cur]);
@@ -227,9 +326,7 @@ cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, i
                                                                c->d_flag, c->d_F0, c->d_state[c->cur]);
         }
         cudaError_t err = cudaGetLastError();
-        if (err == cudaSuccess && c->hist != nullptr)
-            err = cudaMemcpyAsync(c->hist + (int64_t)st * c->cells, c->d_state[c->cur], (size_t)c->cells,
-                                  cudaMemcpyDeviceToDevice, s);
+        if (err == cudaSuccess && c->hist != nullptr) err = jwf_record_row(c, st, s);
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;

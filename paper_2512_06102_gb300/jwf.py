@@ -73,6 +73,12 @@ _SIGS = {
     "jwf_set_wind_series": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP]),
     "jwf_step_record": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 6),
     "jwf_set_seed": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "jwf_packed_size": (ctypes.c_int64, [ctypes.c_int64]),
+    "jwf_pack_states": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, _VP]),
+    "jwf_unpack_states": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, _VP]),
+    "jwf_load_state_packed": (ctypes.c_int, [_VP, _VP, _VP]),
+    "jwf_get_state_packed": (ctypes.c_int, [_VP, _VP, _VP]),
+    "jwf_step_record_packed": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 6),
     "jwf_agent_reset": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
     "jwf_agent_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _VP, _VP,
                                       ctypes.c_int32, _VP, _VP]),
@@ -81,6 +87,7 @@ _SIGS = {
     "jwf_size_classes": (ctypes.c_int32, [_VP, _VP]),
     "jwf_set_class_threads": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
     "jwf_set_round_steps": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "jwf_set_env_priority": (ctypes.c_int, [_VP, _VP]),
     "jwf_get_state": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "jwf_step_relaxed_fwd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_step_relaxed_bwd": (ctypes.c_int, [_VP] * 11),
@@ -124,6 +131,33 @@ def _ptr(t) -> int | None:
             raise ValueError("libjwf takes contiguous tensors")
         return t.data_ptr()
     return int(t)
+
+
+def packed_size(n_cells: int) -> int:
+    """Bytes of a 2-bit packed row of n states (ceil(n / 4) rounded up to 16)."""
+    return int(lib().jwf_packed_size(int(n_cells)))
+
+
+def pack_states(states: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """uint8 states (device, any shape, n elements) -> 2-bit packed uint8
+    [packed_size(n)] (cell i in bits 2(i mod 4).. of byte i // 4)."""
+    n = states.numel()
+    if out is None:
+        out = torch.zeros(packed_size(n), dtype=torch.uint8, device=states.device)
+    st = lib().jwf_pack_states(n, _ptr(states), _ptr(out), _stream(stream))
+    if st != 0:
+        raise RuntimeError(f"jwf_pack_states: {lib().jwf_status_string(st).decode()}")
+    return out
+
+
+def unpack_states(packed: torch.Tensor, n_cells: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """2-bit packed states -> uint8 [n_cells]."""
+    if out is None:
+        out = torch.empty(int(n_cells), dtype=torch.uint8, device=packed.device)
+    st = lib().jwf_unpack_states(int(n_cells), _ptr(packed), _ptr(out), _stream(stream))
+    if st != 0:
+        raise RuntimeError(f"jwf_unpack_states: {lib().jwf_status_string(st).decode()}")
+    return out
 
 
 def _stream(stream=None) -> int:
@@ -287,6 +321,18 @@ class Sim:
     def load_state(self, F0, stream=None):
         self._check(lib().jwf_load_state(self._h, _ptr(F0), _stream(stream)), "jwf_load_state")
 
+    def load_state_packed(self, P0, stream=None):
+        """Initial states as 2-bit packed bytes (pack_states of uint8 [cells])."""
+        self._check(lib().jwf_load_state_packed(self._h, _ptr(P0), _stream(stream)), "jwf_load_state_packed")
+
+    def state_packed(self, out=None, stream=None) -> torch.Tensor:
+        """The current state, 2-bit packed: uint8 [packed_size(cells)]."""
+        if out is None:
+            out = torch.zeros(packed_size(self.cells), dtype=torch.uint8,
+                              device=torch.device("cuda", torch.cuda.current_device()))
+        self._check(lib().jwf_get_state_packed(self._h, _ptr(out), _stream(stream)), "jwf_get_state_packed")
+        return out
+
     def reset(self, env_mask=None, stream=None):
         self._check(lib().jwf_reset(self._h, _ptr(env_mask), _stream(stream)), "jwf_reset")
 
@@ -310,15 +356,30 @@ class Sim:
     def set_round_steps(self, steps: int):
         self._check(lib().jwf_set_round_steps(self._h, int(steps)), "jwf_set_round_steps")
 
+    def set_env_priority(self, priority=None):
+        """Resident-kernel scheduling hint: envs with a higher priority (host
+        float [N], e.g. expected fire duration) are started first; None
+        restores the default order."""
+        if priority is None:
+            self._check(lib().jwf_set_env_priority(self._h, None), "jwf_set_env_priority")
+            return
+        pr = np.ascontiguousarray(np.asarray(priority, np.float32).reshape(-1))
+        if pr.size != self.N:
+            raise ValueError("priority must have one value per env")
+        self._check(lib().jwf_set_env_priority(self._h, pr.ctypes.data), "jwf_set_env_priority")
+
     def set_pair_counter(self, counter):
         """counter: int64 device tensor of four elements (pairs compared,
         candidate Philox blocks, remain-burning draws, words scanned), or None."""
         self._check(lib().jwf_set_pair_counter(self._h, _ptr(counter)), "jwf_set_pair_counter")
 
-    def step(self, k: int = 1, drops=None, burning=None, burnt=None, done=None, stream=None, history=None):
+    def step(self, k: int = 1, drops=None, burning=None, burnt=None, done=None, stream=None, history=None,
+             packed: bool = False):
         """Advance k steps; returns the (burning, burnt, done) tensors [k, N].
         history: optional uint8 [k, cells] device tensor that receives the
-        state after every step (jwf_step_record)."""
+        state after every step (jwf_step_record), or with packed=True uint8
+        [k, packed_size(cells)] that receives it 2-bit packed
+        (jwf_step_record_packed)."""
         dev = torch.device("cuda", torch.cuda.current_device())
         if burning is None:
             burning = torch.empty((k, self.N), dtype=torch.int32, device=dev)
@@ -329,6 +390,12 @@ class Sim:
         if history is None:
             self._check(lib().jwf_step(self._h, int(k), _ptr(drops), _ptr(burning), _ptr(burnt), _ptr(done),
                                        _stream(stream)), "jwf_step")
+        elif packed:
+            if tuple(history.shape) != (k, packed_size(self.cells)) or history.dtype != torch.uint8:
+                raise ValueError("packed history must be uint8 [k, packed_size(cells)]")
+            self._check(lib().jwf_step_record_packed(self._h, int(k), _ptr(drops), _ptr(burning), _ptr(burnt),
+                                                     _ptr(done), _ptr(history), _stream(stream)),
+                        "jwf_step_record_packed")
         else:
             if tuple(history.shape) != (k, self.cells) or history.dtype != torch.uint8:
                 raise ValueError("history must be uint8 [k, cells]")

@@ -175,3 +175,23 @@ def test_rollout_auto_reset_and_counts():
                            seed=0, t_max=2, auto_reset=False)
     b, d, done = ro2.step(3)
     assert done[:, 0].tolist() == [0, 1, 1] and (ro2.t == 3).all()
+
+
+def test_packed_format_hand_worked():
+    # states 1, 2, 3, 0 | 3 -> byte 0 = 1 + 2*4 + 3*16 + 0*64 = 57, byte 1 = 3
+    P = discrete.pack_states(np.array([1, 2, 3, 0, 3], np.uint8))
+    assert P.tolist() == [57, 3]
+    assert discrete.pack_states(np.zeros(0, np.uint8)).size == 0
+    assert discrete.pack_states(np.full(8, 3, np.uint8)).tolist() == [255, 255]
+
+
+def test_packed_format_roundtrip():
+    rng = np.random.default_rng(0)
+    for n in (1, 2, 3, 4, 5, 31, 33, 1000):
+        F = rng.integers(0, 4, size=n).astype(np.uint8)
+        P = discrete.pack_states(F)
+        assert P.size == (n + 3) // 4
+        np.testing.assert_array_equal(discrete.unpack_states(P, n), F)
+        # every cell's two bits, read one by one
+        for i in range(n):
+            assert (int(P[i // 4]) >> (2 * (i % 4))) & 3 == F[i]
