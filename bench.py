@@ -617,6 +617,13 @@ def bench_large(args, D, dev, rank):
     th = int(choice.get("tile_threads", 0))
     sim.set_kernel(jwf.KERNEL_TILED_FUSED, th)
     t_fused = timed(lambda: sim.step(BIG_T, dr), max(2, args.steps))
+    tma = sim.tile_copy()
+    t_loads = None
+    if tma:
+        # the same episode with the regions staged by plain 128-bit loads
+        sim.set_tile_copy(False)
+        t_loads = timed(lambda: sim.step(BIG_T, dr), max(2, args.steps))
+        sim.set_tile_copy(True)
     cnt = torch.zeros(4, dtype=torch.int64, device=dev)
     sim.set_pair_counter(cnt)
     sim.load_state(F0)
@@ -642,6 +649,8 @@ def bench_large(args, D, dev, rank):
             "kernel": "tiled table (table build included)" if t_table <= t_fused else "tiled fused",
             "fused_ms": round(t_fused * 1e3, 3), "table_with_build_ms": round(t_table * 1e3, 3),
             "round_steps": choice.get("round_steps"), "tile_threads": th,
+            "tile_copy": "tma" if tma else "loads",
+            "fused_loads_ms": None if t_loads is None else round(t_loads * 1e3, 3),
             "touched": {"word_steps": words, "cell_steps_scanned": 32 * words,
                         "fraction_of_cell_steps": round(32 * words / (cells * BIG_T), 4),
                         "per_touched_cell_rate": 32 * words / t_fused},

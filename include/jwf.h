@@ -306,6 +306,16 @@ JWF_API jwf_status jwf_set_class_threads(jwf_ctx* ctx, int32_t size_class, int32
  * the redundant work per tile, grows with it). */
 JWF_API jwf_status jwf_set_round_steps(jwf_ctx* ctx, int32_t steps);
 
+/* How the tiled kernels stage a tile's region: 1 = one TMA tensor copy
+ * (cp.async.bulk.tensor, the default where available), 0 = 128-bit loads by
+ * all threads.  TMA serves the envs whose first cell and row pitch (W) are
+ * multiples of 16 bytes; the others always take the loads.  Results do not
+ * depend on the mode.  Errors: JWF_EINVAL (mode), JWF_EUNSUPPORTED (1 asked,
+ * no env qualifies or the driver has no tensor-map encoder).
+ * jwf_tile_copy returns the mode in effect. */
+JWF_API jwf_status jwf_set_tile_copy(jwf_ctx* ctx, int32_t tma);
+JWF_API int32_t jwf_tile_copy(const jwf_ctx* ctx);
+
 /* Scheduling hint for the resident kernels: within each size class, envs are
  * taken from the work queue in descending h_priority (host float [N], read
  * during the call; e.g. the expected number of steps an env's fire lasts) so

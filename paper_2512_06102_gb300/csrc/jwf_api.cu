@@ -48,7 +48,7 @@ void free_all(jwf_ctx* c) {
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
                     c->d_tcnt, c->d_rtiles, c->d_adj, c->d_wser, c->d_agent_drops, c->d_agent_cnt,
-                    c->d_agent_done, c->d_stiles};
+                    c->d_agent_done, c->d_stiles, c->d_tmaps, c->d_tma_ok};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -248,6 +248,7 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
         }
     }
     if (err == cudaSuccess) err = cudaMemset(c->d_red_counter, 0, sizeof(uint32_t));
+    if (err == cudaSuccess) err = jwf_build_tile_maps(c);
     if (err == cudaSuccess) err = cudaDeviceSynchronize();
     if (err != cudaSuccess) {
         const jwf_status st = (err == cudaErrorMemoryAllocation) ? JWF_ENOMEM : JWF_ECUDA;
@@ -674,6 +675,16 @@ jwf_status jwf_set_env_priority(jwf_ctx* ctx, const float* h_priority) {
                  "jwf_set_env_priority");
     return JWF_OK;
 }
+
+jwf_status jwf_set_tile_copy(jwf_ctx* ctx, int32_t tma) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (tma != 0 && tma != 1) return fail(ctx, JWF_EINVAL, "jwf_set_tile_copy: mode must be 0 or 1");
+    if (tma == 1 && !ctx->tma) return fail(ctx, JWF_EUNSUPPORTED, "jwf_set_tile_copy: no env qualifies for TMA");
+    ctx->use_tma = tma == 1;
+    return JWF_OK;
+}
+
+int32_t jwf_tile_copy(const jwf_ctx* ctx) { return ctx != nullptr && ctx->tma && ctx->use_tma ? 1 : 0; }
 
 jwf_status jwf_set_round_steps(jwf_ctx* ctx, int32_t steps) {
     if (ctx == nullptr) return JWF_EINVAL;

@@ -63,6 +63,74 @@ __device__ __forceinline__ void jwf_cp_async_wait_all() { asm volatile("cp.async
 __device__ __forceinline__ void jwf_cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
+// TMA (cp.async.bulk.tensor) with an mbarrier: the tiled step stages its
+// region (tile plus halo) with one 2-D tensor copy.  A tensor map is the
+// 128-byte object cuTensorMapEncodeTiled writes; the kernels only pass its
+// global address to the copy instruction.
+// ---------------------------------------------------------------------------
+struct alignas(64) JwfTmap {
+    unsigned long long w[16];
+};
+
+__device__ __forceinline__ uint32_t jwf_smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void jwf_mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(jwf_smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the asynchronous (TMA) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void jwf_mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(jwf_smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool jwf_mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(jwf_smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ uint64_t jwf_globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of the barrier for at most `ns` nanoseconds;
+// false when the wait gave up.
+__device__ __forceinline__ bool jwf_mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t ns) {
+    const uint64_t t0 = jwf_globaltimer();
+    while (!jwf_mbar_try_wait(bar, parity))
+        if (jwf_globaltimer() - t0 > ns) return false;
+    return true;
+}
+// order this thread's earlier shared-memory accesses before later TMA accesses
+__device__ __forceinline__ void jwf_fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// 2-D tile load global -> shared, completion counted on the barrier (bytes);
+// x (innermost, elements) must be a multiple of 16 bytes, y is any row
+__device__ __forceinline__ void jwf_tma_load_2d(void* dst, const JwfTmap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            jwf_smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(jwf_smem_u32(bar))
+        : "memory");
+}
+// 2-D tile store shared -> global (elements outside the tensor are not written);
+// x >= 0 and a multiple of 16 bytes, y >= 0
+__device__ __forceinline__ void jwf_tma_store_2d(const JwfTmap* map, int x, int y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(jwf_smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void jwf_bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void jwf_bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // Parameters as the kernels see them (by value).
 // ---------------------------------------------------------------------------
 struct JwfDevParams {
@@ -150,6 +218,13 @@ struct jwf_ctx {
     uint16_t* d_tact[2] = {nullptr, nullptr};
     int tact_cur = 0;
     uint8_t* d_tsync = nullptr;
+    // tensor maps of the tiled step, per env: [2 buffers][region box, tile box][N]
+    // (built at creation for envs whose rows start 16-byte aligned), and the
+    // per-env flag that they exist
+    JwfTmap* d_tmaps = nullptr;
+    uint8_t* d_tma_ok = nullptr;
+    bool tma = false;
+    bool use_tma = true;                 // jwf_set_tile_copy: TMA (default) or plain loads
     int32_t* d_tburnt = nullptr;
     int32_t* d_tcnt = nullptr;
     bool tiles_valid = false;
@@ -184,6 +259,7 @@ struct jwf_ctx {
 
 // Device status word bits.
 #define JWF_DEVERR_INDEX 0x1u      // an index check failed (checked build)
+#define JWF_DEVERR_TMA 0x2u        // a tensor-copy wait gave up (the tile was not stepped)
 
 // ---------------------------------------------------------------------------
 // Launchers (host functions; each returns cudaGetLastError() of its launch).
@@ -227,6 +303,10 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
                                      cudaStream_t s);
 cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
                                   int32_t* burnt, uint8_t* done, bool fused, cudaStream_t s);
+// tensor maps of the tiled step's TMA copies (c->d_tmaps, c->d_tma_ok,
+// c->tma); envs that do not qualify, or a driver without the encoder, keep
+// the plain loads
+cudaError_t jwf_build_tile_maps(jwf_ctx* c);
 int jwf_tile_rows();
 int jwf_tile_cols();
 // shared memory a resident launch needs for env shape (H, W) with `threads`

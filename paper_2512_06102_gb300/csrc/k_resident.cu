@@ -4,22 +4,27 @@
 // Persistent CTAs pull whole envs from a work queue (largest first) and keep
 // each env in shared memory as bit planes, 32 cells per word: burning B
 // (double-buffered, one zero row above and below), can-burn C and burned D.
-// One step:
-//   * warps claim 32-word chunks from a per-step counter (dynamic, so the warp
-//     holding the fire front does not set the pace of the others); each lane
-//     owns one word and finds its can-burn cells with a burning neighbour and
-//     its burning cells from eight shifted ORs of the burning plane;
-//   * the warp shares its active cells out across its lanes (ballot + prefix
-//     sum), so every lane draws Philox numbers and evaluates ignition
-//     probabilities for the same number of cells;
-//   * the owner lane writes the next burning word, applies the next step's
-//     tanker drop to it, and counts; one __syncthreads ends the step.
+// One step has three phases separated by barriers:
+//   A. warps claim 32-word chunks from a per-step counter, skip chunks that
+//      cannot change, and for the others find, one word a lane, the can-burn
+//      cells with a burning neighbour and the burning cells (eight shifted ORs
+//      of the burning plane); the work items (remain-burning draws, compared
+//      (target, source) pairs) go to a block-wide queue in shared memory;
+//   B. all threads of the CTA evaluate the queued items (Philox draws, the
+//      ignition probability) and set ignition and burn-out bits;
+//   C. the claimed chunks are written back (new burning plane, the next
+//      step's tanker drop, counts).
+// For grids larger than shared memory, k_step_tiled steps tiles with a halo
+// (temporal blocking), the region staged by one TMA tensor copy.
 // The ignition probability of a compared (target, source) pair is read from
 // the q table or, in the fused variant, evaluated on the spot with the same
 // rate code as the table kernel (rate_model.cuh), so both variants draw the
 // same numbers against the same probabilities.  An env whose fire is out
 // stops early; with auto-reset it restarts from its initial state instead.
+#include <cuda.h>
+
 #include <type_traits>
+#include <vector>
 
 #include "jwf_internal.cuh"
 #include "rate_model.cuh"
@@ -746,11 +751,27 @@ struct TileArgs {
     uint8_t* synced;             // [tiles] both buffers hold this tile's interior
     int32_t* tile_burnt;         // [tiles] burned interior cells after the last round
     unsigned long long* counts;
+    // TMA: per env, the region-box map of the input buffer and the tile-box
+    // maps of both buffers; tma_ok[e] != 0 where they exist (else null)
+    const JwfTmap* tm_region;
+    const JwfTmap* tm_in_tile;
+    const JwfTmap* tm_out_tile;
+    const uint8_t* tma_ok;
+    uint32_t* status;
     int32_t kb;
     int32_t R;
     uint32_t key0, key1;
     float p_continue;
 };
+
+// TMA boxes: the region (tile plus kMaxRound rows and one 32-cell word of
+// columns on each side) and the tile itself, one byte a cell
+constexpr int kBoxCols = kTileCols + 64, kBoxRows = kRegionRows;
+constexpr uint64_t kTmaWaitNs = 2000000000ull;    // a tensor copy that takes 2 s has failed
+
+// the staged region fits where it is put (ignition, burn-out and queue arrays,
+// from a 128-byte boundary)
+static_assert((2 * kRegionWordsAll + kQCap) * 4 >= kBoxRows * kBoxCols + 128, "region staging does not fit");
 
 size_t tiled_smem_bytes(int threads) {
     // planes, warp scratch, chunk flags, ignition and burn-out planes, queue,
@@ -818,6 +839,8 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     __shared__ uint32_t s_act;
     __shared__ int32_t s_qn[3];
     __shared__ int s_active;
+    __shared__ int s_tma;
+    __shared__ alignas(8) uint64_t s_bar;
     __shared__ typename std::conditional<FUSED, RateConsts, int>::type sK_store;
     const RateConsts& sK = *reinterpret_cast<const RateConsts*>(&sK_store);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -843,18 +866,40 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         s_active = act;
     }
     __syncthreads();
+    const bool use_tma = a.tma_ok != nullptr && a.tma_ok[e] != 0;
     if (!s_active) {
         // no fire within reach: the interior stays as it is this round
+        bool copied = true;
         if (!a.synced[tix]) {
-            for (int i = threadIdx.x; i < TY * TX; i += NT) {
-                const int64_t g = off + (int64_t)(ty0 + i / TX) * W + tx0 + i % TX;
-                a.Fout[g] = a.Fin[g];
+            if (use_tma) {
+                // one tensor copy in, one out (cells outside the grid are
+                // neither read nor written)
+                if (threadIdx.x == 0) {
+                    uint8_t* stg = reinterpret_cast<uint8_t*>(sm) + ((128u - (jwf_smem_u32(sm) & 127u)) & 127u);
+                    jwf_mbar_init(&s_bar, 1);
+                    jwf_mbar_expect_tx(&s_bar, kTileRows * kTileCols);
+                    jwf_tma_load_2d(stg, a.tm_in_tile + e, tx0, ty0, &s_bar);
+                    if (jwf_mbar_wait_bounded(&s_bar, 0, kTmaWaitNs)) {
+                        jwf_tma_store_2d(a.tm_out_tile + e, tx0, ty0, stg);
+                        jwf_bulk_commit();
+                        jwf_bulk_wait_all();
+                    } else {
+                        atomicOr(a.status, JWF_DEVERR_TMA);
+                        jwf_mbar_wait_bounded(&s_bar, 0, kTmaWaitNs);     // a late copy lands before the exit
+                        copied = false;
+                    }
+                }
+            } else {
+                for (int i = threadIdx.x; i < TY * TX; i += NT) {
+                    const int64_t g = off + (int64_t)(ty0 + i / TX) * W + tx0 + i % TX;
+                    a.Fout[g] = a.Fin[g];
+                }
             }
         }
         if ((int)threadIdx.x < kb) atomicAdd(&a.cnt[((int64_t)threadIdx.x * 2 + 1) * a.N + e], a.tile_burnt[tix]);
         if (threadIdx.x == 0) {
             a.act_out[tix] = 0;
-            a.synced[tix] = 1;
+            a.synced[tix] = copied ? 1 : 0;
         }
         return;
     }
@@ -885,11 +930,17 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     uint32_t* Q = OU + kRegionWordsAll;
     int* wch = reinterpret_cast<int*>(Q + kQCap) + warp * kRegionChunks;     // chunks this warp claimed
     const int reach = (WW + 1 + 31) >> 5;
-    for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
-    for (int i = threadIdx.x; i < words; i += NT) {
-        IG[i] = 0u;
-        OU[i] = 0u;
+    // the region's bytes are staged where the ignition, burn-out and queue
+    // arrays go (they are not used before the steps start)
+    uint8_t* stg = reinterpret_cast<uint8_t*>(IG) + ((128u - (jwf_smem_u32(IG) & 127u)) & 127u);
+    if (use_tma && threadIdx.x == 0) {
+        // region rows [ty0 - kb, ty0 - kb + kBoxRows), columns [tx0 - 32, tx0 + 160):
+        // x is a multiple of 32 cells; rows and columns outside the grid read as 0
+        jwf_mbar_init(&s_bar, 1);
+        jwf_mbar_expect_tx(&s_bar, kBoxRows * kBoxCols);
+        jwf_tma_load_2d(stg, a.tm_region + e, tx0 - 32, ty0 - kb, &s_bar);
     }
+    for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
     if (threadIdx.x < 3) s_qn[threadIdx.x] = 0;
     if (threadIdx.x < 12) s_cnt[threadIdx.x / 4][threadIdx.x % 4] = 0;
     if (threadIdx.x == 0) {
@@ -899,13 +950,32 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     if (threadIdx.x < 3) s_chunk[threadIdx.x] = 0;
     ignw[lane] = 0u;
     outw[lane] = 0u;
+    if (use_tma && threadIdx.x == 0) s_tma = jwf_mbar_wait_bounded(&s_bar, 0, kTmaWaitNs) ? 1 : 0;
     __syncthreads();
+    if (use_tma && !s_tma) {
+        // the copy did not complete: report, let a late copy land, leave the tile
+        if (threadIdx.x == 0) {
+            atomicOr(a.status, JWF_DEVERR_TMA);
+            jwf_mbar_wait_bounded(&s_bar, 0, kTmaWaitNs);
+        }
+        return;
+    }
     // load the region (cells outside the grid read as no fuel)
     for (int i = threadIdx.x; i < words; i += NT) {
         const int ry = i / WW, w = i - (i / WW) * WW;
         const int gy = oy + ry, gx0 = ox + (w << 5);
         uint32_t b = 0, c = 0, dd = 0;
-        if (gy >= 0 && gy < H) {
+        if (use_tma) {
+            const uint4* src = reinterpret_cast<const uint4*>(stg + ry * kBoxCols + (w << 5));
+            const uint4 lo = src[0], hi = src[1];
+            const uint32_t v8[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                c |= nib_eq(v8[k], 0x01010101u) << (4 * k);
+                b |= nib_eq(v8[k], 0x02020202u) << (4 * k);
+                dd |= nib_eq(v8[k], 0x03030303u) << (4 * k);
+            }
+        } else if (gy >= 0 && gy < H) {
             const uint8_t* src = a.Fin + off + (int64_t)gy * W + gx0;
             if (gx0 >= 0 && gx0 + 32 <= W && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
                 const uint4 lo = __ldg(reinterpret_cast<const uint4*>(src));
@@ -933,6 +1003,10 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         D[i] = dd;
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < words; i += NT) {
+        IG[i] = 0u;
+        OU[i] = 0u;
+    }
     if (a.drops != nullptr) {
         const int gcx = a.drops[(int64_t)e * 2], gcy = a.drops[(int64_t)e * 2 + 1];
         res_action_rel(RH, WW, B0, D, gcx - ox, gcy - oy, a.R, gcx >= 0 && gcy >= 0);
@@ -1414,6 +1488,12 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         a.synced = c->d_tsync;
         a.tile_burnt = c->d_tburnt;
         a.counts = c->d_pairs;
+        const int bi = c->cur, bo = c->cur ^ 1;
+        a.tm_region = c->tma && c->use_tma ? c->d_tmaps + (size_t)(2 * bi) * c->N : nullptr;
+        a.tm_in_tile = c->tma && c->use_tma ? c->d_tmaps + (size_t)(2 * bi + 1) * c->N : nullptr;
+        a.tm_out_tile = c->tma && c->use_tma ? c->d_tmaps + (size_t)(2 * bo + 1) * c->N : nullptr;
+        a.tma_ok = c->tma && c->use_tma ? c->d_tma_ok : nullptr;
+        a.status = c->d_status;
         a.kb = kb;
         a.R = c->drop_radius;
         a.key0 = (uint32_t)(c->seed & 0xffffffffu);
@@ -1441,6 +1521,60 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         }
     }
     return cudaSuccess;
+}
+
+// Tensor maps of the tiled step: per state buffer b and env e, a map with the
+// region box (kBoxCols x kBoxRows) at d_tmaps[(2b) N + e] and one with the tile
+// box (kTileCols x kTileRows) at d_tmaps[(2b + 1) N + e].  An env qualifies when
+// its first cell and its row pitch (W bytes) are multiples of 16 bytes, as
+// the tensor copy requires.
+cudaError_t jwf_build_tile_maps(jwf_ctx* c) {
+    c->tma = false;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || fn == nullptr) {
+        cudaGetLastError();
+        return cudaSuccess;     // no encoder: the plain loads serve every env
+    }
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const Encode encode = reinterpret_cast<Encode>(fn);
+    static_assert(sizeof(CUtensorMap) == sizeof(JwfTmap), "tensor map size");
+    const int N = c->N;
+    std::vector<JwfTmap> maps((size_t)4 * N);
+    std::vector<uint8_t> ok(N, 0);
+    bool any = false;
+    for (int e = 0; e < N; ++e) {
+        const int64_t W = c->W[e], H = c->H[e];
+        if ((c->off[e] & 15) != 0 || (W & 15) != 0) continue;
+        bool good = true;
+        for (int b = 0; b < 2 && good; ++b) {
+            for (int kind = 0; kind < 2 && good; ++kind) {
+                const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+                const cuuint64_t strides[1] = {(cuuint64_t)W};
+                const cuuint32_t box[2] = {(cuuint32_t)(kind == 0 ? kBoxCols : kTileCols),
+                                           (cuuint32_t)(kind == 0 ? kBoxRows : kTileRows)};
+                const cuuint32_t estr[2] = {1, 1};
+                CUtensorMap* m = reinterpret_cast<CUtensorMap*>(&maps[(size_t)(2 * b + kind) * N + e]);
+                good = encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, c->d_state[b] + c->off[e], dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            }
+        }
+        ok[e] = good ? 1 : 0;
+        any = any || good;
+    }
+    if (!any) return cudaSuccess;
+    cudaError_t err = cudaMalloc(reinterpret_cast<void**>(&c->d_tmaps), maps.size() * sizeof(JwfTmap));
+    if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&c->d_tma_ok), (size_t)N);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(c->d_tmaps, maps.data(), maps.size() * sizeof(JwfTmap), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(c->d_tma_ok, ok.data(), (size_t)N, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) c->tma = true;
+    return err;
 }
 
 size_t jwf_resident_smem(int32_t H, int32_t W, int threads) {

@@ -88,6 +88,8 @@ _SIGS = {
     "jwf_set_class_threads": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
     "jwf_set_round_steps": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "jwf_set_env_priority": (ctypes.c_int, [_VP, _VP]),
+    "jwf_set_tile_copy": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "jwf_tile_copy": (ctypes.c_int32, [_VP]),
     "jwf_get_state": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "jwf_step_relaxed_fwd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_step_relaxed_bwd": (ctypes.c_int, [_VP] * 11),
@@ -355,6 +357,13 @@ class Sim:
 
     def set_round_steps(self, steps: int):
         self._check(lib().jwf_set_round_steps(self._h, int(steps)), "jwf_set_round_steps")
+
+    def set_tile_copy(self, tma: bool = True):
+        """Tiled kernels: stage regions with TMA tensor copies (True) or loads."""
+        self._check(lib().jwf_set_tile_copy(self._h, int(bool(tma))), "jwf_set_tile_copy")
+
+    def tile_copy(self) -> bool:
+        return bool(lib().jwf_tile_copy(self._h))
 
     def set_env_priority(self, priority=None):
         """Resident-kernel scheduling hint: envs with a higher priority (host

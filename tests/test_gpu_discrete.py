@@ -26,9 +26,12 @@ KERNELS = [jwf.KERNEL_PLAIN, jwf.KERNEL_RESIDENT, jwf.KERNEL_TILED]
 
 
 def _run_both(scn, q32, k, drops=None, seed=0, kernel=jwf.KERNEL_AUTO, t_max=0, auto_reset=False,
-              splits=None, threads=0):
+              splits=None, threads=0, tile_copy=None):
     sim = make_sim(scn, seed=seed, t_max=t_max, auto_reset=auto_reset)
     sim.set_kernel(kernel, threads)
+    if tile_copy is not None:
+        sim.set_tile_copy(tile_copy)
+        assert sim.tile_copy() == tile_copy
     sim.set_probs(to(q32))
     sim.load_state(to(scn.F0))
     ro = discrete.Rollout(scn.H, scn.W, scn.F0, q32, scn.params.p_continue, seed=seed, t_max=t_max,
@@ -350,6 +353,24 @@ def test_tiled_multi_tile_matches_oracle(shape, N, k):
     q32 = oracle_tables(scn)[0]
     drops = _fire_drops(scn, k, 31)
     _run_both(scn, q32, k, drops=drops, seed=8, kernel=jwf.KERNEL_TILED, splits=[k // 2, k - k // 2])
+
+
+@pytest.mark.parametrize("tma", [True, False])
+@pytest.mark.parametrize("shapes", [[(320, 640), (200, 336)],                  # every env takes the tensor copy
+                                    [(200, 336), (150, 300), (96, 160)]])     # a mix: rows of 300, odd offsets
+def test_tiled_tma_and_loads_match_oracle(shapes, tma):
+    """The tiled step with its regions staged by TMA tensor copies (envs whose
+    first cell and row pitch are 16-byte multiples; quiet tiles copied by a
+    tensor load and store) and by plain loads equals the oracle."""
+    require_gpu()
+    H = [s[0] for s in shapes]
+    W = [s[1] for s in shapes]
+    scn = scenarios.make_scenario(H, W, seed=33)
+    _fires_on_tile_corners(scn)
+    q32 = oracle_tables(scn)[0]
+    k = 40
+    drops = _fire_drops(scn, k, 33)
+    _run_both(scn, q32, k, drops=drops, seed=9, kernel=jwf.KERNEL_TILED, splits=[7, 16, 17], tile_copy=tma)
 
 
 def test_tiled_fused_equals_tiled_table():
