@@ -316,6 +316,14 @@ JWF_API jwf_status jwf_set_round_steps(jwf_ctx* ctx, int32_t steps);
 JWF_API jwf_status jwf_set_tile_copy(jwf_ctx* ctx, int32_t tma);
 JWF_API int32_t jwf_tile_copy(const jwf_ctx* ctx);
 
+/* Split a resident jwf_step of k >= 2 * steps steps into two launches: the
+ * first `steps` steps in the queue order, then the rest with each size
+ * class's envs reordered by their burning-cell count after the first part,
+ * largest first (the envs with the longest fires then start first instead
+ * of last).  Default 0 (never split).  Results do not depend on it; it
+ * is not applied while recording a history.  Errors: JWF_EINVAL (< 0). */
+JWF_API jwf_status jwf_set_reorder_steps(jwf_ctx* ctx, int32_t steps);
+
 /* Scheduling hint for the resident kernels: within each size class, envs are
  * taken from the work queue in descending h_priority (host float [N], read
  * during the call; e.g. the expected number of steps an env's fire lasts) so

@@ -48,7 +48,7 @@ void free_all(jwf_ctx* c) {
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
                     c->d_tcnt, c->d_rtiles, c->d_adj, c->d_wser, c->d_agent_drops, c->d_agent_cnt,
-                    c->d_agent_done, c->d_stiles, c->d_tmaps, c->d_tma_ok};
+                    c->d_agent_done, c->d_stiles, c->d_tmaps, c->d_tma_ok, c->d_order_dyn, c->d_lastb};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -190,6 +190,8 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = dev_alloc(&c->d_W, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_off, N + 1);
     if (err == cudaSuccess) err = dev_alloc(&c->d_order, N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_order_dyn, N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_lastb, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_tiles, tiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_state[0], (size_t)c->cells);
     if (err == cudaSuccess) err = dev_alloc(&c->d_state[1], (size_t)c->cells);
@@ -673,6 +675,13 @@ jwf_status jwf_set_env_priority(jwf_ctx* ctx, const float* h_priority) {
     }
     JWF_CUDA_TRY(ctx, cudaMemcpy(ctx->d_order, order.data(), ctx->N * sizeof(int32_t), cudaMemcpyHostToDevice),
                  "jwf_set_env_priority");
+    return JWF_OK;
+}
+
+jwf_status jwf_set_reorder_steps(jwf_ctx* ctx, int32_t steps) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (steps < 0) return fail(ctx, JWF_EINVAL, "jwf_set_reorder_steps: steps < 0");
+    ctx->reorder_steps = steps;
     return JWF_OK;
 }
 

@@ -58,6 +58,7 @@ struct ResArgs {
     int32_t* out_burnt;
     uint8_t* out_done;
     uint32_t* queue;            // [0] cursor, [1] CTAs finished
+    int32_t* last_burning;      // [N] burning cells after the launch's last step, or null
     uint8_t* history;           // [k] rows: the state after each step, or null
     int64_t cells;              // cells of the context
     int64_t hist_stride;        // bytes between history rows
@@ -373,6 +374,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         uint32_t* Bc = B0;
         uint32_t* Bn = B1;
         int32_t last_burnt = 0;
+        int32_t last_nb = 0;
         int hist_done = 0;          // history rows written
         const bool rec = a.history != nullptr;
         for (int s = 0; s < a.k; ++s) {
@@ -648,6 +650,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 if (a.out_done) a.out_done[o] = done ? 1 : 0;
             }
             last_burnt = nd;
+            last_nb = nb;
             if (done && a.auto_reset) {
                 // restart from the initial state with a fresh random stream
                 t = 0;
@@ -688,6 +691,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         if (threadIdx.x == 0) {
             a.t[e] = t;
             a.episode[e] = ep;
+            if (a.last_burning != nullptr) a.last_burning[e] = last_nb;
         }
         __syncthreads();
     }
@@ -1595,10 +1599,85 @@ int jwf_resident_threads(int32_t H, int32_t W) {
     return 256;
 }
 
+// Reorder each size class's envs by the burning count after the first part
+// of a split launch, largest first (envs whose fire is out go last): one CTA
+// per class, a counting sort over min(count, kSortKeys - 1).  Only the speed
+// depends on the order.
+constexpr int kSortKeys = 1024;
+
+__global__ void __launch_bounds__(1024) k_reorder(const int32_t* __restrict__ order_in, int32_t* __restrict__ order_out,
+                                                  const int32_t* __restrict__ last_burning, int4 starts, int4 counts) {
+    __shared__ int32_t hist[kSortKeys];
+    const int g = blockIdx.x;
+    const int start = g == 0 ? starts.x : g == 1 ? starts.y : g == 2 ? starts.z : starts.w;
+    const int n = g == 0 ? counts.x : g == 1 ? counts.y : g == 2 ? counts.z : counts.w;
+    for (int i = threadIdx.x; i < kSortKeys; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    // bin (kSortKeys - 1 - key): larger counts first
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int key = min(last_burning[order_in[start + i]], kSortKeys - 1);
+        atomicAdd(&hist[kSortKeys - 1 - key], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // exclusive scan of the bins by one warp (32 bins a lane)
+        const int lane = threadIdx.x;
+        int sum = 0;
+        for (int j = 0; j < kSortKeys / 32; ++j) sum += hist[lane * (kSortKeys / 32) + j];
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int run = incl - sum;
+        for (int j = 0; j < kSortKeys / 32; ++j) {
+            const int b = lane * (kSortKeys / 32) + j;
+            const int h = hist[b];
+            hist[b] = run;
+            run += h;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int e = order_in[start + i];
+        const int key = min(last_burning[e], kSortKeys - 1);
+        order_out[start + atomicAdd(&hist[kSortKeys - 1 - key], 1)] = e;
+    }
+}
+
+cudaError_t launch_resident_part(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning, int32_t* burnt,
+                                 uint8_t* done, const int32_t* order, int32_t* last_burning, cudaStream_t s);
+
 cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
                                      int32_t* burnt, uint8_t* done, cudaStream_t s) {
+    const int32_t k1 = c->reorder_steps;
+    const int ng = (int)c->groups.size();
+    if (k1 <= 0 || k < 2 * k1 || c->hist != nullptr || c->d_lastb == nullptr || ng > 4)
+        return launch_resident_part(c, k, drops, burning, burnt, done, c->d_order, nullptr, s);
+    // two launches: k1 steps in the creation order, then the rest with the
+    // envs whose fires are largest after k1 steps first (the longest fires
+    // set the end of the launch, so they should not start last)
+    cudaError_t err = launch_resident_part(c, k1, drops, burning, burnt, done, c->d_order, c->d_lastb, s);
+    if (err != cudaSuccess) return err;
+    int st[4] = {0, 0, 0, 0}, cn[4] = {0, 0, 0, 0};
+    for (int g = 0; g < ng; ++g) {
+        st[g] = c->groups[g].start;
+        cn[g] = c->groups[g].count;
+    }
+    k_reorder<<<ng, 1024, 0, s>>>(c->d_order, c->d_order_dyn, c->d_lastb, make_int4(st[0], st[1], st[2], st[3]),
+                                  make_int4(cn[0], cn[1], cn[2], cn[3]));
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const int64_t o = (int64_t)k1 * c->N;
+    return launch_resident_part(c, k - k1, drops ? drops + 2 * o : nullptr, burning ? burning + o : nullptr,
+                                burnt ? burnt + o : nullptr, done ? done + o : nullptr, c->d_order_dyn, nullptr, s);
+}
+
+cudaError_t launch_resident_part(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning, int32_t* burnt,
+                                 uint8_t* done, const int32_t* order, int32_t* last_burning, cudaStream_t s) {
     const bool fused = c->kernel == JWF_KERNEL_FUSED;
     ResArgs a;
+    a.last_burning = last_burning;
     a.H = c->d_H;
     a.W = c->d_W;
     a.off = c->d_off;
@@ -1659,7 +1738,7 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
             err = cudaStreamWaitEvent(gs, c->ev_fork, 0);
             if (err != cudaSuccess) return err;
         }
-        a.order = c->d_order + G.start;
+        a.order = order + G.start;
         a.nq = G.count;
         a.queue = c->d_queue + 2 * g;
         err = fused ? launch_v<true>(c, threads, a, K, smem, gs, G.count)

@@ -89,6 +89,7 @@ _SIGS = {
     "jwf_set_round_steps": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "jwf_set_env_priority": (ctypes.c_int, [_VP, _VP]),
     "jwf_set_tile_copy": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "jwf_set_reorder_steps": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "jwf_tile_copy": (ctypes.c_int32, [_VP]),
     "jwf_get_state": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "jwf_step_relaxed_fwd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -357,6 +358,11 @@ class Sim:
 
     def set_round_steps(self, steps: int):
         self._check(lib().jwf_set_round_steps(self._h, int(steps)), "jwf_set_round_steps")
+
+    def set_reorder_steps(self, steps: int = 32):
+        """Resident kernels: after `steps` steps, restart the launch with the
+        envs with the most burning cells first (0: one launch)."""
+        self._check(lib().jwf_set_reorder_steps(self._h, int(steps)), "jwf_set_reorder_steps")
 
     def set_tile_copy(self, tma: bool = True):
         """Tiled kernels: stage regions with TMA tensor copies (True) or loads."""

@@ -1,8 +1,10 @@
-"""The resident kernels' work-queue order (jwf_set_env_priority) changes no
-result: a ragged batch (several size classes) stepped in the default,
-ascending-index and random priority orders gives the oracle's final states
-(table variant, the oracle's FP32 table) and the same per-step counts and
-done flags, bit for bit, for both resident variants."""
+"""The resident kernels' work-queue order changes no result: a ragged batch
+(several size classes) stepped in the default, ascending-index and random
+priority orders (jwf_set_env_priority), and with the launch split after 8
+steps and the second part reordered by burning count on the device
+(jwf_set_reorder_steps), gives the oracle's final states (table variant, the
+oracle's FP32 table) and the same per-step counts and done flags, bit for
+bit, for both resident variants."""
 import numpy as np
 import pytest
 
@@ -27,8 +29,10 @@ def test_priority_order_changes_nothing(kernel):
     ro.step(k, np.ascontiguousarray(drops))
     N = len(scn.H)
     base = None
-    for prio in (None, np.arange(N, dtype=np.float32), rng.random(N).astype(np.float32)):
+    prios = (None, np.arange(N, dtype=np.float32), rng.random(N).astype(np.float32))
+    for prio, split in [(p, 0) for p in prios] + [(None, 8), (prios[2], 5)]:
         sim = make_sim(scn, seed=3)
+        sim.set_reorder_steps(split)
         if kernel == jwf.KERNEL_RESIDENT:
             sim.set_probs(to(q32))
         else:
