@@ -372,6 +372,7 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double acc = 0.0;
+    float accf = 0.f;           // a strip's share of dL/dp_continue, added to acc per strip
     for (int64_t it = (int64_t)blockIdx.x * kSweepWarps + warp; it < n_items; it += (int64_t)gridDim.x * kSweepWarps) {
         const int4 w = items[it];
         const int e = w.x, y0 = w.y, x0 = w.z;
@@ -445,7 +446,7 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
                     const int64_t v = off + (int64_t)y * W + x;
                     gun[v] = sat(p_ign != 0.f ? cur.au + nb * p_ign : cur.au);
                     glam[v] = g;
-                    if (pb.x != 0.f) acc += (double)(cur.ab * pb.x);
+                    if (pb.x != 0.f) accf += cur.ab * pb.x;
                 }
             }
             float P[8];
@@ -488,6 +489,8 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
             oc = on;
         }
         jwf_cp_async_wait_all();      // the rows fetched past the strip's end land before the ring is reused
+        acc += (double)accf;
+        accf = 0.f;
     }
     if (gpc == nullptr) return;
 #pragma unroll

@@ -284,7 +284,10 @@ def test_tiled_and_plain_kernels_agree():
     sim.set_relaxed_kernel(jwf.RELAXED_TILED)
     for a, b in zip(out[jwf.RELAXED_TILED][:5], out[jwf.RELAXED_PLAIN][:5]):
         assert torch.allclose(a, b, rtol=1e-6, atol=1e-7 * float(b.abs().max()))
-    assert out[jwf.RELAXED_TILED][5].item() == pytest.approx(out[jwf.RELAXED_PLAIN][5].item(), rel=1e-12)
+    # dL/dp_continue: the sweep sums a_b pb in float over a strip's 32 cells a lane before the FP64 total,
+    # the plain kernel in FP64 per cell; both within FP32 rounding of the sum of |a_b pb|
+    scale = float((ab.abs().double() * (to(pb.astype(np.float32)) * (1 - m)).double()).sum())
+    assert abs(out[jwf.RELAXED_TILED][5].item() - out[jwf.RELAXED_PLAIN][5].item()) <= 1e-6 * scale
 
 
 def test_multi_step_calls_equal_single_steps():
