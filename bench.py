@@ -543,7 +543,7 @@ def bench_relaxed(args, D, dev, rank):
     k_plain = time_kernels()
     sim.set_relaxed_kernel(jwf.RELAXED_TILED)
     hbm, peak_kind = peaks()
-    fwd_b, bwd_b, acc_b = 48, 60, 16
+    fwd_b, bwd_b, acc_b = 48, 60, 12
     ach_b = bwd_b * cells / k_tiled["bwd"] / 1e9
     ach_f = fwd_b * cells / k_tiled["fwd"] / 1e9
     rate = D.world * cells * REL_T / t_keep
@@ -955,7 +955,7 @@ def run_profile(case: str):
     L2, a few GB on the device at most): 'resident' = 1024 grids of 128^2, one
     200-step episode with drops on the fused resident kernel; 'relaxed' = 256
     grids of 128^2, one tiled relaxed forward step, one adjoint step and one
-    8-step rate-adjoint accumulation; 'tiled' = 2 grids of 4096^2, 800 steps with
+    16-step rate-adjoint accumulation; 'tiled' = 2 grids of 4096^2, 800 steps with
     drops on the fused tiled kernel (256 threads a tile, 16 steps a round)."""
     import torch
 
@@ -990,13 +990,13 @@ def run_profile(case: str):
         g = torch.Generator(device=dev).manual_seed(3)
         au = torch.randn(pu0.shape, device=dev, generator=g)
         ab = torch.randn(pu0.shape, device=dev, generator=g)
-        glam = torch.empty((8, sim.cells), device=dev)
+        glam = torch.empty((16, sim.cells), device=dev)
         gpc = torch.zeros(1, dtype=torch.float64, device=dev)
         ou, ob = sim.relaxed_fwd(pu0, pb0)
-        for t in range(8):
+        for t in range(16):
             sim.relaxed_bwd(pu0, pb0, au, ab, None, None, None, glam[t], gpc)
         gr = torch.zeros((sim.cells, 8), device=dev)
-        sim.rates_accumulate(glam, torch.stack([pb0] * 8), gr)
+        sim.rates_accumulate(glam, torch.stack([pb0] * 16), gr)
         torch.cuda.synchronize()
         print(f"profile case relaxed: {float(ou.sum()):.3f} {float(gr.abs().sum()):.3f}")
 

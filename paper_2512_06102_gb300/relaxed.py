@@ -29,7 +29,7 @@ import torch
 
 from . import jwf
 
-CHUNK = 8
+CHUNK = 16
 
 
 def segment_length(T: int, ckpt_every) -> int:
