@@ -410,21 +410,30 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
             }
             int my_b = 0, my_o = 0, my_x = 0;
             uint32_t my_pairs = 0, my_blocks = 0, my_burn = 0, my_chunks = 0;
-            // phase A: warps claim the chunks that can change, clear their
-            // words of the write buffer, and queue their work items
-            for (;;) {
-                int c = 0;
-                if (lane == 0) c = atomicAdd(&s_chunk[s % 3], 1);
-                c = __shfl_sync(0xffffffffu, c, 0);
-                if (c >= nchunks) break;
-                // a chunk with no burning cell within reach, whose write buffer
-                // holds no burning word, cannot change: skip it
-                bool need = fl_n[c] != 0;
-                for (int cc = max(c - reach, 0); cc <= min(c + reach, nchunks - 1) && !need; ++cc)
-                    need = fl_c[cc] != 0;
-                if (!need) continue;
+            // phase A: the chunks that can change are dealt to the warps,
+            // which clear their words of the write buffer and queue their
+            // work items.  A chunk with no burning cell within reach, whose
+            // write buffer holds no burning word, cannot change: it is
+            // skipped.  Every warp finds the needed chunks of a group of 32
+            // with one ballot (lane = chunk); the k-th needed chunk goes to
+            // warp k mod (warps), which also lists it for the write-back.
+            int n_need = 0;                       // needed chunks before this group
+            for (int g0 = 0; g0 < nchunks; g0 += 32) {
+                const int cl = g0 + lane;
+                bool nd = false;
+                if (cl < nchunks) {
+                    nd = fl_n[cl] != 0;
+                    for (int cc = max(cl - reach, 0); cc <= min(cl + reach, nchunks - 1); ++cc) nd |= fl_c[cc] != 0;
+                }
+                const uint32_t need_m = __ballot_sync(0xffffffffu, nd);
+                const int rk = n_need + __popc(need_m & ((1u << lane) - 1u));
+                const bool take = nd && (rk % (NT / 32)) == warp;
+                if (take) clist[rk] = cl;
+                n_need += __popc(need_m);
+                for (uint32_t mine = __ballot_sync(0xffffffffu, take); mine != 0u;) {
+                const int c = g0 + __ffs(mine) - 1;
+                mine &= mine - 1u;
                 ++my_chunks;
-                if (lane == 0) clist[atomicAdd(&s_ncl[s % 3], 1)] = c;
                 const int base = c << 5;
                 const int i = base + lane;
                 uint32_t burn = 0, cand = 0;
@@ -561,7 +570,9 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                     }
                     __syncwarp();
                 }
+                }
             }
+            if (threadIdx.x == 0) s_ncl[s % 3] = n_need;
             __syncthreads();
             // phase B: every thread of the CTA evaluates queued items
             {
