@@ -1074,17 +1074,24 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         // phase A: warps claim the chunks that can change and queue their work
         // items (one per burning cell; one per compared pair in the fused
         // variant, one per candidate cell in the table variant)
-        for (;;) {
-            int c = 0;
-            if (lane == 0) c = atomicAdd(&s_chunk[s % 3], 1);
-            c = __shfl_sync(0xffffffffu, c, 0);
-            if (c >= nchunks) break;
-            // a chunk with no burning cell within reach, whose write buffer
-            // holds no burning word, cannot change: skip it
-            bool need = fl_n[c] != 0;
-            for (int cc = max(c - reach, 0); cc <= min(c + reach, nchunks - 1) && !need; ++cc)
-                need = fl_c[cc] != 0;
-            if (!need) continue;
+        // (a chunk with no burning cell within reach, whose write buffer holds
+        // no burning word, cannot change and is skipped; the needed chunks of
+        // a group of 32 are found by one ballot and the k-th goes to warp
+        // k mod (warps))
+        int n_need = 0;
+        for (int g0 = 0; g0 < nchunks; g0 += 32) {
+            const int cl = g0 + lane;
+            bool nd = false;
+            if (cl < nchunks) {
+                nd = fl_n[cl] != 0;
+                for (int cc = max(cl - reach, 0); cc <= min(cl + reach, nchunks - 1); ++cc) nd |= fl_c[cc] != 0;
+            }
+            const uint32_t need_m = __ballot_sync(0xffffffffu, nd);
+            const int rk = n_need + __popc(need_m & ((1u << lane) - 1u));
+            n_need += __popc(need_m);
+            for (uint32_t mine = __ballot_sync(0xffffffffu, nd && (rk % (NT / 32)) == warp); mine != 0u;) {
+            const int c = g0 + __ffs(mine) - 1;
+            mine &= mine - 1u;
             if (lane == 0) wch[my_chunks] = c;
             ++my_chunks;
             const int base = c << 5;
@@ -1216,6 +1223,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
                                     lane);
                 }
                 __syncwarp();
+            }
             }
         }
         __syncthreads();
