@@ -516,7 +516,8 @@ def bench_relaxed(args, D, dev, rank):
         glam = torch.empty_like(pu0)
         gpc = torch.zeros(1, dtype=torch.float64, device=dev)
         out = {}
-        for name in ("fwd", "bwd"):
+        two = (torch.empty((2,) + pu0.shape, device=dev), torch.empty((2,) + pu0.shape, device=dev))
+        for name in ("fwd", "fwd2", "bwd"):
             for i in range(n + 1):
                 if i == 1:
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -524,6 +525,9 @@ def bench_relaxed(args, D, dev, rank):
                 src, dst = bufs[i % 2], bufs[(i + 1) % 2]
                 if name == "fwd":
                     sim.relaxed_fwd(src[0], src[1], None, dst[0], dst[1])
+                elif name == "fwd2":
+                    # two steps in one pass (the rollout's forward)
+                    sim.relaxed_fwd_steps(bufs[0][0], bufs[0][1], two[0], two[1])
                 else:
                     gs, gd = g[i % 2], g[(i + 1) % 2]
                     sim.relaxed_bwd(bufs[0][0], bufs[0][1], gs[0], gs[1], None, gd[0], gd[1], glam, gpc)
@@ -543,17 +547,18 @@ def bench_relaxed(args, D, dev, rank):
     k_plain = time_kernels()
     sim.set_relaxed_kernel(jwf.RELAXED_TILED)
     hbm, peak_kind = peaks()
-    fwd_b, bwd_b, acc_b = 48, 60, 12
+    fwd1_b, fwd_b, bwd_b, acc_b = 48, 28, 60, 12
     ach_b = bwd_b * cells / k_tiled["bwd"] / 1e9
-    ach_f = fwd_b * cells / k_tiled["fwd"] / 1e9
+    ach_f = fwd1_b * cells / k_tiled["fwd"] / 1e9
+    ach_f2 = 2 * fwd_b * cells / k_tiled["fwd2"] / 1e9
     rate = D.world * cells * REL_T / t_keep
     sim.close()
     return {"metric": "fwd+bwd cell-steps/s at 256x128^2, T=100",
             "value": rate, "unit": "fwd+bwd cell-steps/s",
             "ms_per_step": t_keep * 1e3, "dtype": "f32",
             "memory_policy": "every state kept" if keep_all == 0 else "sqrt(T) checkpoints",
-            "path_bytes_model": f"{fwd_b + bwd_b + acc_b} B/cell-step ({fwd_b} fwd + {bwd_b} fused adjoint + "
-                                f"{acc_b} rate-adjoint accumulation)",
+            "path_bytes_model": f"{fwd_b + bwd_b + acc_b} B/cell-step ({fwd_b} two-step fwd + {bwd_b} fused "
+                                f"adjoint + {acc_b} rate-adjoint accumulation)",
             "path_gbs": round((fwd_b + bwd_b + acc_b) * rate / D.world / 1e9, 1),
             "path_frac": round((fwd_b + bwd_b + acc_b) * rate / D.world / 1e9 / hbm, 4),
             "roofline": {"bound": "hbm", "achieved": round(ach_b, 1), "peak": hbm, "unit": "GB/s",
@@ -566,6 +571,11 @@ def bench_relaxed(args, D, dev, rank):
                              "frac": round(ach_f / hbm, 4), "kernel": "k_relaxed_fwd_tiled",
                              "kernel_us": round(k_tiled["fwd"] * 1e6, 2),
                              "bytes_model": "48 B/cell-step (8 B state in, 32 B rates, 8 B state out)"},
+            "roofline_fwd2": {"bound": "hbm", "achieved": round(ach_f2, 1), "peak": hbm, "unit": "GB/s",
+                              "frac": round(ach_f2 / hbm, 4), "kernel": "k_relaxed_fwd2_tiled (two steps a pass)",
+                              "kernel_us": round(k_tiled["fwd2"] * 1e6, 2),
+                              "bytes_model": "28 B/cell-step (per two steps: 8 B state in, 32 B rates, 16 B "
+                                             "states out)"},
             "sqrt_checkpoints": {"ms_per_step": round(t_sqrt * 1e3, 3),
                                  "value": D.world * cells * REL_T / t_sqrt},
             "T1000_sqrt_checkpoints": {"ms_per_step": round(t_1000 * 1e3, 3),

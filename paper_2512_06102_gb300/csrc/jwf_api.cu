@@ -47,7 +47,7 @@ void free_all(jwf_ctx* c) {
                     c->d_F0, c->d_q, c->d_r, c->d_t, c->d_episode, c->d_cnt, c->d_flag,
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
-                    c->d_tcnt, c->d_rtiles, c->d_adj, c->d_wser, c->d_agent_drops, c->d_agent_cnt,
+                    c->d_tcnt, c->d_rtiles, c->d_r2tiles, c->d_adj, c->d_wser, c->d_agent_drops, c->d_agent_cnt,
                     c->d_agent_done, c->d_stiles, c->d_tmaps, c->d_tma_ok, c->d_order_dyn, c->d_lastb};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
@@ -150,6 +150,11 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
         for (int y = 0; y < c->H[e]; y += JWF_RT_ROWS)
             for (int x = 0; x < c->W[e]; x += JWF_RT_COLS) rtiles.push_back(make_int4(e, y, x, 0));
     c->n_rtiles = (int64_t)rtiles.size();
+    std::vector<int4> r2tiles;
+    for (int32_t e = 0; e < N; ++e)
+        for (int y = 0; y < c->H[e]; y += JWF_R2_ROWS)
+            for (int x = 0; x < c->W[e]; x += JWF_R2_COLS) r2tiles.push_back(make_int4(e, y, x, 0));
+    c->n_r2tiles = (int64_t)r2tiles.size();
     std::vector<int4> stiles;
     for (int32_t e = 0; e < N; ++e)
         for (int y = 0; y < c->H[e]; y += JWF_SW_ROWS)
@@ -202,6 +207,7 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_gr, (size_t)c->cells * 8);
     if (err == cudaSuccess && rates) err = dev_alloc(&c->d_adj, (size_t)c->cells * 2);
     if (err == cudaSuccess) err = dev_alloc(&c->d_rtiles, rtiles.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_r2tiles, r2tiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_stiles, stiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_agent_drops, 2 * (size_t)N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_agent_cnt, (size_t)N);
@@ -229,6 +235,8 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = cudaMemset(c->d_tburnt, 0, tiles4.size() * sizeof(int32_t));
     if (err == cudaSuccess)
         err = cudaMemcpy(c->d_rtiles, rtiles.data(), rtiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(c->d_r2tiles, r2tiles.data(), r2tiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess)
         err = cudaMemcpy(c->d_stiles, stiles.data(), stiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_H, c->H.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -788,12 +796,24 @@ jwf_status jwf_relaxed_fwd_steps(jwf_ctx* ctx, int32_t n_steps, const float* d_p
         return fail(ctx, JWF_EINVAL, "jwf_relaxed_fwd_steps: outputs overlap inputs");
     if (!ctx->have_params || !ctx->have_rates)
         return fail(ctx, JWF_ESTATE, "jwf_relaxed_fwd_steps: needs parameters and a rate table");
-    for (int32_t t = 0; t < n_steps; ++t) {
+    for (int32_t t = 0; t < n_steps;) {
         const float* iu = t == 0 ? d_pun : d_pun_out + (t - 1) * C;
         const float* ib = t == 0 ? d_pburn : d_pburn_out + (t - 1) * C;
         const float* m = d_masks != nullptr ? d_masks + (int64_t)t * C : nullptr;
-        JWF_CUDA_TRY(ctx, jwf_launch_relaxed_fwd(ctx, iu, ib, m, d_pun_out + t * C, d_pburn_out + t * C, S(stream)),
-                     "jwf_relaxed_fwd_steps");
+        if (t + 1 < n_steps && ctx->relaxed_kernel == JWF_RELAXED_TILED) {
+            // two steps per pass: the rate rows are read once for both
+            JWF_CUDA_TRY(ctx,
+                         jwf_launch_relaxed_fwd2(ctx, iu, ib, m, m != nullptr ? m + C : nullptr, d_pun_out + t * C,
+                                                 d_pburn_out + t * C, d_pun_out + (t + 1) * C,
+                                                 d_pburn_out + (t + 1) * C, S(stream)),
+                         "jwf_relaxed_fwd_steps");
+            t += 2;
+        } else {
+            JWF_CUDA_TRY(ctx,
+                         jwf_launch_relaxed_fwd(ctx, iu, ib, m, d_pun_out + t * C, d_pburn_out + t * C, S(stream)),
+                         "jwf_relaxed_fwd_steps");
+            t += 1;
+        }
     }
     return JWF_OK;
 }

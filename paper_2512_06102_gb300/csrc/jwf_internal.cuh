@@ -145,6 +145,9 @@ struct JwfDevParams {
 // The tiled relaxed kernels walk 2-D tiles of JWF_RT_ROWS x JWF_RT_COLS cells.
 #define JWF_RT_ROWS 16
 #define JWF_RT_COLS 64
+// The two-step relaxed forward walks tiles of JWF_R2_ROWS x JWF_R2_COLS cells.
+#define JWF_R2_ROWS 16
+#define JWF_R2_COLS 32
 // The relaxed adjoint sweeps strips of JWF_SW_COLS output columns (one warp,
 // a halo column on each side) down JWF_SW_ROWS rows.
 #define JWF_SW_COLS 30
@@ -215,6 +218,8 @@ struct jwf_ctx {
     int64_t n_tiles4 = 0;
     int4* d_rtiles = nullptr;            // (env, first row, first column) per relaxed 2-D tile
     int64_t n_rtiles = 0;
+    int4* d_r2tiles = nullptr;           // (env, first row, first column) per two-step forward tile
+    int64_t n_r2tiles = 0;
     int4* d_stiles = nullptr;            // (env, first row, first column) per adjoint sweep strip
     int64_t n_stiles = 0;
     int relaxed_kernel = 0;              // 0: tiled (fused adjoint), 1: plain (two-pass adjoint)
@@ -316,6 +321,12 @@ int jwf_tile_cols();
 size_t jwf_resident_smem(int32_t H, int32_t W, int threads);
 int jwf_resident_threads(int32_t H, int32_t W);
 
+// two relaxed steps in one pass (tiled kernels only): the state after step t
+// (pun1, pburn1) and after step t + 1 (pun2, pburn2); masks of the two steps
+// or null
+cudaError_t jwf_launch_relaxed_fwd2(const jwf_ctx* c, const float* pun, const float* pburn, const float* mask0,
+                                    const float* mask1, float* pun1, float* pburn1, float* pun2, float* pburn2,
+                                    cudaStream_t s);
 cudaError_t jwf_launch_relaxed_fwd(const jwf_ctx* c, const float* pun, const float* pburn,
                                    const float* mask, float* pun_out, float* pburn_out,
                                    cudaStream_t s);

@@ -277,6 +277,154 @@ k_relaxed_fwd_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32
     }
 }
 
+// Two steps per pass.  A tile of kR2H x kR2W output cells is staged with a
+// two-cell halo: step t runs on the tile and the ring of cells around it
+// (whose burning probabilities step t + 1 reads), step t + 1 on the tile, so
+// each rate row is read once for both steps (32 B a cell plus the halo's
+// share, instead of 2 x 32 B).  Both steps write the tile's states; every
+// cell's arithmetic is the one-step kernel's, so the results are identical.
+constexpr int kR2H = JWF_R2_ROWS, kR2W = JWF_R2_COLS;
+constexpr int kF2T = 256;                                           // threads of the two-step CTA
+constexpr int kA1H = kR2H + 2, kA1W = kR2W + 2, kA1N = kA1H * kA1W;  // cells of step t (tile + 1)
+constexpr int kA0H = kR2H + 4, kA0W = kR2W + 4, kA0N = kA0H * kA0W;  // p_burn read by step t (tile + 2)
+struct Fwd2Stage {
+    float r[kA1N * 8];
+    float pu[kA1N];
+    float pb[kA0N], m0[kA0N];
+    float m1[kA1N];
+};
+struct Fwd2Smem {
+    Fwd2Stage st[2];
+    float pb1[kA1N];    // p_burn after step t (masked for step t + 1 before use)
+    float pu1[kA1N];    // p_un after step t
+};
+size_t fwd2_smem_bytes() { return sizeof(Fwd2Smem); }
+
+__device__ __forceinline__ void fwd2_stage(Fwd2Stage& b, const int4* __restrict__ tiles, int64_t ti,
+                                           const int32_t* __restrict__ Hs, const int32_t* __restrict__ Ws,
+                                           const int64_t* __restrict__ offs, const float* __restrict__ r,
+                                           const float* __restrict__ pun, const float* __restrict__ pburn,
+                                           const float* __restrict__ mask0, const float* __restrict__ mask1) {
+    const int4 tl = tiles[ti];
+    const int e = tl.x, y0 = tl.y, x0 = tl.z;
+    const int H = Hs[e], W = Ws[e];
+    const int64_t off = offs[e];
+    for (int i = threadIdx.x; i < kA1N; i += kF2T) {
+        const int y = y0 - 1 + i / kA1W, x = x0 - 1 + i % kA1W;
+        if (y < 0 || y >= H || x < 0 || x >= W) {
+            b.pu[i] = 0.f;
+            b.m1[i] = 0.f;
+            continue;
+        }
+        const int64_t v = off + (int64_t)y * W + x;
+        jwf_cp_async16(&b.r[i * 8], r + v * 8);
+        jwf_cp_async16(&b.r[i * 8 + 4], r + v * 8 + 4);
+        jwf_cp_async4(&b.pu[i], pun + v);
+        if (mask1 != nullptr)
+            jwf_cp_async4(&b.m1[i], mask1 + v);
+        else
+            b.m1[i] = 0.f;
+    }
+    for (int i = threadIdx.x; i < kA0N; i += kF2T) {
+        const int y = y0 - 2 + i / kA0W, x = x0 - 2 + i % kA0W;
+        if (y < 0 || y >= H || x < 0 || x >= W) {
+            b.pb[i] = 0.f;
+            b.m0[i] = 0.f;
+            continue;
+        }
+        const int64_t v = off + (int64_t)y * W + x;
+        jwf_cp_async4(&b.pb[i], pburn + v);
+        if (mask0 != nullptr)
+            jwf_cp_async4(&b.m0[i], mask0 + v);
+        else
+            b.m0[i] = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(kF2T)
+k_relaxed_fwd2_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32_t* __restrict__ Hs,
+                     const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs,
+                     const float* __restrict__ r, const float* __restrict__ pun,
+                     const float* __restrict__ pburn, const float* __restrict__ mask0,
+                     const float* __restrict__ mask1, float p_continue, float* __restrict__ pun1,
+                     float* __restrict__ pburn1, float* __restrict__ pun2, float* __restrict__ pburn2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Fwd2Smem& S = *reinterpret_cast<Fwd2Smem*>(smem_raw);
+    int cur = 0;
+    if ((int64_t)blockIdx.x < n_tiles)
+        fwd2_stage(S.st[0], tiles, blockIdx.x, Hs, Ws, offs, r, pun, pburn, mask0, mask1);
+    jwf_cp_async_commit();
+    for (int64_t ti = blockIdx.x; ti < n_tiles; ti += gridDim.x, cur ^= 1) {
+        if (ti + gridDim.x < n_tiles)
+            fwd2_stage(S.st[cur ^ 1], tiles, ti + gridDim.x, Hs, Ws, offs, r, pun, pburn, mask0, mask1);
+        jwf_cp_async_commit();
+        const int4 tl = tiles[ti];
+        const int e = tl.x, y0 = tl.y, x0 = tl.z;
+        const int H = Hs[e], W = Ws[e];
+        const int64_t off = offs[e];
+        jwf_cp_async_wait_prev();
+        __syncthreads();
+        Fwd2Stage& b = S.st[cur];
+        if (mask0 != nullptr) {
+            for (int q = threadIdx.x; q < kA0N; q += kF2T) b.pb[q] = b.pb[q] * (1.0f - b.m0[q]);
+            __syncthreads();
+        }
+        // step t on the tile and its one-cell ring
+        for (int j = threadIdx.x; j < kA1N; j += kF2T) {
+            const int ay = j / kA1W, ax = j - (j / kA1W) * kA1W;
+            const int y = y0 - 1 + ay, x = x0 - 1 + ax;
+            if (y < 0 || y >= H || x < 0 || x >= W) {
+                S.pb1[j] = 0.f;
+                S.pu1[j] = 0.f;
+                continue;
+            }
+            const float4 ra = *reinterpret_cast<const float4*>(&b.r[j * 8]);
+            const float4 rb = *reinterpret_cast<const float4*>(&b.r[j * 8 + 4]);
+            const float rv[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+            float lam = 0.f;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) lam += b.pb[(ay + 1 - jwf_dr(d)) * kA0W + (ax + 1 - jwf_dx(d))] * rv[d];
+            const float p_ign = -expm1f(-lam);
+            const float pu = b.pu[j];
+            const float newly = pu * p_ign;
+            const float u1 = pu - newly;
+            const float b1 = newly + p_continue * b.pb[(ay + 1) * kA0W + ax + 1];
+            S.pu1[j] = u1;
+            S.pb1[j] = b1;
+            if (ay >= 1 && ay <= kR2H && ax >= 1 && ax <= kR2W) {
+                const int64_t v = off + (int64_t)y * W + x;
+                pun1[v] = u1;
+                pburn1[v] = b1;
+            }
+        }
+        __syncthreads();
+        if (mask1 != nullptr) {
+            for (int q = threadIdx.x; q < kA1N; q += kF2T) S.pb1[q] = S.pb1[q] * (1.0f - b.m1[q]);
+            __syncthreads();
+        }
+        // step t + 1 on the tile
+        for (int j = threadIdx.x; j < kR2H * kR2W; j += kF2T) {
+            const int ty = j / kR2W, tx = j - (j / kR2W) * kR2W;
+            const int y = y0 + ty, x = x0 + tx;
+            if (y >= H || x >= W) continue;
+            const int a1 = (ty + 1) * kA1W + (tx + 1);
+            const float4 ra = *reinterpret_cast<const float4*>(&b.r[a1 * 8]);
+            const float4 rb = *reinterpret_cast<const float4*>(&b.r[a1 * 8 + 4]);
+            const float rv[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+            float lam = 0.f;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) lam += S.pb1[(ty + 1 - jwf_dr(d)) * kA1W + (tx + 1 - jwf_dx(d))] * rv[d];
+            const float p_ign = -expm1f(-lam);
+            const float pu = S.pu1[a1];
+            const float newly = pu * p_ign;
+            const int64_t v = off + (int64_t)y * W + x;
+            pun2[v] = pu - newly;
+            pburn2[v] = newly + p_continue * S.pb1[a1];
+        }
+        __syncthreads();
+    }
+}
+
 // Column-sweep adjoint.  A warp owns a strip of JWF_SW_COLS output columns
 // (lane L is column x0 - 1 + L: lanes 0 and 31 are halo columns) and walks
 // down rows y0 - 1 .. y1, one target row per iteration, all in registers:
@@ -547,6 +695,31 @@ cudaError_t jwf_launch_relaxed_fwd(const jwf_ctx* c, const float* pun, const flo
                                                                c->d_r, pun, pburn, mask, c->P.p_continue, pun_out,
                                                                pburn_out);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t jwf_launch_relaxed_fwd2(const jwf_ctx* c, const float* pun, const float* pburn, const float* mask0,
+                                    const float* mask1, float* pun1, float* pburn1, float* pun2, float* pburn2,
+                                    cudaStream_t s) {
+    // persistent CTAs, as many as fit an SM (about three)
+    static int per_sm[64] = {};
+    const size_t smem = fwd2_smem_bytes();
+    if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
+    if (per_sm[c->device] == 0) {
+        cudaError_t err =
+            cudaFuncSetAttribute(k_relaxed_fwd2_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        int b = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_fwd2_tiled, kF2T, smem);
+        if (err != cudaSuccess) return err;
+        per_sm[c->device] = b > 0 ? b : 1;
+    }
+    int64_t grid = (int64_t)c->num_sms * per_sm[c->device];
+    if (grid > c->n_r2tiles) grid = c->n_r2tiles;
+    if (grid < 1) grid = 1;
+    k_relaxed_fwd2_tiled<<<(unsigned)grid, kF2T, smem, s>>>(c->d_r2tiles, c->n_r2tiles, c->d_H, c->d_W, c->d_off,
+                                                             c->d_r, pun, pburn, mask0, mask1, c->P.p_continue,
+                                                             pun1, pburn1, pun2, pburn2);
     return cudaGetLastError();
 }
 
