@@ -964,8 +964,8 @@ def run_profile(case: str):
     """Small cases of the workloads for ncu captures (inputs still larger than
     L2, a few GB on the device at most): 'resident' = 1024 grids of 128^2, one
     200-step episode with drops on the fused resident kernel; 'relaxed' = 256
-    grids of 128^2, one tiled relaxed forward step, one adjoint step and one
-    16-step rate-adjoint accumulation; 'tiled' = 2 grids of 4096^2, 800 steps with
+    grids of 128^2, one tiled relaxed forward step, one two-step forward pass,
+    sixteen adjoint steps and one 16-step rate-adjoint accumulation; 'tiled' = 2 grids of 4096^2, 800 steps with
     drops on the fused tiled kernel (256 threads a tile, 16 steps a round)."""
     import torch
 
@@ -1003,6 +1003,8 @@ def run_profile(case: str):
         glam = torch.empty((16, sim.cells), device=dev)
         gpc = torch.zeros(1, dtype=torch.float64, device=dev)
         ou, ob = sim.relaxed_fwd(pu0, pb0)
+        two = (torch.empty((2, sim.cells), device=dev), torch.empty((2, sim.cells), device=dev))
+        sim.relaxed_fwd_steps(pu0, pb0, two[0], two[1])
         for t in range(16):
             sim.relaxed_bwd(pu0, pb0, au, ab, None, None, None, glam[t], gpc)
         gr = torch.zeros((sim.cells, 8), device=dev)
