@@ -158,12 +158,11 @@ __device__ void block_reduce_vec(double (&val)[NV], double* smem /* [32][NV] */)
 constexpr int kRbThreads = 256;
 constexpr int kRbScalars = 5;   // p_base, alpha_w1, alpha_w2, alpha_s, alpha_gamma
 
-// Rate adjoint of a chunk of relaxed steps: gr[v][d] += sum_t glam_t(v) pb_t(v - Delta_d)
-// (pb = (1 - m) p_burn), summed over the chunk in step order, then added once.
 // Rate adjoint of a block of steps, on the 2-D tiles of the relaxed step:
 //   gr[v][d] += sum_t glam_t(v) pb_t(v - Delta_d),  pb = (1 - m) p_burn,
 // each thread summing four cells of the tile over the steps in registers (in
-// step order, skipping zero factors) and updating gr once.  Step t + 1's
+// step order, without branches: a zero factor adds an exact zero) and
+// updating gr once, unless all its sums are zero.  Step t + 1's
 // p_burn and mask (tile and a one-cell halo, zero outside the grid) and glam
 // (tile) are copied to shared memory while step t is summed.
 constexpr int kAccT = 256;
@@ -215,7 +214,6 @@ k_rates_accumulate(const int4* __restrict__ tiles, const int32_t* __restrict__ H
     for (int k = 0; k < kAccCPT; ++k)
 #pragma unroll
         for (int d = 0; d < 8; ++d) w[k][d] = 0.f;
-    bool any = false;
     acc_stage(st[0], y0, x0, H, W, off, 0, glam, pburn, mask);
     jwf_cp_async_commit();
     for (int t = 0; t < n_steps; ++t) {
@@ -230,20 +228,21 @@ k_rates_accumulate(const int4* __restrict__ tiles, const int32_t* __restrict__ H
             const int ly = ty + k * kAccRowStep;
             if (y0 + ly >= H || x0 + tx >= W) continue;
             const float g = b.gl[ly * kAccCols + tx];
-            if (g == 0.f) continue;
 #pragma unroll
             for (int d = 0; d < 8; ++d) {
                 const int li = (ly + 1 - jwf_dr(d)) * kAccW + (tx + 1 - jwf_dx(d));
                 float pb = b.pb[li];
                 if (mask != nullptr) pb *= 1.0f - b.m[li];
-                if (pb != 0.f) {
-                    w[k][d] += g * pb;
-                    any = true;
-                }
+                w[k][d] += g * pb;
             }
         }
         __syncthreads();
     }
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kAccCPT; ++k)
+#pragma unroll
+        for (int d = 0; d < 8; ++d) any = any || w[k][d] != 0.f;
     if (!any) return;
 #pragma unroll
     for (int k = 0; k < kAccCPT; ++k) {
