@@ -266,7 +266,6 @@ struct jwf_ctx {
 };
 
 // Device status word bits.
-#define JWF_DEVERR_INDEX 0x1u      // an index check failed (checked build)
 #define JWF_DEVERR_TMA 0x2u        // a tensor-copy wait gave up (the tile was not stepped)
 
 // ---------------------------------------------------------------------------
