@@ -175,27 +175,55 @@ struct AccStage {
     float gl[kAccRows * kAccCols];
 };
 
-__device__ __forceinline__ void acc_stage(AccStage& b, int y0, int x0, int H, int W, int64_t off, int64_t base,
+// A thread's share of a step's copies, the same every step: its elements of
+// the p_burn window (tile + one-cell halo) and of the glam tile, as offsets
+// from the tile's first cell (halo offsets are negative; kAccOut outside the
+// grid).
+constexpr int kAccPbPT = (kAccN + kAccT - 1) / kAccT;          // window elements a thread
+constexpr int32_t kAccOut = INT32_MIN;
+struct AccPlan {
+    int32_t pb[kAccPbPT];
+    int32_t gl[kAccCPT];
+};
+
+__device__ __forceinline__ void acc_plan(AccPlan& pl, int y0, int x0, int H, int W) {
+#pragma unroll
+    for (int k = 0; k < kAccPbPT; ++k) {
+        const int i = (int)threadIdx.x + k * kAccT;
+        const int y = y0 - 1 + i / kAccW, x = x0 - 1 + i % kAccW;
+        pl.pb[k] = (i < kAccN && y >= 0 && y < H && x >= 0 && x < W) ? (y - y0) * W + (x - x0) : kAccOut;
+    }
+#pragma unroll
+    for (int k = 0; k < kAccCPT; ++k) {
+        const int i = (int)threadIdx.x + k * kAccT;
+        const int y = y0 + i / kAccCols, x = x0 + i % kAccCols;
+        pl.gl[k] = (y < H && x < W) ? (y - y0) * W + (x - x0) : kAccOut;
+    }
+}
+
+// copies of one step: t0 = the global index of the tile's first cell in that step's planes
+__device__ __forceinline__ void acc_stage(AccStage& b, const AccPlan& pl, int64_t t0,
                                           const float* __restrict__ glam, const float* __restrict__ pburn,
                                           const float* __restrict__ mask) {
-    for (int i = threadIdx.x; i < kAccN; i += kAccT) {
-        const int y = y0 - 1 + i / kAccW, x = x0 - 1 + i % kAccW;
-        if (y < 0 || y >= H || x < 0 || x >= W) {
+#pragma unroll
+    for (int k = 0; k < kAccPbPT; ++k) {
+        const int i = (int)threadIdx.x + k * kAccT;
+        if (i >= kAccN) break;
+        if (pl.pb[k] == kAccOut) {
             b.pb[i] = 0.f;
             b.m[i] = 0.f;
             continue;
         }
-        const int64_t u = base + off + (int64_t)y * W + x;
+        const int64_t u = t0 + pl.pb[k];
         jwf_cp_async4(&b.pb[i], pburn + u);
         if (mask != nullptr)
             jwf_cp_async4(&b.m[i], mask + u);
         else
             b.m[i] = 0.f;
     }
-    for (int i = threadIdx.x; i < kAccRows * kAccCols; i += kAccT) {
-        const int y = y0 + i / kAccCols, x = x0 + i % kAccCols;
-        if (y < H && x < W) jwf_cp_async4(&b.gl[i], glam + base + off + (int64_t)y * W + x);
-    }
+#pragma unroll
+    for (int k = 0; k < kAccCPT; ++k)
+        if (pl.gl[k] != kAccOut) jwf_cp_async4(&b.gl[(int)threadIdx.x + k * kAccT], glam + t0 + pl.gl[k]);
 }
 
 __global__ void __launch_bounds__(kAccT)
@@ -214,11 +242,14 @@ k_rates_accumulate(const int4* __restrict__ tiles, const int32_t* __restrict__ H
     for (int k = 0; k < kAccCPT; ++k)
 #pragma unroll
         for (int d = 0; d < 8; ++d) w[k][d] = 0.f;
-    acc_stage(st[0], y0, x0, H, W, off, 0, glam, pburn, mask);
+    AccPlan pl;
+    acc_plan(pl, y0, x0, H, W);
+    const int64_t tile0 = off + (int64_t)y0 * W + x0;
+    acc_stage(st[0], pl, tile0, glam, pburn, mask);
     jwf_cp_async_commit();
     for (int t = 0; t < n_steps; ++t) {
         if (t + 1 < n_steps)
-            acc_stage(st[(t + 1) & 1], y0, x0, H, W, off, (int64_t)(t + 1) * cells, glam, pburn, mask);
+            acc_stage(st[(t + 1) & 1], pl, (int64_t)(t + 1) * cells + tile0, glam, pburn, mask);
         jwf_cp_async_commit();
         jwf_cp_async_wait_prev();
         __syncthreads();

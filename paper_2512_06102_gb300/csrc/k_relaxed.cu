@@ -462,13 +462,16 @@ struct __align__(16) SwSlot {
     float pbo[32], mo[32];      // ... and at (y + 2, outer column) for the halo lanes
 };
 
+// Issue the copies of target row y into a ring slot: v = the cell index of
+// (y, x) (only used when the cell exists), col / col_o whether this lane's
+// column and (halo lanes) its outer column lie in the grid, dxo = outer
+// column - x.
 __device__ __forceinline__ void sweep_issue(SwSlot& sl, int lane, const float* __restrict__ r,
                                             const float* __restrict__ pun, const float* __restrict__ pburn,
                                             const float* __restrict__ mask, const float* __restrict__ gun_out,
-                                            const float* __restrict__ gburn_out, int64_t off, int y, int x, int xo,
-                                            bool edge, int H, int W) {
-    if (y >= 0 && y < H && x >= 0 && x < W) {
-        const int64_t v = off + (int64_t)y * W + x;
+                                            const float* __restrict__ gburn_out, int64_t v, int y, bool col,
+                                            bool col_o, int dxo, int H, int W) {
+    if (col && (unsigned)y < (unsigned)H) {
         jwf_cp_async16(reinterpret_cast<float*>(&sl.ra[lane]), r + v * 8);
         jwf_cp_async16(reinterpret_cast<float*>(&sl.rb[lane]), r + v * 8 + 4);
         jwf_cp_async4(&sl.pu[lane], pun + v);
@@ -481,9 +484,9 @@ __device__ __forceinline__ void sweep_issue(SwSlot& sl, int lane, const float* _
         sl.au[lane] = 0.f;
         sl.ab[lane] = 0.f;
     }
-    const int y2 = y + 2;
-    if (y2 >= 0 && y2 < H && x >= 0 && x < W) {
-        const int64_t v2 = off + (int64_t)y2 * W + x;
+    const bool row2 = (unsigned)(y + 2) < (unsigned)H;
+    const int64_t v2 = v + 2 * (int64_t)W;
+    if (col && row2) {
         jwf_cp_async4(&sl.pbn[lane], pburn + v2);
         if (mask != nullptr) jwf_cp_async4(&sl.mn[lane], mask + v2);
         else sl.mn[lane] = 0.f;
@@ -491,10 +494,9 @@ __device__ __forceinline__ void sweep_issue(SwSlot& sl, int lane, const float* _
         sl.pbn[lane] = 0.f;
         sl.mn[lane] = 0.f;
     }
-    if (edge && y2 >= 0 && y2 < H && xo >= 0 && xo < W) {
-        const int64_t vo = off + (int64_t)y2 * W + xo;
-        jwf_cp_async4(&sl.pbo[lane], pburn + vo);
-        if (mask != nullptr) jwf_cp_async4(&sl.mo[lane], mask + vo);
+    if (col_o && row2) {
+        jwf_cp_async4(&sl.pbo[lane], pburn + v2 + dxo);
+        if (mask != nullptr) jwf_cp_async4(&sl.mo[lane], mask + v2 + dxo);
         else sl.mo[lane] = 0.f;
     } else {
         sl.pbo[lane] = 0.f;
@@ -543,14 +545,20 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
             oc = sweep_pb(pburn, mask, off, y0, xo, H, W).x;
         }
         const int yb = y0 - 1;                            // first target row
-        for (int k = 0; k < kSwDepth - 1; ++k)
-            sweep_issue(ring[warp][k], lane, r, pun, pburn, mask, gun_out, gburn_out, off, yb + k, x, xo, edge, H, W);
+        const bool col = x >= 0 && x < W, col_o = edge && xo >= 0 && xo < W;
+        // cell indices of (row, x), advanced a row at a time: the row being
+        // issued and the target row
+        int64_t v_is = off + (int64_t)yb * W + x;
+        int64_t v = v_is;
+        for (int k = 0; k < kSwDepth - 1; ++k, v_is += W)
+            sweep_issue(ring[warp][k], lane, r, pun, pburn, mask, gun_out, gburn_out, v_is, yb + k, col, col_o,
+                        xo - x, H, W);
         float g_prev = 0.f, g_cur = 0.f, g_next = 0.f;   // accumulators of rows y - 1, y, y + 1
         float ab_prev = 0.f, m_prev = 0.f;                // a_b and mask of row y - 1
-        for (int y = yb; y <= y1; ++y) {
+        for (int y = yb; y <= y1; ++y, v += W, v_is += W) {
             const int k = y - yb;
-            sweep_issue(ring[warp][(k + kSwDepth - 1) % kSwDepth], lane, r, pun, pburn, mask, gun_out, gburn_out, off,
-                        y + kSwDepth - 1, x, xo, edge, H, W);
+            sweep_issue(ring[warp][(k + kSwDepth - 1) % kSwDepth], lane, r, pun, pburn, mask, gun_out, gburn_out,
+                        v_is, y + kSwDepth - 1, col, col_o, xo - x, H, W);
             cp_async_wait_n<kSwDepth - 1>();
             const SwSlot& sl = ring[warp][k % kSwDepth];
             struct {
@@ -582,7 +590,7 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
             float lam = 0.f;
 #pragma unroll
             for (int d = 0; d < 8; ++d) lam += src[d] * rv[d];
-            const bool valid = y >= 0 && y < H && x >= 0 && x < W;
+            const bool valid = col && (unsigned)y < (unsigned)H;
             float g = 0.f;
             if (valid) {
                 const float em = expf(-lam);
@@ -591,7 +599,6 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
                 const float pe = cur.pu * em;
                 g = pe != 0.f ? sat(nb * pe) : 0.f;
                 if (out_col && y >= y0 && y < y1) {
-                    const int64_t v = off + (int64_t)y * W + x;
                     gun[v] = sat(p_ign != 0.f ? cur.au + nb * p_ign : cur.au);
                     glam[v] = g;
                     if (pb.x != 0.f) accf += cur.ab * pb.x;
@@ -622,7 +629,7 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
                     const float keep = 1.0f - m_prev;
                     gb = keep != 0.f ? gb * keep : 0.f;
                 }
-                gburn[off + (int64_t)(y - 1) * W + x] = sat(gb);
+                gburn[v - W] = sat(gb);
             }
             g_prev = g_cur;
             g_cur = g_next;
