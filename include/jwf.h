@@ -320,8 +320,9 @@ JWF_API int32_t jwf_tile_copy(const jwf_ctx* ctx);
  * first `steps` steps in the queue order, then the rest with each size
  * class's envs reordered by their burning-cell count after the first part,
  * largest first (the envs with the longest fires then start first instead
- * of last).  Default 0 (never split).  Results do not depend on it; it
- * is not applied while recording a history.  Errors: JWF_EINVAL (< 0). */
+ * of last).  Default 12; 0 never splits.  Applied to batches of one size
+ * class (see jwf_size_classes) and not while recording a history.  Results
+ * do not depend on it.  Errors: JWF_EINVAL (< 0). */
 JWF_API jwf_status jwf_set_reorder_steps(jwf_ctx* ctx, int32_t steps);
 
 /* Scheduling hint for the resident kernels: within each size class, envs are

@@ -182,7 +182,7 @@ struct jwf_ctx {
     int32_t* d_order = nullptr;          // env processing order, largest first
     int32_t* d_order_dyn = nullptr;      // [N] order of the second part of a split resident launch
     int32_t* d_lastb = nullptr;          // [N] burning cells after the first part
-    int32_t reorder_steps = 0;           // split resident launches after this many steps (0: never)
+    int32_t reorder_steps = 12;          // split resident launches after this many steps (0: never)
     int2* d_tiles = nullptr;             // (env, first local cell) per JWF_TILE block
     int64_t n_tiles = 0;
     uint8_t* d_state[2] = {nullptr, nullptr};

@@ -1671,7 +1671,9 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
                                      int32_t* burnt, uint8_t* done, cudaStream_t s) {
     const int32_t k1 = c->reorder_steps;
     const int ng = (int)c->groups.size();
-    if (k1 <= 0 || k < 2 * k1 || c->hist != nullptr || c->d_lastb == nullptr || ng > 4)
+    // (one size class only: with several, the classes run on forked streams
+    // and the reorder would join them between the two parts)
+    if (k1 <= 0 || k < 2 * k1 || c->hist != nullptr || c->d_lastb == nullptr || ng != 1)
         return launch_resident_part(c, k, drops, burning, burnt, done, c->d_order, nullptr, s);
     // two launches: k1 steps in the creation order, then the rest with the
     // envs whose fires are largest after k1 steps first (the longest fires
