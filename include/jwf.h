@@ -316,6 +316,13 @@ JWF_API jwf_status jwf_set_round_steps(jwf_ctx* ctx, int32_t steps);
 JWF_API jwf_status jwf_set_tile_copy(jwf_ctx* ctx, int32_t tma);
 JWF_API int32_t jwf_tile_copy(const jwf_ctx* ctx);
 
+/* Bound of the tiled kernels' wait for a tensor copy (default 2 s; 1 ns ..
+ * 10 s).  A wait that runs out sets a bit of the device status word (the
+ * tile is left unstepped) and jwf_sync returns JWF_ETIMEOUT.  With no_copy
+ * != 0 (diagnostics only) the kernels arm the wait but issue no copy, so
+ * every wait runs out: this exercises the timeout path without a fault. */
+JWF_API jwf_status jwf_set_tile_copy_wait(jwf_ctx* ctx, uint64_t timeout_ns, int32_t no_copy);
+
 /* Split a resident jwf_step of k >= 2 * steps steps into two launches: the
  * first `steps` steps in the queue order, then the rest with each size
  * class's envs reordered by their burning-cell count after the first part,

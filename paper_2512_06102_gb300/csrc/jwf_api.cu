@@ -701,6 +701,15 @@ jwf_status jwf_set_tile_copy(jwf_ctx* ctx, int32_t tma) {
     return JWF_OK;
 }
 
+jwf_status jwf_set_tile_copy_wait(jwf_ctx* ctx, uint64_t timeout_ns, int32_t no_copy) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (timeout_ns == 0 || timeout_ns > 10000000000ull)
+        return fail(ctx, JWF_EINVAL, "jwf_set_tile_copy_wait: timeout must be 1 ns .. 10 s");
+    ctx->tma_wait_ns = timeout_ns;
+    ctx->tma_diag_no_copy = no_copy != 0;
+    return JWF_OK;
+}
+
 int32_t jwf_tile_copy(const jwf_ctx* ctx) { return ctx != nullptr && ctx->tma && ctx->use_tma ? 1 : 0; }
 
 jwf_status jwf_set_round_steps(jwf_ctx* ctx, int32_t steps) {

@@ -233,6 +233,8 @@ struct jwf_ctx {
     uint8_t* d_tma_ok = nullptr;
     bool tma = false;
     bool use_tma = true;                 // jwf_set_tile_copy: TMA (default) or plain loads
+    uint64_t tma_wait_ns = 2000000000ull;   // a tensor copy that takes 2 s has failed
+    bool tma_diag_no_copy = false;       // diagnostics (jwf_set_tile_copy_wait): the waits run out
     int32_t* d_tburnt = nullptr;
     int32_t* d_tcnt = nullptr;
     bool tiles_valid = false;

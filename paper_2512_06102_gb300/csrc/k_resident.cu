@@ -773,6 +773,8 @@ struct TileArgs {
     const JwfTmap* tm_out_tile;
     const uint8_t* tma_ok;
     uint32_t* status;
+    uint64_t wait_ns;            // bound of a tensor-copy wait
+    int32_t diag_no_copy;        // diagnostics: arm the barrier but issue no copy (the wait runs out)
     int32_t kb;
     int32_t R;
     uint32_t key0, key1;
@@ -782,7 +784,6 @@ struct TileArgs {
 // TMA boxes: the region (tile plus kMaxRound rows and one 32-cell word of
 // columns on each side) and the tile itself, one byte a cell
 constexpr int kBoxCols = kTileCols + 64, kBoxRows = kRegionRows;
-constexpr uint64_t kTmaWaitNs = 2000000000ull;    // a tensor copy that takes 2 s has failed
 
 // the staged region fits where it is put (ignition, burn-out and queue arrays,
 // from a 128-byte boundary)
@@ -893,14 +894,14 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
                     uint8_t* stg = reinterpret_cast<uint8_t*>(sm) + ((128u - (jwf_smem_u32(sm) & 127u)) & 127u);
                     jwf_mbar_init(&s_bar, 1);
                     jwf_mbar_expect_tx(&s_bar, kTileRows * kTileCols);
-                    jwf_tma_load_2d(stg, a.tm_in_tile + e, tx0, ty0, &s_bar);
-                    if (jwf_mbar_wait_bounded(&s_bar, 0, kTmaWaitNs)) {
+                    if (!a.diag_no_copy) jwf_tma_load_2d(stg, a.tm_in_tile + e, tx0, ty0, &s_bar);
+                    if (jwf_mbar_wait_bounded(&s_bar, 0, a.wait_ns)) {
                         jwf_tma_store_2d(a.tm_out_tile + e, tx0, ty0, stg);
                         jwf_bulk_commit();
                         jwf_bulk_wait_all();
                     } else {
                         atomicOr(a.status, JWF_DEVERR_TMA);
-                        jwf_mbar_wait_bounded(&s_bar, 0, kTmaWaitNs);     // a late copy lands before the exit
+                        jwf_mbar_wait_bounded(&s_bar, 0, a.wait_ns);      // a late copy lands before the exit
                         copied = false;
                     }
                 }
@@ -953,7 +954,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         // x is a multiple of 32 cells; rows and columns outside the grid read as 0
         jwf_mbar_init(&s_bar, 1);
         jwf_mbar_expect_tx(&s_bar, kBoxRows * kBoxCols);
-        jwf_tma_load_2d(stg, a.tm_region + e, tx0 - 32, ty0 - kb, &s_bar);
+        if (!a.diag_no_copy) jwf_tma_load_2d(stg, a.tm_region + e, tx0 - 32, ty0 - kb, &s_bar);
     }
     for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
     if (threadIdx.x < 3) s_qn[threadIdx.x] = 0;
@@ -965,13 +966,13 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     if (threadIdx.x < 3) s_chunk[threadIdx.x] = 0;
     ignw[lane] = 0u;
     outw[lane] = 0u;
-    if (use_tma && threadIdx.x == 0) s_tma = jwf_mbar_wait_bounded(&s_bar, 0, kTmaWaitNs) ? 1 : 0;
+    if (use_tma && threadIdx.x == 0) s_tma = jwf_mbar_wait_bounded(&s_bar, 0, a.wait_ns) ? 1 : 0;
     __syncthreads();
     if (use_tma && !s_tma) {
         // the copy did not complete: report, let a late copy land, leave the tile
         if (threadIdx.x == 0) {
             atomicOr(a.status, JWF_DEVERR_TMA);
-            jwf_mbar_wait_bounded(&s_bar, 0, kTmaWaitNs);
+            jwf_mbar_wait_bounded(&s_bar, 0, a.wait_ns);
         }
         return;
     }
@@ -1517,6 +1518,8 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         a.tm_out_tile = c->tma && c->use_tma ? c->d_tmaps + (size_t)(2 * bo + 1) * c->N : nullptr;
         a.tma_ok = c->tma && c->use_tma ? c->d_tma_ok : nullptr;
         a.status = c->d_status;
+        a.wait_ns = c->tma_wait_ns;
+        a.diag_no_copy = c->tma_diag_no_copy ? 1 : 0;
         a.kb = kb;
         a.R = c->drop_radius;
         a.key0 = (uint32_t)(c->seed & 0xffffffffu);

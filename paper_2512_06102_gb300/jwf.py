@@ -91,6 +91,7 @@ _SIGS = {
     "jwf_set_tile_copy": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "jwf_set_reorder_steps": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "jwf_tile_copy": (ctypes.c_int32, [_VP]),
+    "jwf_set_tile_copy_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_int32]),
     "jwf_get_state": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "jwf_step_relaxed_fwd": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_step_relaxed_bwd": (ctypes.c_int, [_VP] * 11),
@@ -367,6 +368,12 @@ class Sim:
     def set_tile_copy(self, tma: bool = True):
         """Tiled kernels: stage regions with TMA tensor copies (True) or loads."""
         self._check(lib().jwf_set_tile_copy(self._h, int(bool(tma))), "jwf_set_tile_copy")
+
+    def set_tile_copy_wait(self, timeout_ns: int = 2_000_000_000, no_copy: bool = False):
+        """Bound of the tiled kernels' tensor-copy wait; no_copy (diagnostics)
+        arms the wait without a copy so that it runs out."""
+        self._check(lib().jwf_set_tile_copy_wait(self._h, ctypes.c_uint64(int(timeout_ns)), int(bool(no_copy))),
+                    "jwf_set_tile_copy_wait")
 
     def tile_copy(self) -> bool:
         return bool(lib().jwf_tile_copy(self._h))

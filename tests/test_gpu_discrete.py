@@ -417,3 +417,37 @@ def test_tiled_large_grids_sampled():
     np.testing.assert_array_equal(out[0].cpu().numpy()[:, e:e + 1], ob)
     np.testing.assert_array_equal(out[1].cpu().numpy()[:, e:e + 1], od)
     sim.close()
+
+
+def test_tiled_copy_wait_runs_out_and_context_recovers():
+    """The tiled kernels' wait for a tensor copy is bounded: with the
+    diagnostic that arms the wait but issues no copy, every wait runs out
+    after 1 ms, the kernel leaves its tile and sets the status word, and
+    jwf_sync reports JWF_ETIMEOUT (no fault, no hang).  Afterwards the same
+    context, reloaded, steps exactly like the oracle."""
+    require_gpu()
+    scn = scenarios.make_scenario(128, 256, N=1, seed=34)
+    _fires_on_tile_corners(scn)
+    q32 = oracle_tables(scn)[0]
+    sim = make_sim(scn, seed=4)
+    sim.set_kernel(jwf.KERNEL_TILED)
+    sim.set_probs(to(q32))
+    assert sim.tile_copy()
+    sim.load_state(to(scn.F0))
+    sim.set_tile_copy_wait(1_000_000, no_copy=True)
+    sim.step(3)
+    with pytest.raises(jwf.JwfError) as err:
+        sim.sync()
+    assert err.value.status == 4          # JWF_ETIMEOUT
+    sim.set_tile_copy_wait()              # 2 s, copies issued
+    sim.sync()                            # the status word was cleared by the report
+    k = 20
+    sim.load_state(to(scn.F0))
+    out = sim.step(k)
+    torch.cuda.synchronize()
+    sim.sync()
+    ro = discrete.Rollout(scn.H, scn.W, scn.F0, q32, scn.params.p_continue, seed=4)
+    ob, od, odone = ro.step(k)
+    np.testing.assert_array_equal(sim.state().cpu().numpy(), ro.F)
+    np.testing.assert_array_equal(out[0].cpu().numpy(), ob)
+    sim.close()
