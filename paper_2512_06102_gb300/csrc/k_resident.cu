@@ -5,15 +5,18 @@
 // each env in shared memory as bit planes, 32 cells per word: burning B
 // (double-buffered, one zero row above and below), can-burn C and burned D.
 // One step has three phases separated by barriers:
-//   A. warps claim 32-word chunks from a per-step counter, skip chunks that
-//      cannot change, and for the others find, one word a lane, the can-burn
-//      cells with a burning neighbour and the burning cells (eight shifted ORs
-//      of the burning plane); the work items (remain-burning draws, compared
-//      (target, source) pairs) go to a block-wide queue in shared memory;
+//   A. the 32-word chunks that can change are found by one ballot per 32
+//      chunks and dealt to the warps by rank; for each, a warp finds, one
+//      word a lane, the can-burn cells with a burning neighbour and the
+//      burning cells (eight shifted ORs of the burning plane); the work items
+//      (remain-burning draws, compared (target, source) pairs) go to a
+//      block-wide queue in shared memory;
 //   B. all threads of the CTA evaluate the queued items (Philox draws, the
 //      ignition probability) and set ignition and burn-out bits;
-//   C. the claimed chunks are written back (new burning plane, the next
+//   C. the dealt chunks are written back (new burning plane, the next
 //      step's tanker drop, counts).
+// A launch may be split after a few steps (k_reorder between the parts) so
+// that the envs with the largest fires start the rest first.
 // For grids larger than shared memory, k_step_tiled (k_tiled.cu) steps tiles
 // with a halo (temporal blocking).
 // The ignition probability of a compared (target, source) pair is read from
@@ -244,9 +247,8 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
     extern __shared__ uint32_t sm[];
     __shared__ int32_t s_env;
     __shared__ int32_t s_cnt[3][3];     // burning, new burn-outs, doused (per step)
-    __shared__ int32_t s_chunk[3];
     __shared__ int32_t s_qn[3];         // queued work items (per step)
-    __shared__ int32_t s_ncl[3];        // chunks claimed (per step)
+    __shared__ int32_t s_ncl[3];        // chunks that can change (per step)
     __shared__ int32_t s_burnt;
     __shared__ int32_t s_dous;          // cells doused by a drop applied at a step's start
     // the rate constants live in shared memory only in the fused variant
@@ -284,7 +286,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         // chunk activity flags of the two burning buffers
         uint8_t* flag0 = reinterpret_cast<uint8_t*>(D + words + (NT / 32) * kWarpScratch);
         uint8_t* flag1 = flag0 + nchunks;
-        // chunks claimed this step and the block-wide queue of work items
+        // chunks dealt this step and the block-wide queue of work items
         int* clist = reinterpret_cast<int*>(flag0 + 2 * ((nchunks + 3) & ~3));
         uint32_t* Q = reinterpret_cast<uint32_t*>(clist + nchunks);
         const int reach = (WW + 1 + 31) >> 5;                 // chunks a word's neighbours span
@@ -296,7 +298,6 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
         if (threadIdx.x < 9) s_cnt[threadIdx.x / 3][threadIdx.x % 3] = 0;
         if (threadIdx.x < 3) {
-            s_chunk[threadIdx.x] = 0;
             s_qn[threadIdx.x] = 0;
             s_ncl[threadIdx.x] = 0;
         }
@@ -343,7 +344,6 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 s_cnt[(s + 1) % 3][0] = 0;
                 s_cnt[(s + 1) % 3][1] = 0;
                 s_cnt[(s + 1) % 3][2] = 0;
-                s_chunk[(s + 1) % 3] = 0;
                 s_qn[(s + 1) % 3] = 0;
                 s_ncl[(s + 1) % 3] = 0;
             }
@@ -540,7 +540,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 }
             }
             __syncthreads();
-            // phase C: the claimed chunks are written back, dealt to the warps
+            // phase C: the dealt chunks are written back, round-robin over the warps
             {
                 const int ncl = s_ncl[s % 3];
                 for (int k = warp; k < ncl; k += NT / 32) {
@@ -724,7 +724,7 @@ size_t jwf_resident_smem(int32_t H, int32_t W, int threads) {
     // queued work items address words with 14 bits
     if ((int64_t)H * ((W + 31) / 32) >= (int64_t)1 << 14) return (size_t)1 << 40;
     const int64_t nchunks = ((int64_t)H * ((W + 31) / 32) + 31) / 32;
-    // two chunk-flag byte arrays, the claimed-chunk list and the work queue
+    // two chunk-flag byte arrays, the dealt-chunk list and the work queue
     const int64_t flag_words = 2 * ((nchunks + 3) / 4) + nchunks + kResQCap;
     return (size_t)(res_plane_words(H, W) + nwarps * kWarpScratch + flag_words) * sizeof(uint32_t);
 }

@@ -85,7 +85,7 @@ static_assert((2 * kRegionWordsAll + kQCap) * 4 >= kBoxRows * kBoxCols + 128, "r
 
 size_t tiled_smem_bytes(int threads) {
     // planes, warp scratch, chunk flags, ignition and burn-out planes, queue,
-    // per-warp claimed-chunk lists
+    // per-warp lists of dealt chunks
     return (size_t)(2 * (kRegionRows + 2) * kRegionWords + 2 * kRegionWordsAll + (threads / 32) * kWarpScratch +
                     2 * kTileFlagBytes / 4 + 2 * kRegionWordsAll + kQCap + (threads / 32) * kRegionChunks) *
            sizeof(uint32_t);
@@ -144,7 +144,6 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     // per step: interior burning, interior burn-outs, interior cells doused by
     // the next step's drop, region burning
     __shared__ int32_t s_cnt[3][4];
-    __shared__ int32_t s_chunk[3];
     __shared__ int32_t s_d0;
     __shared__ uint32_t s_act;
     __shared__ int32_t s_qn[3];
@@ -238,7 +237,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     uint32_t* IG = reinterpret_cast<uint32_t*>(fl_c + 2 * kTileFlagBytes);   // ignitions this step
     uint32_t* OU = IG + kRegionWordsAll;                                      // burn-outs this step
     uint32_t* Q = OU + kRegionWordsAll;
-    int* wch = reinterpret_cast<int*>(Q + kQCap) + warp * kRegionChunks;     // chunks this warp claimed
+    int* wch = reinterpret_cast<int*>(Q + kQCap) + warp * kRegionChunks;     // chunks dealt to this warp
     const int reach = (WW + 1 + 31) >> 5;
     // the region's bytes are staged where the ignition, burn-out and queue
     // arrays go (they are not used before the steps start)
@@ -257,7 +256,6 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         s_d0 = 0;
         s_act = 0u;
     }
-    if (threadIdx.x < 3) s_chunk[threadIdx.x] = 0;
     ignw[lane] = 0u;
     outw[lane] = 0u;
     if (use_tma && threadIdx.x == 0) s_tma = jwf_mbar_wait_bounded(&s_bar, 0, a.wait_ns) ? 1 : 0;
@@ -352,7 +350,6 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             s_cnt[(s + 1) % 3][1] = 0;
             s_cnt[(s + 1) % 3][2] = 0;
             s_cnt[(s + 1) % 3][3] = 0;
-            s_chunk[(s + 1) % 3] = 0;
             s_qn[(s + 1) % 3] = 0;
         }
         bool hasn = false;
@@ -366,7 +363,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         }
         int my_b = 0, my_o = 0, my_x = 0, my_r = 0;
         uint32_t my_pairs = 0, my_blocks = 0, my_burn = 0, my_chunks = 0;
-        // phase A: warps claim the chunks that can change and queue their work
+        // phase A: the chunks that can change are dealt to the warps, which queue their work
         // items (one per burning cell; one per compared pair in the fused
         // variant, one per candidate cell in the table variant)
         // (a chunk with no burning cell within reach, whose write buffer holds
@@ -542,7 +539,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             }
         }
         __syncthreads();
-        // phase C: each warp writes back the chunks it claimed
+        // phase C: each warp writes back the chunks dealt to it
         for (int k = 0; k < (int)my_chunks; ++k) {
             const int c = wch[k];
             const int i = (c << 5) + lane;
