@@ -23,9 +23,10 @@
  *    h_* are host pointers.  Every call is asynchronous on the given
  *    cudaStream_t (passed as void*; NULL = the legacy default stream) and
  *    returns once the work is enqueued.  Argument errors are reported
- *    immediately and leave the context unchanged.  Errors raised inside a
- *    kernel (a bounded wait that ran out, an index check in a checked build)
- *    are written to a device status word and reported by jwf_sync().
+ *    immediately and leave the context unchanged.  An error raised inside a
+ *    kernel (a bounded wait that ran out: the tiled step's wait for its
+ *    tensor copy) is written to a device status word and reported by
+ *    jwf_sync().
  *  - No call aborts, throws or traps; every failure is a jwf_status.
  *  - One context must be used from one stream at a time (calls on one
  *    context that overlap on the GPU race).
