@@ -61,9 +61,12 @@ def signature(sim: jwf.Sim, kernel: int, probe_steps: int) -> str:
     return f"{dev}|k{kernel}|p{probe_steps}|{h.hexdigest()[:20]}"
 
 
-def _time(fn, reps: int = 2) -> float:
+def _time(fn, reps: int = 2, prep=None) -> float:
+    """Best device time of fn() over reps; prep() (untimed) runs before each."""
     best = float("inf")
     for _ in range(reps):
+        if prep is not None:
+            prep()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
@@ -96,12 +99,22 @@ def tune(sim: jwf.Sim, F0: torch.Tensor, drops: torch.Tensor | None = None, kern
         choice = {"class_threads": {}, "round_steps": 16, "tile_threads": 0}
         tiled = kernel in (jwf.KERNEL_TILED, jwf.KERNEL_TILED_FUSED)
         if tiled:
+            # the first rounds are dominated by the one-time copies of the
+            # tiles without fire; time the probe after probe_steps untimed
+            # steps (same drops), when only the fire fronts work
+            def warm():
+                sim.load_state(F0)
+                sim.step(probe_steps, dr)
+
+            def late():
+                sim.step(probe_steps, dr)
+
             best = None
             for th in TILE_THREADS:
                 sim.set_kernel(kernel, th)
                 for rs in ROUND_STEPS:
                     sim.set_round_steps(rs)
-                    t = _time(probe)
+                    t = _time(late, prep=warm)
                     if best is None or t < best[0]:
                         best = (t, rs, th)
             choice["round_steps"] = best[1]
