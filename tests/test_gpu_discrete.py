@@ -451,3 +451,49 @@ def test_tiled_copy_wait_runs_out_and_context_recovers():
     np.testing.assert_array_equal(sim.state().cpu().numpy(), ro.F)
     np.testing.assert_array_equal(out[0].cpu().numpy(), ob)
     sim.close()
+
+
+@pytest.mark.parametrize("kernel", [jwf.KERNEL_RESIDENT, jwf.KERNEL_FUSED])
+def test_resident_maximum_size(kernel):
+    """The largest grids the resident kernels hold in shared memory (longer
+    side 512, the top size class; 512 x 500 leaves a partial word in every
+    row) next to a small one, with drops, against the oracle bit for bit."""
+    require_gpu()
+    H = [512, 512, 33]
+    W = [512, 500, 512]
+    scn = scenarios.make_scenario(H, W, seed=35)
+    _fires_on_tile_corners(scn)
+    q32 = oracle_tables(scn)[0]
+    k = 30
+    drops = _fire_drops(scn, k, 35)
+    sim = make_sim(scn, seed=6)
+    sim.set_kernel(kernel)
+    if kernel == jwf.KERNEL_FUSED:
+        sim.set_terrain(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+        fused = sim
+        # the fused rates equal the oracle's table only to 1e-6: compare with the table path instead
+        ref = make_sim(scn, seed=6)
+        ref.set_kernel(jwf.KERNEL_RESIDENT)
+        ref.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+        outs = []
+        for s in (fused, ref):
+            s.load_state(to(scn.F0))
+            o = [x.cpu().numpy() for x in s.step(k, to(drops))]
+            outs.append((s.state().cpu().numpy(), o))
+            s.close()
+        np.testing.assert_array_equal(outs[0][0], outs[1][0])
+        for a, b in zip(outs[0][1], outs[1][1]):
+            np.testing.assert_array_equal(a, b)
+        return
+    sim.set_probs(to(q32))
+    assert sim.size_classes() == [3]
+    sim.load_state(to(scn.F0))
+    out = [x.cpu().numpy() for x in sim.step(k, to(drops))]
+    st = sim.state().cpu().numpy()
+    sim.close()
+    ro = discrete.Rollout(scn.H, scn.W, scn.F0, q32, scn.params.p_continue, seed=6)
+    ob, od, odone = ro.step(k, np.ascontiguousarray(drops))
+    np.testing.assert_array_equal(st, ro.F)
+    np.testing.assert_array_equal(out[0], ob)
+    np.testing.assert_array_equal(out[1], od)
+    np.testing.assert_array_equal(out[2], odone)
