@@ -52,3 +52,17 @@ def test_host_side_errors_without_gpu(libjwf):
     assert h.value is None
     assert libjwf.jwf_destroy(None) == 0
     assert libjwf.jwf_step(None, 1, None, None, None, None, None) == 1
+    # context-free calls: 2-bit packing sizes and argument checks
+    assert libjwf.jwf_packed_size(0) == 0
+    assert libjwf.jwf_packed_size(1) == 16            # ceil(1 / 4) rounded up to 16 bytes
+    assert libjwf.jwf_packed_size(64) == 16
+    assert libjwf.jwf_packed_size(65) == 32
+    assert libjwf.jwf_packed_size(-1) == -1
+    assert libjwf.jwf_pack_states(-1, None, None, None) == 1
+    assert libjwf.jwf_pack_states(5, None, None, None) == 1
+    assert libjwf.jwf_unpack_states(5, None, None, None) == 1
+    # every context call rejects a null context
+    for name, args in [("jwf_set_reorder_steps", (None, 8)), ("jwf_set_tile_copy", (None, 1)),
+                       ("jwf_set_tile_copy_wait", (None, 1000, 0)), ("jwf_set_env_priority", (None, None)),
+                       ("jwf_load_state_packed", (None, None, None)), ("jwf_get_state_packed", (None, None, None))]:
+        assert getattr(libjwf, name)(*args) == 1, name
