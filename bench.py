@@ -193,9 +193,12 @@ def run_ours(args):
     rank, world = D.rank, D.world
     torch.cuda.set_device(D.local)
     dev = torch.device("cuda", D.local)
-    if rank == 0 or not build.up_to_date():
+    # one build per node (local rank 0); the other ranks wait for it
+    if D.local == 0:
         build.build()
     D.barrier()
+    if not build.up_to_date():
+        raise RuntimeError("libjwf is missing or older than its sources after the local build")
 
     scn = scenarios.make_scenario(SIDE, SIDE, N=N_ENVS, seed=rank)
     drops = scenarios.drops(EPISODE, scn.H, scn.W, seed=rank)

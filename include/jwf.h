@@ -506,10 +506,12 @@ JWF_API jwf_status jwf_rates_contract(jwf_ctx* ctx, const float* d_gr, const uin
  * for JWF_NOALLOC_MAX_CELLS cells, plus reduction partial sums) that every
  * GPU loading the library holds until the process exits.  Errors: JWF_EINVAL
  * when n_envs * H * W exceeds JWF_NOALLOC_MAX_CELLS, for null pointers,
- * p_continue outside [0, 1] or outputs that alias inputs; JWF_ECUDA when the
- * device or a launch fails.  The first call on each device looks up the
- * array's device address with that device current: make that first call
- * before any stream capture.  All calls share the array, which keeps the
+ * p_continue outside [0, 1], or an output buffer (d_gun, d_gburn, d_gpc)
+ * that shares a byte with an input or with another output (sizes as above);
+ * JWF_ECUDA when the device or a launch fails.  Every call looks up the
+ * array's device address on the current device; the first lookup on a device
+ * loads the library's device code there, so make the first call on each
+ * device before any stream capture.  All calls share the array, which keeps the
  * last call's contents: calls that overlap on the GPU (on different streams
  * or from different host threads) race, so the caller must serialise them. */
 JWF_API jwf_status jwf_step_relaxed_bwd_noalloc(int32_t n_envs, int32_t H, int32_t W,

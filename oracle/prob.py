@@ -7,7 +7,7 @@ Written from arXiv 2512.06102, Section 3 ("Directional propagation" and
 "Ignition probability"), Eqs. 1-4, in plain PyTorch float64 so that autograd
 can differentiate the rates with respect to the parameters.
 
-Conventions (the paper leaves them open; readings listed in the design doc):
+Conventions (where the paper leaves them open):
   * direction d = 0..7 has angle d*pi/4 (east = 0, counter-clockwise, Eq. 1);
     Delta_d = (dx, dy) with dy positive northward; rows grow southward, so the
     row offset of Delta_d is -dy;

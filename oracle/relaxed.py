@@ -8,7 +8,7 @@ update", Eqs. 5-10, with p_ignite from Eq. 4.  Plain PyTorch float64 ops, so
 that autograd supplies the reference gradient of a rollout (the gradient is
 the derivative of this forward; the tests pin it with central differences).
 
-Readings (the paper is silent; listed in the design doc):
+Readings (where the paper is silent):
   * In Eq. 4 the burning indicator b(u) is replaced by p_burn(u), so
     p_ignite(v) = 1 - exp(-sum_d p_burn(v - Delta_d) * r(v, d)).
   * The burned-out probability is implicit: p_bd = 1 - p_un - p_burn.

@@ -48,7 +48,9 @@ def up_to_date() -> bool:
 
 
 def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+    # objects carry the process id: two processes building at once never
+    # write the same file (the final rename of the library is atomic)
+    obj = os.path.join(OUT, f"{os.path.basename(src)[:-3]}.{os.getpid()}.o")
     cmd = [nvcc(), *ARCH, *NVFLAGS, "-I", INCLUDE, "-c", src, "-o", obj]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
@@ -74,6 +76,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    for o in objs:
+        os.remove(o)
     return LIB
 
 

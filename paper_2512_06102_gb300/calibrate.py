@@ -5,9 +5,10 @@ Targets are burn maps: the fraction of seeded runs of the stochastic step
 steps.  The fit runs the relaxed rollout (Eqs. 5-10) from the same initial
 fires, takes the Section 4 loss (BCE on the spread shape + MSE after average
 pooling) and updates the free parameters with Adam, as the paper does with
-its raw-probabilities routine.  Under torch.distributed each rank fits its
-own shard of the grids and the gradients are summed over ranks before the
-update, so every rank takes the same step.
+its raw-probabilities routine.  Under torch.distributed each rank holds a
+shard of the grids and evaluates its share of the whole batch's loss; the
+shares' gradients (and values) are summed over ranks before the update, so
+every rank takes the same step as a single process holding the whole batch.
 
 theta layout (float64): [p_base, alpha_w1, alpha_w2, alpha_s, alpha_gamma,
 p_continue, mu_veg[C], mu_den[C]].  By default p_base, the two wind
@@ -57,40 +58,58 @@ def burn_maps(H: int, W: int, n_envs: int, params, scene, F0: torch.Tensor, T: i
     return acc / float(len(seeds))
 
 
-def fit(sim: jwf.Sim, scene, F0: torch.Tensor, target: torch.Tensor, theta0: torch.Tensor, T: int,
+def sharded_loss_grad(z: torch.Tensor, local_loss: torch.Tensor | None, free: torch.Tensor) -> float:
+    """Backward of this rank's share of the whole-batch loss (None when the
+    rank holds no grids), restricted to the free parameters and summed over
+    ranks into z.grad; returns the whole batch's loss."""
+    if local_loss is not None:
+        local_loss.backward()
+        lv = local_loss.detach().to(torch.float64)
+    else:
+        lv = torch.zeros((), dtype=torch.float64)
+    if z.grad is None:
+        z.grad = torch.zeros_like(z)
+    g = z.grad.detach()
+    g.mul_(free.to(g.device))
+    return shard.reduce_loss_and_grad_(g, lv.to(g.device))
+
+
+def fit(sim: jwf.Sim | None, scene, F0: torch.Tensor, target: torch.Tensor, theta0: torch.Tensor, T: int,
         iters: int = 100, lr: float = 0.05, free: torch.Tensor | None = None, pool: int = 4,
         ckpt_every=None, callback=None):
     """Adam on the free parameters of theta, in steps relative to each
-    parameter's size; returns (theta, [loss per iteration]).  sim must have
-    been created with keep_rates=True and hold a uniform batch (the pooled
-    loss reshapes to [N, H, W])."""
-    H, W = int(sim.H[0]), int(sim.W[0])
-    if not (np.all(sim.H == H) and np.all(sim.W == W)):
-        raise ValueError("calibration needs a uniform batch")
-    free = default_free(sim.n_classes) if free is None else free
+    parameter's size; returns (theta, [whole-batch loss per iteration]).  sim
+    must have been created with keep_rates=True and hold a uniform batch (the
+    pooled loss reshapes to [N, H, W]).  Under torch.distributed every rank
+    calls fit with its own shard; a rank whose shard is empty passes
+    sim=None (scene, F0 and target are then ignored) and still takes part in
+    every reduction."""
     theta0 = theta0.detach().to(torch.float64)
+    n_classes = (theta0.numel() - 6) // 2
+    if sim is not None:
+        H, W = int(sim.H[0]), int(sim.W[0])
+        if not (np.all(sim.H == H) and np.all(sim.W == W)):
+            raise ValueError("calibration needs a uniform batch")
+        pb0 = (F0 == 2).to(torch.float32)
+        pu0 = 1.0 - pb0
+        cell_size = sim.params.cell_size if sim.params is not None else 30.0
+    n_total = shard.global_count(0 if sim is None else sim.N)
+    free = default_free(n_classes) if free is None else free
     # Adam steps in units of each parameter's own size (the coefficients span
     # two orders of magnitude): theta = theta0 + scale * z
     scale = theta0.abs().clamp_min(0.05)
     z = torch.zeros_like(theta0, requires_grad=True)
     opt = torch.optim.Adam([z], lr=lr)
-    pb0 = (F0 == 2).to(torch.float32)
-    pu0 = 1.0 - pb0
-    cell_size = sim.params.cell_size if sim.params is not None else 30.0
     losses = []
     for it in range(iters):
         opt.zero_grad()
         theta = theta0 + scale * z
-        ou, _ = relaxed.rollout(theta, pu0, pb0, sim, scene, T, ckpt_every=ckpt_every, cell_size=cell_size)
-        loss = relaxed.calibration_loss(ou, target, H, W, pool=pool)
-        loss.backward()
-        g = z.grad.detach()
-        g.mul_(free.to(g.device))
-        shard.allreduce_sum_(g)
-        lv = loss.detach().double().reshape(1)
-        shard.allreduce_sum_(lv)
+        loss = None
+        if sim is not None:
+            ou, _ = relaxed.rollout(theta, pu0, pb0, sim, scene, T, ckpt_every=ckpt_every, cell_size=cell_size)
+            loss = relaxed.calibration_loss(ou, target, H, W, pool=pool, n_total=n_total)
+        losses.append(sharded_loss_grad(z, loss, free))
         opt.step()
-        losses.append(float(lv.item()))
         if callback is not None:
             callback(it, (theta0 + scale * z).detach(), losses[-1])
     return (theta0 + scale * z).detach(), losses

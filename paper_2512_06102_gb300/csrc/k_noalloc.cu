@@ -9,8 +9,6 @@
 // in one file-scope device array, g_noalloc_scratch, sized for at most
 // JWF_NOALLOC_MAX_CELLS cells.  Every GPU that loads the library holds that
 // array (about 16 MiB) until the process exits.
-#include <mutex>
-
 #include "jwf_internal.cuh"
 
 namespace {
@@ -124,25 +122,22 @@ k_na_bwd_b(int64_t cells, int H, int W, const float* __restrict__ r, const float
     }
 }
 
-// Device address of the scratch array, resolved once per device.
-constexpr int kMaxDevices = 64;
-std::mutex g_na_mutex;
-unsigned char* g_na_ptr[kMaxDevices] = {};
-
+// Device address of the scratch array on the current device.  Looked up on
+// every call (a host-side table lookup once the module is loaded), so that a
+// context that was destroyed and created again never sees a stale address.
 cudaError_t scratch_address(unsigned char** out) {
-    int dev = 0;
-    cudaError_t err = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (err != cudaSuccess) return err;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (g_na_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (err != cudaSuccess) return err;
-        g_na_ptr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_na_ptr[dev];
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
+}
+
+// [a, a + na) and [b, b + nb) share a byte (null buffers share none)
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    if (a == nullptr || b == nullptr) return false;
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
 }
 
 }  // namespace
@@ -160,11 +155,19 @@ extern "C" jwf_status jwf_step_relaxed_bwd_noalloc(int32_t n_envs, int32_t H, in
         d_gburn_out == nullptr || d_gun == nullptr || d_gburn == nullptr)
         return JWF_EINVAL;
     if (!(p_continue >= 0.f && p_continue <= 1.f)) return JWF_EINVAL;
+    // every output must be disjoint from every input and from the other
+    // outputs: the two passes read the inputs after the first has written
+    const size_t fb = (size_t)cells * sizeof(float);
     const void* ins[] = {d_pun, d_pburn, d_mask, d_gun_out, d_gburn_out, d_r};
-    const void* outs[] = {d_gun, d_gburn};
-    for (const void* o : outs)
-        for (const void* i : ins)
-            if (o == i) return JWF_EINVAL;
+    const size_t in_bytes[] = {fb, fb, fb, fb, fb, 8 * fb};
+    const void* outs[] = {d_gun, d_gburn, d_gpc};
+    const size_t out_bytes[] = {fb, fb, sizeof(double)};
+    for (int o = 0; o < 3; ++o) {
+        for (int i = 0; i < 6; ++i)
+            if (overlaps(outs[o], out_bytes[o], ins[i], in_bytes[i])) return JWF_EINVAL;
+        for (int p = o + 1; p < 3; ++p)
+            if (overlaps(outs[o], out_bytes[o], outs[p], out_bytes[p])) return JWF_EINVAL;
+    }
     unsigned char* base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return JWF_ECUDA;
     float* glam = reinterpret_cast<float*>(base);

@@ -210,10 +210,31 @@ def relaxed_bwd_noalloc(n_envs: int, H: int, W: int, r, p_continue: float, pun, 
     batch without a context, for callers that cannot allocate device memory
     (the library allocates nothing; output tensors the caller does not pass
     are created here, by torch).  Returns (gun, gburn)."""
+    cells = int(n_envs) * int(H) * int(W)
+    if int(n_envs) < 1 or int(H) < 1 or int(W) < 1:
+        raise ValueError("n_envs, H and W must be positive")
     if gun is None:
         gun = torch.empty_like(pun)
     if gburn is None:
         gburn = torch.empty_like(pburn)
+    # the library takes raw pointers: check every buffer against the sizes
+    # the call implies before it can read or write past an end
+    planes = {"pun": pun, "pburn": pburn, "gun_out": gun_out, "gburn_out": gburn_out, "gun": gun,
+              "gburn": gburn, "mask": mask}
+    device = r.device if isinstance(r, torch.Tensor) else None
+    for name, t, n, dt in ([("r", r, 8 * cells, torch.float32)]
+                           + [(k, v, cells, torch.float32) for k, v in planes.items()]
+                           + [("gpc", gpc, 1, torch.float64)]):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if t.numel() != n:
+            raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+        if t.device != device:
+            raise ValueError(f"{name} is on {t.device}, r on {device}")
     st = lib().jwf_step_relaxed_bwd_noalloc(int(n_envs), int(H), int(W), _ptr(r), ctypes.c_float(p_continue),
                                             _ptr(pun), _ptr(pburn), _ptr(mask), _ptr(gun_out), _ptr(gburn_out),
                                             _ptr(gun), _ptr(gburn), _ptr(gpc), _stream(stream))

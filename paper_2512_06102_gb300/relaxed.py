@@ -226,13 +226,23 @@ def straight_through(theta, sim, scene, F0, T, build_tables=True, cell_size=30.0
 
 
 def calibration_loss(p_un_T: torch.Tensor, target: torch.Tensor, H: int, W: int, pool: int = 4,
-                     w_mse: float = 1.0) -> torch.Tensor:
+                     w_mse: float = 1.0, n_total: int | None = None) -> torch.Tensor:
     """Section 4: binary cross-entropy on the spread shape plus MSE after 2-D
-    average pooling; the prediction is 1 - p_un.  Uniform batches of H x W."""
+    average pooling; the prediction is 1 - p_un.  Uniform batches of H x W.
+
+    Both terms are means over the whole batch.  A rank that holds n of the
+    batch's n_total grids passes n_total: its value is then its share (the
+    sums over its own grids divided by the whole batch's counts), and the
+    shares of all ranks add up to the loss of the whole batch, as do their
+    gradients.  n_total=None means this call sees the whole batch."""
     pred = (1.0 - p_un_T).reshape(-1, H, W)
     tgt = target.reshape(-1, H, W)
-    bce = torch.nn.functional.binary_cross_entropy(pred, tgt)
     n = pred.shape[0]
+    n_all = n if n_total is None else int(n_total)
+    if n_all < 1:
+        raise ValueError("the batch holds no grids")
+    bce = torch.nn.functional.binary_cross_entropy(pred, tgt, reduction="sum") / float(n_all * H * W)
     pp = pred.reshape(n, H // pool, pool, W // pool, pool).mean(dim=(2, 4))
     tp = tgt.reshape(n, H // pool, pool, W // pool, pool).mean(dim=(2, 4))
-    return bce + w_mse * ((pp - tp) ** 2).mean()
+    mse = ((pp - tp) ** 2).sum() / float(n_all * (H // pool) * (W // pool))
+    return bce + w_mse * mse
