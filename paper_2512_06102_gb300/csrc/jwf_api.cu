@@ -48,7 +48,8 @@ void free_all(jwf_ctx* c) {
                     c->d_status, c->d_queue, c->d_partials, c->d_red_counter, c->d_glam, c->d_gr, c->d_wexp,
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
                     c->d_tcnt, c->d_rtiles, c->d_r2tiles, c->d_adj, c->d_wser, c->d_agent_drops, c->d_agent_cnt,
-                    c->d_agent_done, c->d_stiles, c->d_tmaps, c->d_tma_ok, c->d_order_dyn, c->d_lastb};
+                    c->d_agent_done, c->d_stiles, c->d_tmaps, c->d_tma_ok, c->d_order_dyn, c->d_lastb,
+                    c->d_tplan};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -228,6 +229,8 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = dev_alloc(&c->d_tsync, tiles4.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_tburnt, tiles4.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_tcnt, (size_t)16 * 2 * N);
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tplan, (size_t)4 + N + 2 * tiles4.size());
+    if (err == cudaSuccess) err = cudaMemset(c->d_tplan, 0, ((size_t)4 + N) * sizeof(int32_t));
     if (err == cudaSuccess)
         err = cudaMemcpy(c->d_tiles4, tiles4.data(), tiles4.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess)

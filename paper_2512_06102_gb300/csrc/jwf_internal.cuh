@@ -237,6 +237,12 @@ struct jwf_ctx {
     bool tma_diag_no_copy = false;       // diagnostics (jwf_set_tile_copy_wait): the waits run out
     int32_t* d_tburnt = nullptr;
     int32_t* d_tcnt = nullptr;
+    // per-round plan of the persistent tiled step: [0] active tiles, [1]
+    // quiet tiles to copy once, [2] work cursor, [3] unused, then the burned
+    // cells of each env's quiet tiles [N], the active list and the copy list
+    // [n_tiles4 each]; the header and the per-env sums are zero between rounds
+    int32_t* d_tplan = nullptr;
+    int tiled_grid[2] = {0, 0};          // persistent CTAs of the tiled step (table, fused)
     bool tiles_valid = false;
     int32_t round_steps = 16;            // steps per tiled launch (1..16)
     // size classes of the resident path and the streams/events they fork onto

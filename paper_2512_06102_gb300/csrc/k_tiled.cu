@@ -69,6 +69,8 @@ struct TileArgs {
     uint32_t* status;
     uint64_t wait_ns;            // bound of a tensor-copy wait
     int32_t diag_no_copy;        // diagnostics: arm the barrier but issue no copy (the wait runs out)
+    int32_t* plan;               // the round's plan (k_tile_plan): counts, cursor, lists
+    int64_t n_tiles;
     int32_t kb;
     int32_t R;
     uint32_t key0, key1;
@@ -137,8 +139,142 @@ __device__ __forceinline__ uint32_t col_bits(int w, int c0, int c1) {
     return span << lo;
 }
 
+// The plan of a round, one thread per tile.  A tile runs the round when it
+// holds fire or a neighbour holds fire within kMaxRound cells of the side or
+// corner they share (fire moves at most one cell a step): it goes to the
+// active list.  Every other tile keeps its interior: its burned cells go to
+// its env's sum, its activity for the next round is none, and when the other
+// buffer does not hold its interior yet it goes to the copy list.  The plan
+// kernel also zeroes the round's per-step count scratch.
+__global__ void __launch_bounds__(256)
+k_tile_plan(int64_t n_tiles, const int4* __restrict__ tiles, const int4* __restrict__ env_tiles,
+            const uint16_t* __restrict__ act_in, uint16_t* __restrict__ act_out, const uint8_t* __restrict__ synced,
+            const int32_t* __restrict__ tile_burnt, int32_t N, int32_t* __restrict__ plan,
+            int32_t* __restrict__ cnt, int64_t n_cnt) {
+    const int64_t tix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = tix; i < n_cnt; i += (int64_t)gridDim.x * blockDim.x) cnt[i] = 0;
+    const int lane = threadIdx.x & 31;
+    bool active = false, copy = false;
+    if (tix < n_tiles) {
+        const int4 tl = tiles[tix];
+        const int e = tl.x, tr = tl.y, tc = tl.z;
+        const int4 et = env_tiles[e];
+        // the bit of neighbour (dy, dx) that faces this tile
+        constexpr uint16_t facing[3][3] = {{kActSE, kActS, kActSW}, {kActE, kActAny, kActW}, {kActNE, kActN, kActNW}};
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int r = tr + dy, c = tc + dx;
+                if (r >= 0 && r < et.z && c >= 0 && c < et.y)
+                    active |= (act_in[et.x + r * et.y + c] & facing[dy + 1][dx + 1]) != 0;
+            }
+        if (!active) {
+            act_out[tix] = 0;
+            copy = synced[tix] == 0;
+            const int32_t b = tile_burnt[tix];
+            if (b != 0) atomicAdd(&plan[4 + e], b);
+        }
+    }
+    const uint32_t am = __ballot_sync(0xffffffffu, active);
+    const uint32_t cm = __ballot_sync(0xffffffffu, copy);
+    int base_a = 0, base_c = 0;
+    if (lane == 0) {
+        if (am) base_a = atomicAdd(&plan[0], __popc(am));
+        if (cm) base_c = atomicAdd(&plan[1], __popc(cm));
+    }
+    base_a = __shfl_sync(0xffffffffu, base_a, 0);
+    base_c = __shfl_sync(0xffffffffu, base_c, 0);
+    const uint32_t below = (1u << lane) - 1u;
+    int32_t* act_list = plan + 4 + N;
+    if (active) act_list[base_a + __popc(am & below)] = (int32_t)tix;
+    if (copy) act_list[n_tiles + base_c + __popc(cm & below)] = (int32_t)tix;
+}
+
+// Tile activity and burned interior cells from a state buffer, one CTA per
+// tile (after the state changed outside the tiled path): the same activity
+// bits a round leaves behind, so that only tiles with fire within reach run
+// the next round, and the burned count a quiet tile reports.  The interior is
+// copied to the other buffer on the way, so both buffers hold it.
+__global__ void __launch_bounds__(256)
+k_tile_act_init(const int4* __restrict__ tiles, const int32_t* __restrict__ Hs, const int32_t* __restrict__ Ws,
+                const int64_t* __restrict__ offs, const uint8_t* __restrict__ F, uint8_t* __restrict__ Fo,
+                uint16_t* __restrict__ act, uint8_t* __restrict__ synced, int32_t* __restrict__ tile_burnt) {
+    __shared__ uint32_t s_act;
+    __shared__ int32_t s_burnt;
+    const int tix = blockIdx.x;
+    const int4 tl = tiles[tix];
+    const int e = tl.x;
+    const int H = Hs[e], W = Ws[e];
+    const int ty0 = tl.y * kTileRows, tx0 = tl.z * kTileCols;
+    const int TY = min(kTileRows, H - ty0), TX = min(kTileCols, W - tx0);
+    const uint8_t* Fe = F + offs[e];
+    uint8_t* Foe = Fo + offs[e];
+    if (threadIdx.x == 0) {
+        s_act = 0u;
+        s_burnt = 0;
+    }
+    __syncthreads();
+    constexpr int band = kMaxRound;
+    uint32_t a = 0u;
+    int nd = 0;
+    // one cell's contribution: burned count, activity bits of a burning cell
+    auto cell = [&](uint8_t st, int y, int x) {
+        nd += st == 3;
+        if (st != 2) return;
+        const bool n = y < band, so = TY - 1 - y < band, wb = x < band, eb = TX - 1 - x < band;
+        a |= kActAny | (n ? kActN : 0) | (so ? kActS : 0) | (wb ? kActW : 0) | (eb ? kActE : 0) |
+             (n && wb ? kActNW : 0) | (n && eb ? kActNE : 0) | (so && wb ? kActSW : 0) | (so && eb ? kActSE : 0);
+    };
+    if (((offs[e] | (int64_t)W) & 15) == 0 && (TX & 15) == 0) {
+        // 16 cells a thread: rows start on 16-byte boundaries (tx0 is a multiple of 128)
+        const int segs = TX >> 4;
+        for (int i = threadIdx.x; i < TY * segs; i += blockDim.x) {
+            const int y = i / segs, x0 = (i - y * segs) << 4;
+            const int64_t g = (int64_t)(ty0 + y) * W + tx0 + x0;
+            const uint4 v = *reinterpret_cast<const uint4*>(Fe + g);
+            *reinterpret_cast<uint4*>(Foe + g) = v;
+            const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                nd += __popc(__vcmpeq4(w4[k], 0x03030303u)) >> 3;
+                const uint32_t b = __vcmpeq4(w4[k], 0x02020202u);
+                if (b == 0u) continue;
+                for (int j = 0; j < 4; ++j)
+                    if ((b >> (8 * j)) & 1u) cell(2, y, x0 + 4 * k + j);
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < TY * TX; i += blockDim.x) {
+            const int y = i / TX, x = i - (i / TX) * TX;
+            const int64_t g = (int64_t)(ty0 + y) * W + tx0 + x;
+            const uint8_t st = Fe[g];
+            Foe[g] = st;
+            cell(st, y, x);
+        }
+    }
+    a = __reduce_or_sync(0xffffffffu, a);
+    nd = __reduce_add_sync(0xffffffffu, nd);
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicOr(&s_act, a);
+        if (nd) atomicAdd(&s_burnt, nd);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        act[tix] = (uint16_t)s_act;
+        synced[tix] = 1;
+        tile_burnt[tix] = s_burnt;
+    }
+}
+
+// Persistent CTAs take the round's items from the plan: the active tiles
+// (stepped) and then the quiet tiles whose interior is copied once to the
+// other buffer.
+// resident CTAs per SM the register budget is set for, and the work items a
+// thread of the fused variant evaluates at once
+__host__ __device__ constexpr int tiled_min_blocks(int nt) { return nt == 256 ? 2 : nt == 128 ? 4 : 1; }
+__host__ __device__ constexpr int tiled_ilp(int nt) { return nt == 512 ? 4 : 2; }
+
 template <int NT, bool FUSED>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, tiled_min_blocks(NT))
 k_step_tiled(const TileArgs a, const RateConsts Kc) {
     extern __shared__ uint32_t sm[];
     // per step: interior burning, interior burn-outs, interior cells doused by
@@ -147,74 +283,74 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     __shared__ int32_t s_d0;
     __shared__ uint32_t s_act;
     __shared__ int32_t s_qn[3];
-    __shared__ int s_active;
+    __shared__ int s_item;
     __shared__ int s_tma;
     __shared__ alignas(8) uint64_t s_bar;
     __shared__ typename std::conditional<FUSED, RateConsts, int>::type sK_store;
     const RateConsts& sK = *reinterpret_cast<const RateConsts*>(&sK_store);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tix = blockIdx.x;
+    if (FUSED) {
+        for (int i = threadIdx.x; i < (int)(sizeof(RateConsts) / 4); i += NT)
+            reinterpret_cast<float*>(&sK_store)[i] = reinterpret_cast<const float*>(&Kc)[i];
+    }
+    const int32_t n_act = a.plan[0], n_copy = a.plan[1];
+    const int32_t* act_list = a.plan + 4 + a.N;
+    const int32_t* copy_list = act_list + a.n_tiles;
+    // only thread 0 uses the barrier: it counts the completed tensor copies
+    // and waits for phase parity ph
+    uint32_t ph = 0;
+    if (threadIdx.x == 0) jwf_mbar_init(&s_bar, 1);
+    const int kb = a.kb;
+    for (;;) {
+    // each thread's earlier shared-memory accesses are ordered before the
+    // next tensor copy into the same memory
+    jwf_fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.plan[2], 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_act + n_copy) break;
+    const bool is_copy = item >= n_act;
+    const int tix = is_copy ? copy_list[item - n_act] : act_list[item];
     const int4 tl = a.tiles[tix];
     const int e = tl.x, tr = tl.y, tc = tl.z;
     const int H = a.H[e], W = a.W[e];
     const int64_t off = a.off[e];
-    const int4 et = a.env_tiles[e];
     const int ty0 = tr * kTileRows, tx0 = tc * kTileCols;
     const int TY = min(kTileRows, H - ty0), TX = min(kTileCols, W - tx0);
-    const int kb = a.kb;
-    if (threadIdx.x == 0) {
-        // the bit of neighbour (dy, dx) that faces this tile
-        constexpr uint16_t facing[3][3] = {{kActSE, kActS, kActSW}, {kActE, kActAny, kActW}, {kActNE, kActN, kActNW}};
-        int act = 0;
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int r = tr + dy, c = tc + dx;
-                if (r >= 0 && r < et.z && c >= 0 && c < et.y)
-                    act |= (a.act_in[et.x + r * et.y + c] & facing[dy + 1][dx + 1]) != 0;
-            }
-        s_active = act;
-    }
-    __syncthreads();
     const bool use_tma = a.tma_ok != nullptr && a.tma_ok[e] != 0;
-    if (!s_active) {
-        // no fire within reach: the interior stays as it is this round
-        bool copied = true;
-        if (!a.synced[tix]) {
-            if (use_tma) {
-                // one tensor copy in, one out (cells outside the grid are
-                // neither read nor written)
-                if (threadIdx.x == 0) {
-                    uint8_t* stg = reinterpret_cast<uint8_t*>(sm) + ((128u - (jwf_smem_u32(sm) & 127u)) & 127u);
-                    jwf_mbar_init(&s_bar, 1);
-                    jwf_mbar_expect_tx(&s_bar, kTileRows * kTileCols);
-                    if (!a.diag_no_copy) jwf_tma_load_2d(stg, a.tm_in_tile + e, tx0, ty0, &s_bar);
-                    if (jwf_mbar_wait_bounded(&s_bar, 0, a.wait_ns)) {
-                        jwf_tma_store_2d(a.tm_out_tile + e, tx0, ty0, stg);
-                        jwf_bulk_commit();
-                        jwf_bulk_wait_all();
-                    } else {
-                        atomicOr(a.status, JWF_DEVERR_TMA);
-                        jwf_mbar_wait_bounded(&s_bar, 0, a.wait_ns);      // a late copy lands before the exit
-                        copied = false;
-                    }
+    if (is_copy) {
+        // no fire within reach: the interior stays as it is; copy it once to
+        // the other buffer (cells outside the grid are neither read nor written)
+        if (use_tma) {
+            if (threadIdx.x == 0) {
+                uint8_t* stg = reinterpret_cast<uint8_t*>(sm) + ((128u - (jwf_smem_u32(sm) & 127u)) & 127u);
+                jwf_mbar_expect_tx(&s_bar, kTileRows * kTileCols);
+                if (!a.diag_no_copy) jwf_tma_load_2d(stg, a.tm_in_tile + e, tx0, ty0, &s_bar);
+                int ok = 1;
+                if (jwf_mbar_wait_bounded(&s_bar, ph, a.wait_ns)) {
+                    jwf_tma_store_2d(a.tm_out_tile + e, tx0, ty0, stg);
+                    jwf_bulk_commit();
+                    jwf_bulk_wait_all();
+                } else {
+                    atomicOr(a.status, JWF_DEVERR_TMA);
+                    jwf_mbar_wait_bounded(&s_bar, ph, a.wait_ns);      // a late copy lands before the exit
+                    ok = 0;
                 }
-            } else {
-                for (int i = threadIdx.x; i < TY * TX; i += NT) {
-                    const int64_t g = off + (int64_t)(ty0 + i / TX) * W + tx0 + i % TX;
-                    a.Fout[g] = a.Fin[g];
-                }
+                ph ^= 1u;
+                a.synced[tix] = (uint8_t)ok;
+                s_tma = ok;
             }
+            __syncthreads();
+            if (!s_tma) break;          // the barrier's phase is unknown: this CTA stops
+        } else {
+            for (int i = threadIdx.x; i < TY * TX; i += NT) {
+                const int64_t g = off + (int64_t)(ty0 + i / TX) * W + tx0 + i % TX;
+                a.Fout[g] = a.Fin[g];
+            }
+            if (threadIdx.x == 0) a.synced[tix] = 1;
         }
-        if ((int)threadIdx.x < kb) atomicAdd(&a.cnt[((int64_t)threadIdx.x * 2 + 1) * a.N + e], a.tile_burnt[tix]);
-        if (threadIdx.x == 0) {
-            a.act_out[tix] = 0;
-            a.synced[tix] = copied ? 1 : 0;
-        }
-        return;
-    }
-    if (FUSED) {
-        for (int i = threadIdx.x; i < (int)(sizeof(RateConsts) / 4); i += NT)
-            reinterpret_cast<float*>(&sK_store)[i] = reinterpret_cast<const float*>(&Kc)[i];
+        continue;
     }
     // region: rows [ty0 - kb, ty0 + TY + kb), columns [tx0 - 32, tx0 + TX + 32)
     const int oy = ty0 - kb, ox = tx0 - 32;
@@ -245,7 +381,6 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     if (use_tma && threadIdx.x == 0) {
         // region rows [ty0 - kb, ty0 - kb + kBoxRows), columns [tx0 - 32, tx0 + 160):
         // x is a multiple of 32 cells; rows and columns outside the grid read as 0
-        jwf_mbar_init(&s_bar, 1);
         jwf_mbar_expect_tx(&s_bar, kBoxRows * kBoxCols);
         if (!a.diag_no_copy) jwf_tma_load_2d(stg, a.tm_region + e, tx0 - 32, ty0 - kb, &s_bar);
     }
@@ -258,16 +393,18 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     }
     ignw[lane] = 0u;
     outw[lane] = 0u;
-    if (use_tma && threadIdx.x == 0) s_tma = jwf_mbar_wait_bounded(&s_bar, 0, a.wait_ns) ? 1 : 0;
+    if (use_tma && threadIdx.x == 0) s_tma = jwf_mbar_wait_bounded(&s_bar, ph, a.wait_ns) ? 1 : 0;
     __syncthreads();
     if (use_tma && !s_tma) {
-        // the copy did not complete: report, let a late copy land, leave the tile
+        // the copy did not complete: report, let a late copy land, and stop
+        // (the barrier's phase is unknown; other CTAs take the remaining tiles)
         if (threadIdx.x == 0) {
             atomicOr(a.status, JWF_DEVERR_TMA);
-            jwf_mbar_wait_bounded(&s_bar, 0, a.wait_ns);
+            jwf_mbar_wait_bounded(&s_bar, ph, a.wait_ns);
         }
-        return;
+        break;
     }
+    if (use_tma) ph ^= 1u;
     // load the region (cells outside the grid read as no fuel)
     for (int i = threadIdx.x; i < words; i += NT) {
         const int ry = i / WW, w = i - (i / WW) * WW;
@@ -519,8 +656,35 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             }
         }
         __syncthreads();
-        // phase B: every thread of the CTA evaluates queued items
-        {
+        // phase B: every thread of the CTA evaluates queued items (the fused
+        // variant several at a time)
+        if (FUSED) {
+            constexpr int ILP = tiled_ilp(NT);
+            const int qn = min(s_qn[s % 3], kQCap);
+            for (int q0 = threadIdx.x; q0 < qn; q0 += NT * ILP) {
+                int yy[ILP], xx[ILP], kind[ILP], dd[ILP], iis[ILP], js[ILP];
+#pragma unroll
+                for (int k = 0; k < ILP; ++k) {
+                    const int q = q0 + k * NT;
+                    const uint32_t it = Q[q < qn ? q : q0];
+                    const int ii = (int)(it >> 20), j = (int)(it >> 15) & 31;
+                    const int ry = ii / WW;
+                    yy[k] = oy + ry;
+                    xx[k] = ox + ((ii - ry * WW) << 5) + j;
+                    kind[k] = q < qn ? ((it & (1u << 14)) ? 2 : 1) : 0;
+                    dd[k] = (int)(it & 7u);
+                    iis[k] = ii;
+                    js[k] = j;
+                }
+                bool below[ILP];
+                eval_items<ILP>(a, sK, e, off, W, yy, xx, kind, dd, tt, ep4, below);
+#pragma unroll
+                for (int k = 0; k < ILP; ++k) {
+                    if (kind[k] == 2 && below[k]) atomicOr(&IG[iis[k]], 1u << js[k]);
+                    if (kind[k] == 1 && !below[k]) atomicOr(&OU[iis[k]], 1u << js[k]);
+                }
+            }
+        } else {
             const int qn = min(s_qn[s % 3], kQCap);
             for (int q = threadIdx.x; q < qn; q += NT) {
                 const uint32_t it = Q[q];
@@ -666,17 +830,27 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         a.act_out[tix] = (uint16_t)s_act;
         a.synced[tix] = 0;
     }
+    }
 }
 
-// After a round: per-step outputs, done flags and t += kb, one thread per env.
-__global__ void k_round_finalize(int32_t N, int32_t kb, const int32_t* __restrict__ cnt, int32_t* __restrict__ t,
-                                 int32_t t_max, int32_t* __restrict__ burning, int32_t* __restrict__ burnt,
-                                 uint8_t* __restrict__ done) {
+// After a round: per-step outputs (burned = the active tiles' per-step
+// counts + the quiet tiles' cells), done flags and t += kb, one thread per
+// env; the plan's header and per-env sums are cleared for the next round.
+__global__ void k_round_finalize(int32_t N, int32_t kb, const int32_t* __restrict__ cnt, int32_t* __restrict__ plan,
+                                 int32_t* __restrict__ t, int32_t t_max, int32_t* __restrict__ burning,
+                                 int32_t* __restrict__ burnt, uint8_t* __restrict__ done) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e == 0) {
+        plan[0] = 0;
+        plan[1] = 0;
+        plan[2] = 0;
+    }
     if (e >= N) return;
+    const int32_t quiet = plan[4 + e];
+    plan[4 + e] = 0;
     const int32_t t0 = t[e];
     for (int s = 0; s < kb; ++s) {
-        const int32_t nb = cnt[((int64_t)s * 2) * N + e], nd = cnt[((int64_t)s * 2 + 1) * N + e];
+        const int32_t nb = cnt[((int64_t)s * 2) * N + e], nd = cnt[((int64_t)s * 2 + 1) * N + e] + quiet;
         const int64_t o = (int64_t)s * N + e;
         if (burning) burning[o] = nb;
         if (burnt) burnt[o] = nd;
@@ -687,19 +861,27 @@ __global__ void k_round_finalize(int32_t N, int32_t kb, const int32_t* __restric
 
 constexpr int kMaxDev = 64;
 
+// One persistent CTA per resident slot (never more than there are tiles);
+// the attribute and occupancy queries run once per device.
 template <int NT, bool FUSED>
 cudaError_t launch_tiled_t(const jwf_ctx* c, const TileArgs& a, const RateConsts& K, cudaStream_t s) {
-    static size_t set_smem[kMaxDev] = {};
+    static int per_sm[kMaxDev] = {};
     const size_t smem = tiled_smem_bytes(NT);
     const int dev = c->device;
     if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-    if (smem > set_smem[dev]) {
-        const cudaError_t err = cudaFuncSetAttribute(k_step_tiled<NT, FUSED>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (per_sm[dev] == 0) {
+        cudaError_t err = cudaFuncSetAttribute(k_step_tiled<NT, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
         if (err != cudaSuccess) return err;
-        set_smem[dev] = smem;
+        int n = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_tiled<NT, FUSED>, NT, smem);
+        if (err != cudaSuccess) return err;
+        if (n < 1) return cudaErrorInvalidConfiguration;
+        per_sm[dev] = n;
     }
-    k_step_tiled<NT, FUSED><<<(unsigned)c->n_tiles4, NT, smem, s>>>(a, K);
+    int64_t grid = (int64_t)per_sm[dev] * c->num_sms;
+    if (grid > c->n_tiles4) grid = c->n_tiles4;
+    k_step_tiled<NT, FUSED><<<(unsigned)grid, NT, smem, s>>>(a, K);
     return cudaGetLastError();
 }
 }  // namespace
@@ -713,9 +895,13 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
                                   int32_t* burnt, uint8_t* done, bool fused, cudaStream_t s) {
     cudaError_t err;
     if (!c->tiles_valid) {
-        // the state changed outside the tiled path: every tile may be active
-        err = cudaMemsetAsync(c->d_tact[c->tact_cur], 0xFF, (size_t)c->n_tiles4 * sizeof(uint16_t), s);
-        if (err == cudaSuccess) err = cudaMemsetAsync(c->d_tsync, 0, (size_t)c->n_tiles4, s);
+        // the state changed outside the tiled path: each tile's activity and
+        // burned cells from the current state
+        k_tile_act_init<<<(unsigned)c->n_tiles4, 256, 0, s>>>(c->d_tiles4, c->d_H, c->d_W, c->d_off,
+                                                             c->d_state[c->cur], c->d_state[c->cur ^ 1],
+                                                             c->d_tact[c->tact_cur],
+                                                             c->d_tsync, c->d_tburnt);
+        err = cudaGetLastError();
         if (err != cudaSuccess) return err;
         c->tiles_valid = true;
     }
@@ -728,7 +914,13 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
     if (c->hist != nullptr) rs = 1;     // recording: the state after every step
     for (int32_t s0 = 0; s0 < k; s0 += rs) {
         const int32_t kb = (k - s0) < rs ? (k - s0) : rs;
-        err = cudaMemsetAsync(c->d_tcnt, 0, (size_t)kb * 2 * c->N * sizeof(int32_t), s);
+        // the plan: active tiles, quiet tiles to copy, the quiet tiles' burned
+        // cells per env (and the round's count scratch zeroed)
+        const int64_t n_cnt = (int64_t)kb * 2 * c->N;
+        k_tile_plan<<<(unsigned)((c->n_tiles4 + 255) / 256), 256, 0, s>>>(
+            c->n_tiles4, c->d_tiles4, c->d_env_tiles, c->d_tact[c->tact_cur], c->d_tact[c->tact_cur ^ 1],
+            c->d_tsync, c->d_tburnt, c->N, c->d_tplan, c->d_tcnt, n_cnt);
+        err = cudaGetLastError();
         if (err != cudaSuccess) return err;
         TileArgs a;
         a.H = c->d_H;
@@ -761,6 +953,8 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         a.status = c->d_status;
         a.wait_ns = c->tma_wait_ns;
         a.diag_no_copy = c->tma_diag_no_copy ? 1 : 0;
+        a.plan = c->d_tplan;
+        a.n_tiles = c->n_tiles4;
         a.kb = kb;
         a.R = c->drop_radius;
         a.key0 = (uint32_t)(c->seed & 0xffffffffu);
@@ -775,7 +969,7 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
             err = fused ? launch_tiled_t<256, true>(c, a, K, s) : launch_tiled_t<256, false>(c, a, K, s);
         if (err != cudaSuccess) return err;
         const int64_t o = (int64_t)s0 * c->N;
-        k_round_finalize<<<(c->N + 255) / 256, 256, 0, s>>>(c->N, kb, c->d_tcnt, c->d_t, c->t_max,
+        k_round_finalize<<<(c->N + 255) / 256, 256, 0, s>>>(c->N, kb, c->d_tcnt, c->d_tplan, c->d_t, c->t_max,
                                                              burning ? burning + o : nullptr,
                                                              burnt ? burnt + o : nullptr, done ? done + o : nullptr);
         err = cudaGetLastError();

@@ -54,4 +54,51 @@ __device__ __forceinline__ bool pair_ignites(const Args& a, const RateConsts& K,
     return jwf_u24(uw) < prob_of(r);
 }
 
+// Fused variant, up to ILP work items of one thread at once: kind 1 is a
+// burning cell's remain-burning draw, kind 2 a compared (target, source)
+// pair in direction d, kind 0 no item (its coordinates must still be a cell
+// of the env).  The items' memory loads, Philox blocks and rates are issued
+// stage by stage across the items, so that their latencies overlap.  below[k]
+// = the item's uniform is below its probability: for a pair the source
+// ignites the target (as pair_ignites), for a draw the cell keeps burning.
+template <int ILP, class Args>
+__device__ __forceinline__ void eval_items(const Args& a, const RateConsts& K, int e, int64_t off, int W,
+                                           const int (&yy)[ILP], const int (&xx)[ILP], const int (&kind)[ILP],
+                                           const int (&dd)[ILP], uint32_t tt, uint32_t ep4, bool (&below)[ILP]) {
+    int cv[ILP], cu[ILP];
+    float zv[ILP], zu[ILP];
+    float2 w2[ILP];
+    uint32_t cell[ILP];
+    const int ts = a.wser_n > 0 ? min((int)tt, a.wser_n - 1) : 0;
+    const float2* wx = a.wexp + ((int64_t)ts * a.N + e) * 8;
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        cell[k] = (uint32_t)(yy[k] * W + xx[k]);
+        const bool pair = kind[k] == 2;
+        const int d = pair ? dd[k] : 0;
+        const int64_t v = off + cell[k];
+        const int64_t u = pair ? off + (int64_t)(yy[k] - jwf_dr(d)) * W + (xx[k] - jwf_dx(d)) : v;
+        cv[k] = a.cls[v];
+        cu[k] = a.cls[u];
+        zv[k] = a.dem[v];
+        zu[k] = a.dem[u];
+        w2[k] = wx[d];
+    }
+    uint32_t uw[ILP];
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        const bool pair = kind[k] == 2;
+        const int d = dd[k];
+        const uint4 u4 = jwf_philox(make_uint4(cell[k], tt, (uint32_t)e, ep4 + (pair ? (uint32_t)(d >> 2) : 2u)),
+                                    a.key0, a.key1);
+        uw[k] = !pair ? u4.x : (d & 3) == 0 ? u4.x : (d & 3) == 1 ? u4.y : (d & 3) == 2 ? u4.z : u4.w;
+    }
+#pragma unroll
+    for (int k = 0; k < ILP; ++k) {
+        float p = a.p_continue;
+        if (kind[k] == 2) p = prob_of(rate_of(K.G[cv[k]][cu[k]], zv[k], zu[k], {w2[k].x, w2[k].y}, dd[k], K));
+        below[k] = jwf_u24(uw[k]) < p;
+    }
+}
+
 }  // namespace
