@@ -49,7 +49,7 @@ void free_all(jwf_ctx* c) {
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
                     c->d_tcnt, c->d_rtiles, c->d_r2tiles, c->d_adj, c->d_wser, c->d_agent_drops, c->d_agent_cnt,
                     c->d_agent_done, c->d_stiles, c->d_tmaps, c->d_tma_ok, c->d_order_dyn, c->d_lastb,
-                    c->d_tplan};
+                    c->d_tplan, c->d_s2tiles};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -161,6 +161,11 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
         for (int y = 0; y < c->H[e]; y += JWF_SW_ROWS)
             for (int x = 0; x < c->W[e]; x += JWF_SW_COLS) stiles.push_back(make_int4(e, y, x, 0));
     c->n_stiles = (int64_t)stiles.size();
+    std::vector<int4> s2tiles;
+    for (int32_t e = 0; e < N; ++e)
+        for (int y = 0; y < c->H[e]; y += JWF_SW2_ROWS)
+            for (int x = 0; x < c->W[e]; x += JWF_SW2_COLS) s2tiles.push_back(make_int4(e, y, x, 0));
+    c->n_s2tiles = (int64_t)s2tiles.size();
     // processing order: size class (by the longer side) descending, then
     // cells descending; each class is one resident launch
     auto size_class = [&](int32_t e) {
@@ -210,6 +215,7 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = dev_alloc(&c->d_rtiles, rtiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_r2tiles, r2tiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_stiles, stiles.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_s2tiles, s2tiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_agent_drops, 2 * (size_t)N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_agent_cnt, (size_t)N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_agent_done, (size_t)N);
@@ -242,6 +248,8 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
         err = cudaMemcpy(c->d_r2tiles, r2tiles.data(), r2tiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess)
         err = cudaMemcpy(c->d_stiles, stiles.data(), stiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(c->d_s2tiles, s2tiles.data(), s2tiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_H, c->H.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_W, c->W.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_off, c->off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -850,20 +858,40 @@ jwf_status jwf_relaxed_bwd_steps(jwf_ctx* ctx, int32_t n_steps, const float* d_p
         return fail(ctx, JWF_EINVAL, "jwf_relaxed_bwd_steps: outputs overlap inputs");
     if (!ctx->have_params || !ctx->have_rates)
         return fail(ctx, JWF_ESTATE, "jwf_relaxed_bwd_steps: needs parameters and a rate table");
-    // step t writes its adjoints to the outputs when t is even, else to the
-    // context's scratch, so that step 0 ends in the outputs
+    // passes from the last step down: one step (an odd count's last step, or
+    // every step on the plain kernels) or two (the tiled kernels); the passes
+    // alternate between the outputs and the context's scratch so that the
+    // last pass, the one that ends at step 0, writes the outputs
+    const bool two = ctx->relaxed_kernel == JWF_RELAXED_TILED && d_glam != nullptr;
+    const int32_t passes = two ? n_steps / 2 + n_steps % 2 : n_steps;
     float* su = ctx->d_adj;
     float* sb = ctx->d_adj + C;
-    for (int32_t t = n_steps - 1; t >= 0; --t) {
-        const float* iu = t == n_steps - 1 ? d_gun_out : ((t + 1) % 2 == 0 ? d_gun : su);
-        const float* ib = t == n_steps - 1 ? d_gburn_out : ((t + 1) % 2 == 0 ? d_gburn : sb);
-        float* ou = t % 2 == 0 ? d_gun : su;
-        float* ob = t % 2 == 0 ? d_gburn : sb;
+    const float* iu = d_gun_out;
+    const float* ib = d_gburn_out;
+    int32_t t_hi = n_steps;               // the pass covers steps [t_lo, t_hi)
+    for (int32_t p = 0; p < passes; ++p) {
+        const int32_t len = (two && !(p == 0 && n_steps % 2 == 1)) ? 2 : 1;
+        const int32_t t = t_hi - len;
+        const bool to_out = (passes - 1 - p) % 2 == 0;
+        float* ou = to_out ? d_gun : su;
+        float* ob = to_out ? d_gburn : sb;
         const float* m = d_masks != nullptr ? d_masks + (int64_t)t * C : nullptr;
-        float* glam = d_glam != nullptr ? d_glam + (int64_t)t * C : ctx->d_glam;
-        JWF_CUDA_TRY(ctx, jwf_launch_relaxed_bwd(ctx, d_pun + t * C, d_pburn + t * C, m, iu, ib, ou, ob, glam, d_gpc,
+        if (len == 2) {
+            JWF_CUDA_TRY(ctx,
+                         jwf_launch_relaxed_bwd2(ctx, d_pun + t * C, d_pburn + t * C, m, d_pun + (t + 1) * C,
+                                                 d_pburn + (t + 1) * C, m != nullptr ? m + C : nullptr, iu, ib, ou,
+                                                 ob, d_glam + (int64_t)t * C, d_glam + (int64_t)(t + 1) * C, d_gpc,
                                                  S(stream)),
-                     "jwf_relaxed_bwd_steps");
+                         "jwf_relaxed_bwd_steps");
+        } else {
+            float* glam = d_glam != nullptr ? d_glam + (int64_t)t * C : ctx->d_glam;
+            JWF_CUDA_TRY(ctx, jwf_launch_relaxed_bwd(ctx, d_pun + t * C, d_pburn + t * C, m, iu, ib, ou, ob, glam,
+                                                     d_gpc, S(stream)),
+                         "jwf_relaxed_bwd_steps");
+        }
+        iu = ou;
+        ib = ob;
+        t_hi = t;
     }
     return JWF_OK;
 }

@@ -151,7 +151,11 @@ struct JwfDevParams {
 // The relaxed adjoint sweeps strips of JWF_SW_COLS output columns (one warp,
 // a halo column on each side) down JWF_SW_ROWS rows.
 #define JWF_SW_COLS 30
-#define JWF_SW_ROWS 16
+#define JWF_SW_ROWS 32
+// The two-step adjoint sweeps strips of JWF_SW2_COLS output columns (two halo
+// columns on each side) down JWF_SW2_ROWS rows.
+#define JWF_SW2_COLS 28
+#define JWF_SW2_ROWS 32
 
 // A size class of envs run by one resident launch: envs order[start ..
 // start + count), the largest shape in it, and its block size (0: by size).
@@ -222,6 +226,8 @@ struct jwf_ctx {
     int64_t n_r2tiles = 0;
     int4* d_stiles = nullptr;            // (env, first row, first column) per adjoint sweep strip
     int64_t n_stiles = 0;
+    int4* d_s2tiles = nullptr;           // ... per two-step adjoint sweep strip
+    int64_t n_s2tiles = 0;
     int relaxed_kernel = 0;              // 0: tiled (fused adjoint), 1: plain (two-pass adjoint)
     uint16_t* d_tact[2] = {nullptr, nullptr};
     int tact_cur = 0;
@@ -337,6 +343,14 @@ cudaError_t jwf_launch_relaxed_fwd2(const jwf_ctx* c, const float* pun, const fl
 cudaError_t jwf_launch_relaxed_fwd(const jwf_ctx* c, const float* pun, const float* pburn,
                                    const float* mask, float* pun_out, float* pburn_out,
                                    cudaStream_t s);
+// two adjoint steps in one pass (tiled kernels only): states before step t
+// (pun0, pburn0) and before step t + 1 (pun1, pburn1), masks of the two steps
+// or null, the adjoints of the state after step t + 1 in, of the state before
+// step t out, and dL/dlam of both steps
+cudaError_t jwf_launch_relaxed_bwd2(jwf_ctx* c, const float* pun0, const float* pburn0, const float* mask0,
+                                    const float* pun1, const float* pburn1, const float* mask1,
+                                    const float* gun_out, const float* gburn_out, float* gun, float* gburn,
+                                    float* glam0, float* glam1, double* gpc, cudaStream_t s);
 cudaError_t jwf_launch_relaxed_bwd(jwf_ctx* c, const float* pun, const float* pburn,
                                    const float* mask, const float* gun_out,
                                    const float* gburn_out, float* gun, float* gburn,

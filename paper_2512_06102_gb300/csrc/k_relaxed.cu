@@ -675,6 +675,310 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
         *counter = 0u;
     }
 }
+// Two adjoint steps per pass.  The sweep carries the adjoint of step t + 1
+// (target row y) and, one row behind, the adjoint of step t (target row
+// y - 1): the adjoint of p_burn at row y - 1 after step t + 1's sweep is
+// complete once row y has been swept, and it is the incoming adjoint of step
+// t at that row, so each rate row is read once for both steps and the
+// adjoint between the steps never leaves the chip.  Lane L is column
+// x0 - 2 + L: step t + 1 is valid on lanes 1..30 (lanes 0 and 31 also keep
+// their outer column's p_burn), step t on lanes 2..29, the strip's output
+// columns.  Every cell's arithmetic, and the order of each sum, is that of
+// k_relaxed_bwd_sweep, so the adjoints equal two one-step sweeps.
+struct __align__(16) Sw2Slot {
+    float4 ra[32], rb[32];          // rate row of (y, x)
+    float pu1[32], au[32], ab[32];  // p_un before step t + 1 and the incoming adjoints at (y, x)
+    float pbn1[32], mn1[32];        // p_burn and mask of step t + 1 at (y + 2, x)
+    float pbo1[32], mo1[32];        // ... and at (y + 2, outer column) for the halo lanes
+    float pu0[32];                  // p_un before step t at (y - 1, x)
+    float pbn0[32], mn0[32];        // p_burn and mask of step t at (y + 1, x)
+};
+constexpr int kSw2Depth = 3;
+
+__device__ __forceinline__ void sweep2_issue(Sw2Slot& sl, int lane, const float* __restrict__ r,
+                                             const float* __restrict__ pun0, const float* __restrict__ pburn0,
+                                             const float* __restrict__ mask0, const float* __restrict__ pun1,
+                                             const float* __restrict__ pburn1, const float* __restrict__ mask1,
+                                             const float* __restrict__ gun_out, const float* __restrict__ gburn_out,
+                                             int64_t v, int y, bool col, bool col_o, int dxo, int H, int W) {
+    const bool here = col && (unsigned)y < (unsigned)H;
+    if (here) {
+        jwf_cp_async16(reinterpret_cast<float*>(&sl.ra[lane]), r + v * 8);
+        jwf_cp_async16(reinterpret_cast<float*>(&sl.rb[lane]), r + v * 8 + 4);
+        jwf_cp_async4(&sl.pu1[lane], pun1 + v);
+        jwf_cp_async4(&sl.au[lane], gun_out + v);
+        jwf_cp_async4(&sl.ab[lane], gburn_out + v);
+    } else {
+        sl.ra[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sl.rb[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sl.pu1[lane] = 0.f;
+        sl.au[lane] = 0.f;
+        sl.ab[lane] = 0.f;
+    }
+    const bool row2 = (unsigned)(y + 2) < (unsigned)H;
+    const int64_t v2 = v + 2 * (int64_t)W;
+    if (col && row2) {
+        jwf_cp_async4(&sl.pbn1[lane], pburn1 + v2);
+        if (mask1 != nullptr) jwf_cp_async4(&sl.mn1[lane], mask1 + v2);
+        else sl.mn1[lane] = 0.f;
+    } else {
+        sl.pbn1[lane] = 0.f;
+        sl.mn1[lane] = 0.f;
+    }
+    if (col_o && row2) {
+        jwf_cp_async4(&sl.pbo1[lane], pburn1 + v2 + dxo);
+        if (mask1 != nullptr) jwf_cp_async4(&sl.mo1[lane], mask1 + v2 + dxo);
+        else sl.mo1[lane] = 0.f;
+    } else {
+        sl.pbo1[lane] = 0.f;
+        sl.mo1[lane] = 0.f;
+    }
+    if (col && (unsigned)(y - 1) < (unsigned)H) jwf_cp_async4(&sl.pu0[lane], pun0 + v - W);
+    else sl.pu0[lane] = 0.f;
+    if (col && (unsigned)(y + 1) < (unsigned)H) {
+        jwf_cp_async4(&sl.pbn0[lane], pburn0 + v + W);
+        if (mask0 != nullptr) jwf_cp_async4(&sl.mn0[lane], mask0 + v + W);
+        else sl.mn0[lane] = 0.f;
+    } else {
+        sl.pbn0[lane] = 0.f;
+        sl.mn0[lane] = 0.f;
+    }
+    jwf_cp_async_commit();
+}
+
+__global__ void __launch_bounds__(kSweepWarps * 32)
+k_relaxed_bwd_sweep2(const int4* __restrict__ items, int64_t n_items, const int32_t* __restrict__ Hs,
+                     const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs, const float* __restrict__ r,
+                     const float* __restrict__ pun0, const float* __restrict__ pburn0,
+                     const float* __restrict__ mask0, const float* __restrict__ pun1,
+                     const float* __restrict__ pburn1, const float* __restrict__ mask1,
+                     const float* __restrict__ gun_out, const float* __restrict__ gburn_out, float p_continue,
+                     float* __restrict__ gun, float* __restrict__ gburn, float* __restrict__ glam0,
+                     float* __restrict__ glam1, double* __restrict__ partials, uint32_t* __restrict__ counter,
+                     double* __restrict__ gpc) {
+    __shared__ double red[kSweepWarps];
+    __shared__ bool am_last;
+    __shared__ Sw2Slot ring[kSweepWarps][kSw2Depth];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc = 0.0;
+    float accf = 0.f;
+    for (int64_t it = (int64_t)blockIdx.x * kSweepWarps + warp; it < n_items; it += (int64_t)gridDim.x * kSweepWarps) {
+        const int4 w = items[it];
+        const int e = w.x, y0 = w.y, x0 = w.z;
+        const int H = Hs[e], W = Ws[e];
+        const int64_t off = offs[e];
+        const int y1 = min(y0 + JWF_SW2_ROWS, H);
+        const int x = x0 - 2 + lane;
+        const bool out_col = lane >= 2 && lane <= JWF_SW2_COLS + 1 && x < W;
+        const int xo = lane == 0 ? x - 1 : x + 1;
+        const bool edge = lane == 0 || lane == 31;
+        const bool col = x >= 0 && x < W, col_o = edge && xo >= 0 && xo < W;
+        const int yb = y0 - 2;                            // first target row of step t + 1
+        // step t + 1: p_burn window rows y - 1, y, y + 1 (and the halo lanes' outer column)
+        float2 pa1 = sweep_pb(pburn1, mask1, off, yb - 1, x, H, W);
+        float2 pb1 = sweep_pb(pburn1, mask1, off, yb, x, H, W);
+        float2 pc1 = sweep_pb(pburn1, mask1, off, yb + 1, x, H, W);
+        float oa = 0.f, ob = 0.f, oc = 0.f;
+        if (edge) {
+            oa = sweep_pb(pburn1, mask1, off, yb - 1, xo, H, W).x;
+            ob = sweep_pb(pburn1, mask1, off, yb, xo, H, W).x;
+            oc = sweep_pb(pburn1, mask1, off, yb + 1, xo, H, W).x;
+        }
+        // step t (target row y - 1): window rows y - 2, y - 1, y
+        float2 pa0 = sweep_pb(pburn0, mask0, off, yb - 2, x, H, W);
+        float2 pb0 = sweep_pb(pburn0, mask0, off, yb - 1, x, H, W);
+        float2 pc0 = sweep_pb(pburn0, mask0, off, yb, x, H, W);
+        int64_t v_is = off + (int64_t)yb * W + x;
+        int64_t v = v_is;
+        for (int k = 0; k < kSw2Depth - 1; ++k, v_is += W)
+            sweep2_issue(ring[warp][k], lane, r, pun0, pburn0, mask0, pun1, pburn1, mask1, gun_out, gburn_out, v_is,
+                         yb + k, col, col_o, xo - x, H, W);
+        float h_prev = 0.f, h_cur = 0.f, h_next = 0.f;   // step t + 1 accumulators, rows y - 1, y, y + 1
+        float g_prev = 0.f, g_cur = 0.f, g_next = 0.f;   // step t accumulators, rows y - 2, y - 1, y
+        float ab2_prev = 0.f, m1_prev = 0.f;              // incoming a_b and step t + 1 mask of row y - 1
+        float au1_prev = 0.f;                             // step t + 1's dL/dp_un of row y - 1
+        float ab1_prev = 0.f;                             // step t + 1's dL/dp_burn of row y - 2
+        float rp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // rate row of y - 1
+        for (int y = yb; y <= y1 + 1; ++y, v += W, v_is += W) {
+            const int k = y - yb;
+            sweep2_issue(ring[warp][(k + kSw2Depth - 1) % kSw2Depth], lane, r, pun0, pburn0, mask0, pun1, pburn1,
+                         mask1, gun_out, gburn_out, v_is, y + kSw2Depth - 1, col, col_o, xo - x, H, W);
+            cp_async_wait_n<kSw2Depth - 1>();
+            const Sw2Slot& sl = ring[warp][k % kSw2Depth];
+            const float4 ra4 = sl.ra[lane], rb4 = sl.rb[lane];
+            const float pu1v = sl.pu1[lane], au2 = sl.au[lane], ab2 = sl.ab[lane];
+            const float pbn1 = sl.pbn1[lane], mn1 = sl.mn1[lane];
+            const float2 pn1 = make_float2(mask1 != nullptr ? pbn1 * (1.0f - mn1) : pbn1, mn1);
+            const float on = mask1 != nullptr ? sl.pbo1[lane] * (1.0f - sl.mo1[lane]) : sl.pbo1[lane];
+            const float pu0v = sl.pu0[lane];
+            const float pbn0 = sl.pbn0[lane], mn0 = sl.mn0[lane];
+            const float2 pn0 = make_float2(mask0 != nullptr ? pbn0 * (1.0f - mn0) : pbn0, mn0);
+            const float rv[8] = {ra4.x, ra4.y, ra4.z, ra4.w, rb4.x, rb4.y, rb4.z, rb4.w};
+            // ---- step t + 1, target row y ----
+            float h1;
+            float gun1;
+            {
+                float la = __shfl_up_sync(FULL, pa1.x, 1), lb = __shfl_up_sync(FULL, pb1.x, 1),
+                      lc = __shfl_up_sync(FULL, pc1.x, 1);
+                float ra_ = __shfl_down_sync(FULL, pa1.x, 1), rb_ = __shfl_down_sync(FULL, pb1.x, 1),
+                      rc_ = __shfl_down_sync(FULL, pc1.x, 1);
+                if (lane == 0) {
+                    la = oa;
+                    lb = ob;
+                    lc = oc;
+                }
+                if (lane == 31) {
+                    ra_ = oa;
+                    rb_ = ob;
+                    rc_ = oc;
+                }
+                const float src[8] = {lb, lc, pc1.x, rc_, rb_, ra_, pa1.x, la};
+                float lam = 0.f;
+#pragma unroll
+                for (int d = 0; d < 8; ++d) lam += src[d] * rv[d];
+                const bool valid = col && (unsigned)y < (unsigned)H;
+                h1 = 0.f;
+                gun1 = 0.f;
+                if (valid) {
+                    const float em = expf(-lam);
+                    const float p_ign = -expm1f(-lam);
+                    const float nb = ab2 - au2;
+                    const float pe = pu1v * em;
+                    h1 = pe != 0.f ? sat(nb * pe) : 0.f;
+                    gun1 = sat(p_ign != 0.f ? au2 + nb * p_ign : au2);
+                    if (out_col && y >= y0 && y < y1) {
+                        glam1[v] = h1;
+                        if (pb1.x != 0.f) accf += ab2 * pb1.x;
+                    }
+                }
+                float P[8];
+#pragma unroll
+                for (int d = 0; d < 8; ++d) P[d] = h1 * rv[d];
+                const float fr0 = __shfl_down_sync(FULL, P[0], 1), fr1 = __shfl_down_sync(FULL, P[1], 1),
+                            fr7 = __shfl_down_sync(FULL, P[7], 1);
+                const float fl3 = __shfl_up_sync(FULL, P[3], 1), fl4 = __shfl_up_sync(FULL, P[4], 1),
+                            fl5 = __shfl_up_sync(FULL, P[5], 1);
+                h_prev += P[6];
+                h_prev += fr7;
+                h_prev += fl5;
+                h_cur += fr0;
+                h_cur += fl4;
+                h_next += P[2];
+                h_next += fr1;
+                h_next += fl3;
+            }
+            // step t + 1's dL/dp_burn of row y - 1 is complete
+            float ab1 = p_continue != 0.f ? p_continue * ab2_prev + h_prev : h_prev;
+            if (mask1 != nullptr) {
+                const float keep = 1.0f - m1_prev;
+                ab1 = keep != 0.f ? ab1 * keep : 0.f;
+            }
+            ab1 = sat(ab1);
+            // ---- step t, target row y - 1 ----
+            {
+                const int yy = y - 1;
+                float la = __shfl_up_sync(FULL, pa0.x, 1), lb = __shfl_up_sync(FULL, pb0.x, 1),
+                      lc = __shfl_up_sync(FULL, pc0.x, 1);
+                const float ra_ = __shfl_down_sync(FULL, pa0.x, 1), rb_ = __shfl_down_sync(FULL, pb0.x, 1),
+                            rc_ = __shfl_down_sync(FULL, pc0.x, 1);
+                const float src[8] = {lb, lc, pc0.x, rc_, rb_, ra_, pa0.x, la};
+                float lam = 0.f;
+#pragma unroll
+                for (int d = 0; d < 8; ++d) lam += src[d] * rp[d];
+                const bool valid = col && (unsigned)yy < (unsigned)H;
+                float g = 0.f;
+                if (valid) {
+                    const float em = expf(-lam);
+                    const float p_ign = -expm1f(-lam);
+                    const float nb = ab1 - au1_prev;
+                    const float pe = pu0v * em;
+                    g = pe != 0.f ? sat(nb * pe) : 0.f;
+                    if (out_col && yy >= y0 && yy < y1) {
+                        gun[v - W] = sat(p_ign != 0.f ? au1_prev + nb * p_ign : au1_prev);
+                        glam0[v - W] = g;
+                        if (pb0.x != 0.f) accf += ab1 * pb0.x;
+                    }
+                }
+                float P[8];
+#pragma unroll
+                for (int d = 0; d < 8; ++d) P[d] = g * rp[d];
+                const float fr0 = __shfl_down_sync(FULL, P[0], 1), fr1 = __shfl_down_sync(FULL, P[1], 1),
+                            fr7 = __shfl_down_sync(FULL, P[7], 1);
+                const float fl3 = __shfl_up_sync(FULL, P[3], 1), fl4 = __shfl_up_sync(FULL, P[4], 1),
+                            fl5 = __shfl_up_sync(FULL, P[5], 1);
+                g_prev += P[6];
+                g_prev += fr7;
+                g_prev += fl5;
+                g_cur += fr0;
+                g_cur += fl4;
+                g_next += P[2];
+                g_next += fr1;
+                g_next += fl3;
+                // step t's dL/dp_burn of row y - 2 is complete
+                if (out_col && yy - 1 >= y0 && yy - 1 < y1) {
+                    float gb = p_continue != 0.f ? p_continue * ab1_prev + g_prev : g_prev;
+                    if (mask0 != nullptr) {
+                        const float keep = 1.0f - pa0.y;
+                        gb = keep != 0.f ? gb * keep : 0.f;
+                    }
+                    gburn[v - 2 * (int64_t)W] = sat(gb);
+                }
+            }
+            h_prev = h_cur;
+            h_cur = h_next;
+            h_next = 0.f;
+            g_prev = g_cur;
+            g_cur = g_next;
+            g_next = 0.f;
+            ab2_prev = ab2;
+            m1_prev = pb1.y;
+            au1_prev = gun1;
+            ab1_prev = ab1;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) rp[d] = rv[d];
+            pa1 = pb1;
+            pb1 = pc1;
+            pc1 = pn1;
+            oa = ob;
+            ob = oc;
+            oc = on;
+            pa0 = pb0;
+            pb0 = pc0;
+            pc0 = pn0;
+        }
+        jwf_cp_async_wait_all();
+        acc += (double)accf;
+        accf = 0.f;
+    }
+    if (gpc == nullptr) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kSweepWarps; ++i) s += red[i];
+        partials[blockIdx.x] = s;
+        __threadfence();
+        am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(&partials[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < kSweepWarps; ++i) tot += red[i];
+        *gpc += tot;
+        *counter = 0u;
+    }
+}
 }  // namespace
 
 cudaError_t jwf_launch_relaxed_fwd(const jwf_ctx* c, const float* pun, const float* pburn,
@@ -765,5 +1069,28 @@ cudaError_t jwf_launch_relaxed_bwd(jwf_ctx* c, const float* pun, const float* pb
             c->d_stiles, c->n_stiles, c->d_H, c->d_W, c->d_off, c->d_r, pun, pburn, mask, gun_out, gburn_out,
             c->P.p_continue, gun, gburn, glam, c->d_partials, c->d_red_counter, gpc);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t jwf_launch_relaxed_bwd2(jwf_ctx* c, const float* pun0, const float* pburn0, const float* mask0,
+                                    const float* pun1, const float* pburn1, const float* mask1,
+                                    const float* gun_out, const float* gburn_out, float* gun, float* gburn,
+                                    float* glam0, float* glam1, double* gpc, cudaStream_t s) {
+    static int per_sm[64] = {};
+    if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
+    if (per_sm[c->device] == 0) {
+        int b = 0;
+        const cudaError_t err =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_bwd_sweep2, kSweepWarps * 32, 0);
+        if (err != cudaSuccess) return err;
+        per_sm[c->device] = b > 0 ? b : 1;
+    }
+    int64_t grid = (c->n_s2tiles + kSweepWarps - 1) / kSweepWarps;
+    if (grid > (int64_t)c->num_sms * per_sm[c->device]) grid = (int64_t)c->num_sms * per_sm[c->device];
+    if (grid > c->partial_cap) grid = c->partial_cap;
+    if (grid < 1) grid = 1;
+    k_relaxed_bwd_sweep2<<<(unsigned)grid, kSweepWarps * 32, 0, s>>>(
+        c->d_s2tiles, c->n_s2tiles, c->d_H, c->d_W, c->d_off, c->d_r, pun0, pburn0, mask0, pun1, pburn1, mask1,
+        gun_out, gburn_out, c->P.p_continue, gun, gburn, glam0, glam1, c->d_partials, c->d_red_counter, gpc);
     return cudaGetLastError();
 }
