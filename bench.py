@@ -526,7 +526,12 @@ def bench_relaxed(args, D, dev, rank):
         gpc = torch.zeros(1, dtype=torch.float64, device=dev)
         out = {}
         two = (torch.empty((2,) + pu0.shape, device=dev), torch.empty((2,) + pu0.shape, device=dev))
-        for name in ("fwd", "fwd2", "bwd"):
+        PU2, PB2 = torch.stack([pu0, pu0]), torch.stack([pb0, pb0])
+        glam2 = torch.empty((2,) + pu0.shape, device=dev)
+        glam16 = torch.randn((16,) + pu0.shape, device=dev)
+        pb16 = torch.rand((16,) + pu0.shape, device=dev)
+        gr = torch.zeros((cells, 8), device=dev)
+        for name in ("fwd", "fwd2", "bwd", "bwd2", "acc16"):
             for i in range(n + 1):
                 if i == 1:
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -537,6 +542,13 @@ def bench_relaxed(args, D, dev, rank):
                 elif name == "fwd2":
                     # two steps in one pass (the rollout's forward)
                     sim.relaxed_fwd_steps(bufs[0][0], bufs[0][1], two[0], two[1])
+                elif name == "bwd2":
+                    # two adjoint steps in one pass (the rollout's backward)
+                    gs, gd = g[i % 2], g[(i + 1) % 2]
+                    sim.relaxed_bwd_steps(PU2, PB2, gs[0], gs[1], gd[0], gd[1], glam=glam2, gpc=gpc)
+                elif name == "acc16":
+                    # the rate adjoint of a 16-step block
+                    sim.rates_accumulate(glam16, pb16, gr)
                 else:
                     gs, gd = g[i % 2], g[(i + 1) % 2]
                     sim.relaxed_bwd(bufs[0][0], bufs[0][1], gs[0], gs[1], None, gd[0], gd[1], glam, gpc)
@@ -556,8 +568,10 @@ def bench_relaxed(args, D, dev, rank):
     k_plain = time_kernels()
     sim.set_relaxed_kernel(jwf.RELAXED_TILED)
     hbm, peak_kind = peaks()
-    fwd1_b, fwd_b, bwd_b, acc_b = 48, 28, 60, 12
-    ach_b = bwd_b * cells / k_tiled["bwd"] / 1e9
+    fwd1_b, fwd_b, bwd1_b, bwd_b, acc_b = 48, 28, 60, 36, 12
+    ach_b = 2 * bwd_b * cells / k_tiled["bwd2"] / 1e9
+    ach_b1 = bwd1_b * cells / k_tiled["bwd"] / 1e9
+    ach_acc = 16 * acc_b * cells / k_tiled["acc16"] / 1e9
     ach_f = fwd1_b * cells / k_tiled["fwd"] / 1e9
     ach_f2 = 2 * fwd_b * cells / k_tiled["fwd2"] / 1e9
     rate = D.world * cells * REL_T / t_keep
@@ -566,16 +580,27 @@ def bench_relaxed(args, D, dev, rank):
             "value": rate, "unit": "fwd+bwd cell-steps/s",
             "ms_per_step": t_keep * 1e3, "dtype": "f32",
             "memory_policy": "every state kept" if keep_all == 0 else "sqrt(T) checkpoints",
-            "path_bytes_model": f"{fwd_b + bwd_b + acc_b} B/cell-step ({fwd_b} two-step fwd + {bwd_b} fused "
-                                f"adjoint + {acc_b} rate-adjoint accumulation)",
+            "path_bytes_model": f"{fwd_b + bwd_b + acc_b} B/cell-step ({fwd_b} two-step fwd + {bwd_b} two-step "
+                                f"fused adjoint + {acc_b} rate-adjoint accumulation)",
             "path_gbs": round((fwd_b + bwd_b + acc_b) * rate / D.world / 1e9, 1),
             "path_frac": round((fwd_b + bwd_b + acc_b) * rate / D.world / 1e9 / hbm, 4),
             "roofline": {"bound": "hbm", "achieved": round(ach_b, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(ach_b / hbm, 4), "peak_source": peak_kind,
-                         "traffic": kernel_traffic("k_relaxed_bwd_sweep", "paper_2512_06102_gb300/csrc/k_relaxed.cu"),
-                         "kernel": "k_relaxed_bwd_sweep", "kernel_us": round(k_tiled["bwd"] * 1e6, 2),
-                         "bytes_model": "60 B/cell-step (32 B rates, 8 B state, 8 B adjoint in, 8 B adjoint "
-                                        "out, 4 B glam)"},
+                         "traffic": kernel_traffic("k_relaxed_bwd_sweep2", "paper_2512_06102_gb300/csrc/k_relaxed.cu"),
+                         "kernel": "k_relaxed_bwd_sweep2 (two adjoint steps a pass)",
+                         "kernel_us": round(k_tiled["bwd2"] * 1e6, 2),
+                         "bytes_model": "36 B/cell-step (per two steps: 32 B rates, 16 B states, 8 B adjoint in, "
+                                        "8 B adjoint out, 8 B glam)"},
+            "roofline_bwd1": {"bound": "hbm", "achieved": round(ach_b1, 1), "peak": hbm, "unit": "GB/s",
+                              "frac": round(ach_b1 / hbm, 4), "kernel": "k_relaxed_bwd_sweep (one step, "
+                              "jwf_step_relaxed_bwd)", "kernel_us": round(k_tiled["bwd"] * 1e6, 2),
+                              "bytes_model": "60 B/cell-step (32 B rates, 8 B state, 8 B adjoint in, 8 B adjoint "
+                                             "out, 4 B glam)"},
+            "roofline_acc": {"bound": "hbm", "achieved": round(ach_acc, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(ach_acc / hbm, 4), "kernel": "k_rates_accumulate (16-step block)",
+                             "kernel_us": round(k_tiled["acc16"] * 1e6, 2),
+                             "bytes_model": "12 B/cell-step (4 B glam, 4 B p_burn; 64 B rate adjoint read and "
+                                            "written per 16 steps)"},
             "roofline_fwd": {"bound": "hbm", "achieved": round(ach_f, 1), "peak": hbm, "unit": "GB/s",
                              "frac": round(ach_f / hbm, 4), "kernel": "k_relaxed_fwd_tiled",
                              "kernel_us": round(k_tiled["fwd"] * 1e6, 2),
@@ -1000,7 +1025,7 @@ def run_profile(case: str):
     L2, a few GB on the device at most): 'resident' = 1024 grids of 128^2, one
     200-step episode with drops on the fused resident kernel; 'relaxed' = 256
     grids of 128^2, one tiled relaxed forward step, one two-step forward pass,
-    sixteen adjoint steps and one 16-step rate-adjoint accumulation; 'tiled' = 2 grids of 4096^2, 800 steps with
+    two one-step adjoints, sixteen adjoint steps in two-step passes and one 16-step rate-adjoint accumulation; 'tiled' = 2 grids of 4096^2, 800 steps with
     drops on the fused tiled kernel (256 threads a tile, 16 steps a round)."""
     import torch
 
@@ -1041,8 +1066,12 @@ def run_profile(case: str):
         ou, ob = sim.relaxed_fwd(pu0, pb0)
         two = (torch.empty((2, sim.cells), device=dev), torch.empty((2, sim.cells), device=dev))
         sim.relaxed_fwd_steps(pu0, pb0, two[0], two[1])
-        for t in range(16):
+        for t in range(2):
             sim.relaxed_bwd(pu0, pb0, au, ab, None, None, None, glam[t], gpc)
+        # sixteen adjoint steps in two-step passes (the rollout's backward)
+        gu16, gb16 = torch.empty_like(pu0), torch.empty_like(pu0)
+        sim.relaxed_bwd_steps(torch.stack([pu0] * 16), torch.stack([pb0] * 16), au, ab, gu16, gb16, glam=glam,
+                              gpc=gpc)
         gr = torch.zeros((sim.cells, 8), device=dev)
         sim.rates_accumulate(glam, torch.stack([pb0] * 16), gr)
         torch.cuda.synchronize()
