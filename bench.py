@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-rollout", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-tanker", action="store_true")
-    ap.add_argument("--profile", choices=["resident", "relaxed", "tiled"], default=None,
+    ap.add_argument("--profile", choices=["resident", "relaxed", "tiled", "plain"], default=None,
                     help="run one small case of a kernel family once (for ncu captures); prints no bench line")
     return ap.parse_args()
 
@@ -1026,7 +1026,8 @@ def run_profile(case: str):
     200-step episode with drops on the fused resident kernel; 'relaxed' = 256
     grids of 128^2, one tiled relaxed forward step, one two-step forward pass,
     two one-step adjoints, sixteen adjoint steps in two-step passes and one 16-step rate-adjoint accumulation; 'tiled' = 2 grids of 4096^2, 800 steps with
-    drops on the fused tiled kernel (256 threads a tile, 16 steps a round)."""
+    drops on the fused tiled kernel (256 threads a tile, 16 steps a round); 'plain' = the batched
+    workload (4096 grids of 128^2, probability table) for 20 steps of the plain one-launch-per-step path."""
     import torch
 
     from paper_2512_06102_gb300 import build, jwf, scenarios
@@ -1034,7 +1035,19 @@ def run_profile(case: str):
     build.build()
     dev = torch.device("cuda", 0)
     to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    if case in ("resident", "tiled"):
+    if case == "plain":
+        # the plain one-launch-per-step comparator on the batched workload (table path)
+        scn = scenarios.make_scenario(SIDE, SIDE, N=N_ENVS, seed=0)
+        drops = scenarios.drops(20, scn.H, scn.W, seed=0)
+        sim = jwf.Sim(SIDE, SIDE, n_envs=N_ENVS, n_classes=scenarios.N_CLASSES, seed=0)
+        sim.set_params(scn.params)
+        sim.set_kernel(jwf.KERNEL_PLAIN)
+        sim.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+        sim.load_state(to(scn.F0))
+        out = sim.step(20, to(drops))
+        torch.cuda.synchronize()
+        print(f"profile case plain: burned after 20 steps {int(out[1][-1].sum())}")
+    elif case in ("resident", "tiled"):
         N, S, K = (1024, SIDE, EPISODE) if case == "resident" else (2, BIG_SIDE, 800)
         scn = scenarios.make_scenario(S, S, N=N, seed=0)
         drops = scenarios.drops(K, scn.H, scn.W, seed=0)

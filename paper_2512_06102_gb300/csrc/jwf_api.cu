@@ -49,7 +49,7 @@ void free_all(jwf_ctx* c) {
                     c->d_tiles4, c->d_env_tiles, c->d_tact[0], c->d_tact[1], c->d_tsync, c->d_tburnt,
                     c->d_tcnt, c->d_rtiles, c->d_r2tiles, c->d_adj, c->d_wser, c->d_agent_drops, c->d_agent_cnt,
                     c->d_agent_done, c->d_stiles, c->d_tmaps, c->d_tma_ok, c->d_order_dyn, c->d_lastb,
-                    c->d_tplan, c->d_s2tiles};
+                    c->d_tplan, c->d_s2tiles, c->d_ptiles};
     for (void* p : ptrs)
         if (p != nullptr) cudaFree(p);
 }
@@ -135,6 +135,13 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     for (int32_t e = 0; e < N; ++e)
         if ((c->off[e] & 31) != 0 || (c->W[e] & 31) != 0) c->packed_aligned = false;
     c->n_tiles = (int64_t)tiles.size();
+    std::vector<int2> ptiles;
+    for (int32_t e = 0; e < N; ++e) {
+        const int64_t nseg = (int64_t)c->H[e] * ((c->W[e] + JWF_PLAIN_SEG - 1) / JWF_PLAIN_SEG);
+        for (int64_t s = 0; s < nseg; s += (int64_t)JWF_TILE * JWF_PLAIN_SEGS_PER_THREAD)
+            ptiles.push_back(make_int2(e, (int)s));
+    }
+    c->n_ptiles = (int64_t)ptiles.size();
     // tiles of the tiled path: (env, tile row, tile column) and per-env layout
     std::vector<int4> tiles4, env_tiles(N);
     for (int32_t e = 0; e < N; ++e) {
@@ -204,6 +211,7 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = dev_alloc(&c->d_order_dyn, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_lastb, N);
     if (err == cudaSuccess) err = dev_alloc(&c->d_tiles, tiles.size());
+    if (err == cudaSuccess) err = dev_alloc(&c->d_ptiles, ptiles.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_state[0], (size_t)c->cells);
     if (err == cudaSuccess) err = dev_alloc(&c->d_state[1], (size_t)c->cells);
     if (err == cudaSuccess) err = dev_alloc(&c->d_F0, (size_t)c->cells);
@@ -255,6 +263,8 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = cudaMemcpy(c->d_off, c->off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_order, order.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(c->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(c->d_ptiles, ptiles.data(), ptiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemset(c->d_t, 0, N * sizeof(int32_t));
     if (err == cudaSuccess) err = cudaMemset(c->d_episode, 0, N * sizeof(int32_t));
     if (err == cudaSuccess) err = cudaMemset(c->d_cnt, 0, 2 * N * sizeof(int32_t));

@@ -142,6 +142,10 @@ struct JwfDevParams {
 
 // Per-cell kernels walk blocks of JWF_TILE consecutive cells of one env.
 #define JWF_TILE 256
+// The plain step: a thread steps row segments of JWF_PLAIN_SEG cells, a block
+// JWF_PLAIN_SEGS_PER_THREAD x JWF_TILE consecutive segments of one env.
+#define JWF_PLAIN_SEG 16
+#define JWF_PLAIN_SEGS_PER_THREAD 4
 // The tiled relaxed kernels walk 2-D tiles of JWF_RT_ROWS x JWF_RT_COLS cells.
 #define JWF_RT_ROWS 16
 #define JWF_RT_COLS 64
@@ -189,6 +193,8 @@ struct jwf_ctx {
     int32_t reorder_steps = 12;          // split resident launches after this many steps (0: never)
     int2* d_tiles = nullptr;             // (env, first local cell) per JWF_TILE block
     int64_t n_tiles = 0;
+    int2* d_ptiles = nullptr;            // (env, first row segment) per plain-step block
+    int64_t n_ptiles = 0;
     uint8_t* d_state[2] = {nullptr, nullptr};
     int cur = 0;                         // index of the current state buffer
     uint8_t* d_F0 = nullptr;

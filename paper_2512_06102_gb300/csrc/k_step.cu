@@ -13,18 +13,6 @@
 
 namespace {
 
-// ---------------------------------------------------------------------------
-// helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool in_drop(int y, int x, int cx, int cy, int R) {
-    return cx >= 0 && cy >= 0 && abs(y - cy) <= R && abs(x - cx) <= R;
-}
-
-// state after the action of this step (burning under the drop -> burned)
-__device__ __forceinline__ uint8_t acted(uint8_t s, int y, int x, int cx, int cy, int R) {
-    return (s == 2 && in_drop(y, x, cx, cy, R)) ? (uint8_t)3 : s;
-}
-
 __global__ void k_load(const int64_t cells, const uint8_t* __restrict__ F0, uint8_t* __restrict__ Fc,
                        uint8_t* __restrict__ F0c, int32_t* __restrict__ t, int32_t* __restrict__ ep,
                        int32_t N) {
@@ -157,10 +145,67 @@ __global__ void k_action(const int64_t cells, const uint8_t* __restrict__ mask, 
 }
 
 // ---------------------------------------------------------------------------
-// Plain step: one thread per cell, reads F_t (global), writes F_{t+1}.
-// Counts go to cnt[0][e] (burning) and cnt[1][e] (burned) by warp-aggregated
-// atomics; k_finalize turns them into the per-step outputs.
+// Plain step: one launch per step, state in global memory (reads F_t, writes
+// F_{t+1}), the q table read for the cells that can ignite.  A thread steps a
+// segment of up to 16 cells of one row: the three rows around it are read as
+// 16-byte vectors where they are aligned (byte by byte otherwise) and the
+// burning sources after the step's drop become bit masks, so that a cell's
+// eight sources are bit tests.  Counts: one shared-memory reduction and one
+// atomic per block and counter into cnt[0][e] (burning), cnt[1][e] (burned);
+// k_finalize turns them into the per-step outputs.
 // ---------------------------------------------------------------------------
+constexpr int kSeg = JWF_PLAIN_SEG;
+
+// 4 states (one word) -> 4-bit mask of the bytes equal to `pattern`
+__device__ __forceinline__ uint32_t eq4(uint32_t w, uint32_t pattern) {
+    const uint32_t m = __vcmpeq4(w, pattern);
+    return (((m & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
+}
+// 4-bit mask -> 4 bytes of 0 / 1
+__device__ __forceinline__ uint32_t spread4(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
+
+// Row y over columns x0 - 1 .. x0 + kSeg: masks (bit k + 1 = column x0 + k,
+// bit 0 = x0 - 1, bit n + 1 = x0 + n) of the cells in state 1, 2 and 3;
+// rows and columns outside the grid are 0
+struct RowBits {
+    uint32_t c, b, d;
+};
+__device__ __forceinline__ RowBits row_bits(const uint8_t* __restrict__ Fe, int y, int x0, int n, int H, int W,
+                                            bool vec) {
+    RowBits r = {0u, 0u, 0u};
+    if (y < 0 || y >= H) return r;
+    const uint8_t* row = Fe + (int64_t)y * W;
+    if (vec) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + x0));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            r.c |= eq4(w[j], 0x01010101u) << (4 * j + 1);
+            r.b |= eq4(w[j], 0x02020202u) << (4 * j + 1);
+            r.d |= eq4(w[j], 0x03030303u) << (4 * j + 1);
+        }
+    } else {
+        for (int k = 0; k < n; ++k) {
+            const uint32_t st = row[x0 + k];
+            r.c |= (uint32_t)(st == 1) << (k + 1);
+            r.b |= (uint32_t)(st == 2) << (k + 1);
+            r.d |= (uint32_t)(st == 3) << (k + 1);
+        }
+    }
+    if (x0 > 0 && row[x0 - 1] == 2) r.b |= 1u;
+    if (x0 + n < W && row[x0 + n] == 2) r.b |= 1u << (n + 1);
+    return r;
+}
+
+// bits [lo, hi] of an 18-bit row mask (columns cx - R .. cx + R) doused by the
+// step's drop, or 0 when the row or the drop is out of reach
+__device__ __forceinline__ uint32_t drop_mask(int y, int x0, int cx, int cy, int R) {
+    if (cx < 0 || cy < 0 || abs(y - cy) > R) return 0u;
+    const int lo = max(cx - R - x0 + 1, 0), hi = min(cx + R - x0 + 1, kSeg + 1);
+    if (lo > hi) return 0u;
+    return ((hi - lo == 31) ? 0xffffffffu : ((1u << (hi - lo + 1)) - 1u)) << lo;
+}
+
 __global__ void __launch_bounds__(JWF_TILE)
 k_step_plain(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
              const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs, int32_t N,
@@ -168,62 +213,112 @@ k_step_plain(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
              const float* __restrict__ q, const int32_t* __restrict__ drops,
              const int32_t* __restrict__ tcur, const int32_t* __restrict__ episode,
              uint32_t key0, uint32_t key1, float p_continue, int R, int32_t* __restrict__ cnt) {
+    __shared__ int32_t s_n[2];
     const int2 tile = tiles[blockIdx.x];
     const int e = tile.x;
     const int W = Ws[e], H = Hs[e];
-    const int local = tile.y + (int)threadIdx.x;
-    const bool valid = local < H * W;
+    const int segs = (W + kSeg - 1) / kSeg;
+    if (threadIdx.x < 2) s_n[threadIdx.x] = 0;
+    __syncthreads();
     int cx = -1, cy = -1;
     if (drops != nullptr) {
         cx = drops[2 * e];
         cy = drops[2 * e + 1];
     }
-    uint8_t nxt = 0;
-    if (valid) {
-        const int64_t off = offs[e];
-        const int y = local / W, x = local - (local / W) * W;
-        const uint8_t s = acted(Fin[off + local], y, x, cx, cy, R);
-        nxt = s;
-        const uint32_t t = (uint32_t)tcur[e];
-        const uint32_t ep4 = 4u * (uint32_t)episode[e];
-        if (s == 1) {
-            uint32_t dm = 0;
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const int uy = y - jwf_dr(d), ux = x - jwf_dx(d);
-                if (uy < 0 || uy >= H || ux < 0 || ux >= W) continue;
-                const uint8_t su = acted(Fin[off + (int64_t)uy * W + ux], uy, ux, cx, cy, R);
-                if (su == 2) dm |= 1u << d;
+    const int64_t off = offs[e];
+    const uint32_t t = (uint32_t)tcur[e];
+    const uint32_t ep4 = 4u * (uint32_t)episode[e];
+    const uint8_t* Fe = Fin + off;
+    int nb = 0, nd = 0;
+    // the block's JWF_PLAIN_SEGS_PER_THREAD x JWF_TILE consecutive segments of the env
+#pragma unroll 1
+    for (int i = 0; i < JWF_PLAIN_SEGS_PER_THREAD; ++i) {
+        const int u = tile.y + i * JWF_TILE + (int)threadIdx.x;      // segment of the env
+        if (u >= H * segs) break;
+        const int y = u / segs;
+        const int x0 = (u - y * segs) * kSeg;
+        const int n = min(kSeg, W - x0);
+        const uint32_t nmask = n == 32 ? 0xffffffffu : ((1u << n) - 1u);
+        // rows start on 16-byte boundaries and the segment is whole
+        const bool vec = n == kSeg && ((off | (int64_t)W) & 15) == 0;
+        const RowBits ru = row_bits(Fe, y - 1, x0, n, H, W, vec);
+        const RowBits rc = row_bits(Fe, y, x0, n, H, W, vec);
+        const RowBits rd = row_bits(Fe, y + 1, x0, n, H, W, vec);
+        // burning sources after the step's drop (burning under it -> burned)
+        const uint32_t mu = ru.b & ~drop_mask(y - 1, x0, cx, cy, R);
+        const uint32_t mdr = drop_mask(y, x0, cx, cy, R);
+        const uint32_t mc = rc.b & ~mdr;
+        const uint32_t md = rd.b & ~drop_mask(y + 1, x0, cx, cy, R);
+        // the segment's own cells (bit k = column x0 + k)
+        const uint32_t own_c = (rc.c >> 1) & nmask;
+        const uint32_t own_b = (mc >> 1) & nmask;                           // burning after the drop
+        const uint32_t own_d = ((rc.d | (rc.b & mdr)) >> 1) & nmask;        // burned, or doused now
+        // can-burn cells with a burning source: bit k of a row mask is column
+        // x0 + k - 1, so cell k's sources sit at bits k, k + 1, k + 2
+        const uint32_t any = mc | (mc >> 2) | md | (md >> 1) | (md >> 2) | mu | (mu >> 1) | (mu >> 2);
+        const uint32_t cand = own_c & any;
+        uint32_t ign = 0u, outb = 0u;
+        const uint32_t row0 = (uint32_t)(y * W + x0);
+        for (uint32_t m = cand; m != 0u; m &= m - 1u) {
+            const int k = __ffs(m) - 1;
+            // sources of directions 0..7: (y, x-1), (y+1, x-1), (y+1, x), (y+1, x+1), (y, x+1),
+            // (y-1, x+1), (y-1, x), (y-1, x-1)
+            const uint32_t dm = ((mc >> k) & 1u) | (((md >> k) & 1u) << 1) | (((md >> (k + 1)) & 1u) << 2) |
+                                (((md >> (k + 2)) & 1u) << 3) | (((mc >> (k + 2)) & 1u) << 4) |
+                                (((mu >> (k + 2)) & 1u) << 5) | (((mu >> (k + 1)) & 1u) << 6) |
+                                (((mu >> k) & 1u) << 7);
+            const uint32_t local = row0 + (uint32_t)k;
+            const float4* q4 = reinterpret_cast<const float4*>(q + (off + local) * 8);
+            bool hit = false;
+            if (dm & 0x0Fu) {
+                const uint4 r = jwf_philox(make_uint4(local, t, (uint32_t)e, ep4 + 0u), key0, key1);
+                const float4 qa = __ldg(q4);
+                hit |= ((dm & 1u) && jwf_u24(r.x) < qa.x) || ((dm & 2u) && jwf_u24(r.y) < qa.y) ||
+                       ((dm & 4u) && jwf_u24(r.z) < qa.z) || ((dm & 8u) && jwf_u24(r.w) < qa.w);
             }
-            if (dm != 0) {
-                const float4* q4 = reinterpret_cast<const float4*>(q + (off + local) * 8);
-                bool ign = false;
-                if (dm & 0x0Fu) {
-                    const uint4 u = jwf_philox(make_uint4((uint32_t)local, t, (uint32_t)e, ep4 + 0u), key0, key1);
-                    const float4 qa = __ldg(q4);
-                    ign |= ((dm & 1u) && jwf_u24(u.x) < qa.x) || ((dm & 2u) && jwf_u24(u.y) < qa.y) ||
-                           ((dm & 4u) && jwf_u24(u.z) < qa.z) || ((dm & 8u) && jwf_u24(u.w) < qa.w);
-                }
-                if (dm & 0xF0u) {
-                    const uint4 u = jwf_philox(make_uint4((uint32_t)local, t, (uint32_t)e, ep4 + 1u), key0, key1);
-                    const float4 qb = __ldg(q4 + 1);
-                    ign |= ((dm & 16u) && jwf_u24(u.x) < qb.x) || ((dm & 32u) && jwf_u24(u.y) < qb.y) ||
-                           ((dm & 64u) && jwf_u24(u.z) < qb.z) || ((dm & 128u) && jwf_u24(u.w) < qb.w);
-                }
-                if (ign) nxt = 2;
+            if (!hit && (dm & 0xF0u)) {
+                const uint4 r = jwf_philox(make_uint4(local, t, (uint32_t)e, ep4 + 1u), key0, key1);
+                const float4 qb = __ldg(q4 + 1);
+                hit |= ((dm & 16u) && jwf_u24(r.x) < qb.x) || ((dm & 32u) && jwf_u24(r.y) < qb.y) ||
+                       ((dm & 64u) && jwf_u24(r.z) < qb.z) || ((dm & 128u) && jwf_u24(r.w) < qb.w);
             }
-        } else if (s == 2) {
-            const uint4 u = jwf_philox(make_uint4((uint32_t)local, t, (uint32_t)e, ep4 + 2u), key0, key1);
-            nxt = (jwf_u24(u.x) < p_continue) ? (uint8_t)2 : (uint8_t)3;
+            if (hit) ign |= 1u << k;
         }
-        Fout[off + local] = nxt;
+        for (uint32_t m = own_b; m != 0u; m &= m - 1u) {
+            const int k = __ffs(m) - 1;
+            const uint4 r = jwf_philox(make_uint4(row0 + (uint32_t)k, t, (uint32_t)e, ep4 + 2u), key0, key1);
+            if (!(jwf_u24(r.x) < p_continue)) outb |= 1u << k;
+        }
+        // the next states: 1 can burn, 2 burning, 3 burned (0 stays 0)
+        const uint32_t s1 = own_c & ~ign;
+        const uint32_t s2 = (own_b & ~outb) | ign;
+        const uint32_t s3 = own_d | outb;
+        nb += __popc(s2);
+        nd += __popc(s3);
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int sh = 4 * j;
+            w[j] = spread4((s1 >> sh) & 0xFu) + 2u * spread4((s2 >> sh) & 0xFu) + 3u * spread4((s3 >> sh) & 0xFu);
+        }
+        uint8_t* dst = Fout + off + (int64_t)y * W + x0;
+        if (vec) {
+            *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            for (int k = 0; k < n; ++k) dst[k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+        }
     }
-    // a block never straddles two envs
-    const uint32_t b2 = __ballot_sync(0xffffffffu, valid && nxt == 2);
-    const uint32_t b3 = __ballot_sync(0xffffffffu, valid && nxt == 3);
+    // a block never straddles two envs: one atomic per counter
+    nb = __reduce_add_sync(0xffffffffu, nb);
+    nd = __reduce_add_sync(0xffffffffu, nd);
     if ((threadIdx.x & 31) == 0) {
-        if (b2) atomicAdd(&cnt[e], __popc(b2));
-        if (b3) atomicAdd(&cnt[N + e], __popc(b3));
+        if (nb) atomicAdd(&s_n[0], nb);
+        if (nd) atomicAdd(&s_n[1], nd);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_n[0]) atomicAdd(&cnt[e], s_n[0]);
+        if (s_n[1]) atomicAdd(&cnt[N + e], s_n[1]);
     }
 }
 
@@ -312,8 +407,8 @@ cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, i
     for (int32_t st = 0; st < k; ++st) {
         const uint8_t* Fin = c->d_state[c->cur];
         uint8_t* Fout = c->d_state[c->cur ^ 1];
-        k_step_plain<<<(unsigned)c->n_tiles, JWF_TILE, 0, s>>>(
-            c->d_tiles, c->d_H, c->d_W, c->d_off, c->N, Fin, Fout, c->d_q,
+        k_step_plain<<<(unsigned)c->n_ptiles, JWF_TILE, 0, s>>>(
+            c->d_ptiles, c->d_H, c->d_W, c->d_off, c->N, Fin, Fout, c->d_q,
             drops ? drops + (int64_t)st * c->N * 2 : nullptr, c->d_t, c->d_episode, key0, key1,
             c->P.p_continue, c->drop_radius, c->d_cnt);
         const int64_t o = (int64_t)st * c->N;
