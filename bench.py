@@ -44,6 +44,7 @@ REL_ENVS, REL_T = 256, 100
 RAG_ENVS, RAG_T, RAG_TMAX = 10000, 500, 200
 BIG_ENVS, BIG_SIDE, BIG_T = 8, 4096, 1000
 TANK_ENVS, TANK_SIDE, TANK_T = 16384, 20, 500
+CAL_ENVS, CAL_T, CAL_ITERS, CAL_ITERS_1000 = 256, 100, 40, 2
 METRIC = "CA cell-updates/s at 4096x128^2 (200-step episode with tanker drops)"
 CPU_SAMPLE_ENVS = 48
 REF_PER_CORE = 4            # grids per host process and step of the reference arm
@@ -67,6 +68,7 @@ def parse():
     ap.add_argument("--no-rollout", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-tanker", action="store_true")
+    ap.add_argument("--no-calibrate", action="store_true")
     ap.add_argument("--profile", choices=["resident", "relaxed", "tiled", "plain"], default=None,
                     help="run one small case of a kernel family once (for ncu captures); prints no bench line")
     return ap.parse_args()
@@ -432,6 +434,9 @@ def run_ours(args):
     tank = None
     if not args.no_tanker:
         tank = bench_tanker(args, D, dev, rank)
+    cal = None
+    if not args.no_calibrate:
+        cal = bench_calibrate(args, D, dev, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -463,6 +468,8 @@ def run_ours(args):
         line["large"] = big
     if tank is not None:
         line["tanker"] = tank
+    if cal is not None:
+        line["calibrate"] = cal
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
@@ -622,6 +629,89 @@ def bench_relaxed(args, D, dev, rank):
                             "adjoint_speedup_vs_unfused_pair": round(k_plain["bwd"] / k_tiled["bwd"], 2)}}
 
 
+def bench_calibrate(args, D, dev, rank):
+    """Gradient-based calibration (Section 4) at the differentiation
+    workload's size: 256 grids of 128 x 128, targets = burn maps of the
+    stochastic step (mean over 5 seeds) from hidden parameters (the defaults
+    with p_base and the wind and slope coefficients scaled by U(0.7, 1.3) and
+    the burnable classes' mu_veg shifted by U(-0.1, 0.1), seeded), Adam on the
+    relaxed rollout from the defaults (T = 100, every state kept; the default
+    free set: p_base, alpha_w1, alpha_w2, alpha_s and mu_veg).  Reports fit
+    iterations/s (forward, backward, loss and update, host included), the loss
+    and the fitted, hidden and starting coefficients; then a few iterations at
+    T = 1000 with sqrt(T) checkpoints."""
+    import time
+
+    import torch
+
+    from paper_2512_06102_gb300 import calibrate, jwf, scenarios
+
+    scn = scenarios.make_scenario(SIDE, SIDE, N=CAL_ENVS, seed=300 + rank)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    scene = (to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+    F0 = to(scn.F0)
+    C = scenarios.N_CLASSES
+    rng = np.random.default_rng(301 + rank)
+    truth = scenarios.Params()
+    for name in ("p_base", "alpha_w1", "alpha_w2", "alpha_s"):
+        setattr(truth, name, float(getattr(truth, name)) * float(rng.uniform(0.7, 1.3)))
+    burnable = scenarios.burnable_classes(truth.mu_den)
+    mv = np.array(truth.mu_veg, np.float32)
+    mv[burnable] += rng.uniform(-0.1, 0.1, size=int(np.sum(burnable))).astype(np.float32)
+    truth.mu_veg = mv
+    target = calibrate.burn_maps(SIDE, SIDE, CAL_ENVS, truth, scene, F0, CAL_T)
+    start = calibrate.theta_of(scenarios.Params(), C)
+    sim = jwf.Sim(SIDE, SIDE, n_envs=CAL_ENVS, n_classes=C, keep_rates=True)
+    sim.set_params(scenarios.Params())
+
+    def run(T, iters, ckpt=None):
+        torch.cuda.synchronize()
+        D.barrier()
+        t0 = time.perf_counter()
+        th, ls = calibrate.fit(sim, scene, F0, target, start, T, iters=iters, ckpt_every=ckpt)
+        torch.cuda.synchronize()
+        return D.max(time.perf_counter() - t0), th, ls
+
+    run(CAL_T, 2)                                   # warm-up
+    t_fit, theta, losses = run(CAL_T, CAL_ITERS)
+    t_1000, _, losses_1000 = run(1000, CAL_ITERS_1000, "sqrt")
+    # no model mismatch: targets from the relaxed rollout itself with the
+    # hidden coefficients, the four coefficients free
+    from paper_2512_06102_gb300 import relaxed as rlx
+    pb0 = (F0 == 2).float()
+    with torch.no_grad():
+        ou, _ = rlx.rollout(calibrate.theta_of(truth, C), 1.0 - pb0, pb0, sim, scene, CAL_T)
+    rtarget = (1.0 - ou).clamp(0.0, 1.0)
+    free4 = torch.zeros_like(start)
+    free4[0:4] = 1.0
+    theta_r, losses_r = calibrate.fit(sim, scene, F0, rtarget, start, CAL_T, iters=3 * CAL_ITERS, free=free4)
+    with torch.no_grad():
+        floor = float(torch.nn.functional.binary_cross_entropy(rtarget, rtarget))
+    sim.close()
+    names = ("p_base", "alpha_w1", "alpha_w2", "alpha_s")
+    coef = {n: {"start": round(float(start[i]), 5), "hidden": round(float(getattr(truth, n)), 5),
+                "fitted": round(float(theta[i]), 5)} for i, n in enumerate(names)}
+    return {"metric": "calibration fit iterations/s at 256x128^2, T=100 (Adam on the relaxed rollout)",
+            "value": CAL_ITERS / t_fit, "unit": "iterations/s", "iterations": CAL_ITERS,
+            "ms_per_iteration": round(t_fit / CAL_ITERS * 1e3, 3),
+            "fwd_bwd_cell_steps_per_s": D.world * CAL_ENVS * SIDE * SIDE * CAL_T * CAL_ITERS / t_fit,
+            "loss_first": round(losses[0], 6), "loss_last": round(losses[-1], 6),
+            "target_mean_burned": round(float(target.mean()), 5), "coefficients": coef,
+            "mu_veg_fitted_minus_hidden_max_abs": round(float(np.max(np.abs(
+                theta[6:6 + C].numpy()[burnable] - np.asarray(truth.mu_veg, np.float64)[burnable]))), 5),
+            "relaxed_targets": {"iterations": 3 * CAL_ITERS, "loss_first": round(losses_r[0], 6),
+                                "loss_last": round(losses_r[-1], 6), "loss_floor": round(floor, 6),
+                                "coefficients": {n: {"start": round(float(start[i]), 5),
+                                                     "hidden": round(float(getattr(truth, n)), 5),
+                                                     "fitted": round(float(theta_r[i]), 5)}
+                                                 for i, n in enumerate(names)}},
+            "T1000_sqrt_checkpoints": {"iterations": CAL_ITERS_1000,
+                                       "ms_per_iteration": round(t_1000 / CAL_ITERS_1000 * 1e3, 3),
+                                       "loss_first": round(losses_1000[0], 6)},
+            "note": "targets come from the stochastic step; the mean-field relaxed model is not its multi-step "
+                    "expectation, so the fitted coefficients need not equal the hidden ones"}
+
+
 def bench_large(args, D, dev, rank):
     """8 grids of 4096 x 4096, one 1000-step episode with a random 3x3 drop per
     grid and step, on the tiled temporally blocked path: rates evaluated per
@@ -682,6 +772,29 @@ def bench_large(args, D, dev, rank):
         sim.step(BIG_T, dr)
 
     t_table = timed(table_episode, max(2, args.steps))
+    # the states 2-bit packed at the boundary: the initial fires in and the
+    # final state out (a quarter of the bytes; inside, the kernels keep one
+    # byte a cell), and the same episode run from the packed initial state
+    sim.set_kernel(jwf.KERNEL_TILED_FUSED, th)
+    P0 = jwf.pack_states(F0)
+    Pout = torch.zeros_like(P0)
+
+    def packed_io():
+        sim.load_state_packed(P0)
+        sim.state_packed(Pout)
+
+    F0u = torch.empty_like(F0)
+    t_pack = timed(lambda: jwf.pack_states(F0, P0), 5)
+    t_unpack = timed(lambda: jwf.unpack_states(P0, cells, F0u), 5)
+    t_io_packed = timed(packed_io, 5)
+    t_io_u8 = timed(lambda: (sim.load_state(F0), sim.state_views()[0].clone()), 5)
+
+    def packed_episode():
+        sim.load_state_packed(P0)
+        sim.step(BIG_T, dr)
+        sim.state_packed(Pout)
+
+    t_packed_ep = timed(packed_episode, max(2, args.steps))
     sim.set_kernel(jwf.KERNEL_PLAIN)
     t_plain200 = timed(lambda: sim.step(200, dr[:200]), 1)
     sim.close()
@@ -702,6 +815,13 @@ def bench_large(args, D, dev, rank):
                                "unit": "T lane-ops/s", "frac": round(ops / t_fused / 1e12 / peak_ops, 4),
                                "work": {"pairs": pairs, "philox_blocks_candidates": blocks, "burning_draws": draws,
                                         "word_steps": words}},
+            "packed_2bit": {"bytes_per_state": int(P0.numel()), "u8_bytes_per_state": cells,
+                            "pack_ms": round(t_pack * 1e3, 3), "unpack_ms": round(t_unpack * 1e3, 3),
+                            "load_and_read_packed_ms": round(t_io_packed * 1e3, 3),
+                            "load_and_read_u8_ms": round(t_io_u8 * 1e3, 3),
+                            "episode_packed_in_out_ms": round(t_packed_ep * 1e3, 3),
+                            "note": "states travel 2-bit packed at the boundary; the tiled kernel keeps one byte a "
+                                    "cell inside (its region copies are a small share of the episode)"},
             "comparators": {"plain_one_launch_per_step_ms_per_1000": round(t_plain200 * 5e3, 1),
                             "speedup_vs_plain": round(t_plain200 * 5 / best, 2)}}
 
@@ -809,6 +929,20 @@ def bench_rollout(args, D, dev, rank):
         del g
     k_use = min(res, key=res.get)
     t_graph = res[k_use]
+    # the work of the rollout, counted on the device on one eager pass (the
+    # trajectory is deterministic: the timed graph does the same work)
+    cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+    counted = rollout.GraphRollout(sim, RAG_T, dr, capture=False, steps_per_launch=k_use)
+    sim.set_pair_counter(cnt)
+    sim.load_state(F0)
+    counted.run()
+    sim.set_pair_counter(None)
+    torch.cuda.synchronize()
+    pairs, blocks, draws, words = (int(x) for x in cnt.tolist())
+    del counted
+    ops = OPS_WORD * words + OPS_PHILOX * (blocks + draws) + OPS_DRAW * (pairs + draws) + OPS_RATE * pairs
+    props = torch.cuda.get_device_properties(dev)
+    alu_peak = props.multi_processor_count * 128 * 2.07e9 / 1e12
     eager = rollout.GraphRollout(sim, RAG_T, dr, capture=False, steps_per_launch=1)
     t_eager = timed(lambda: (sim.load_state(F0), eager.run()))
     # plain one-launch-per-step path on the same rollout (table built first)
@@ -824,6 +958,11 @@ def bench_rollout(args, D, dev, rank):
             "ms_per_rollout": round(t_graph * 1e3, 3), "steps_per_launch": k_use,
             "graph_ms_by_steps_per_launch": {str(k): round(v * 1e3, 3) for k, v in res.items()},
             "autotune": choice,
+            "roofline": {"bound": "alu", "achieved": round(ops / t_graph / 1e12, 3), "peak": round(alu_peak, 2),
+                         "unit": "T lane-ops/s", "frac": round(ops / t_graph / 1e12 / alu_peak, 4), "traffic": None,
+                         "kernel": "k_step_resident (fused), four size classes on forked streams, whole rollout",
+                         "work": {"pairs": pairs, "philox_blocks_candidates": blocks, "burning_draws": draws,
+                                  "word_steps": words}},
             "comparators": {"eager_one_step_launches_ms": round(t_eager * 1e3, 3),
                             "plain_one_launch_per_step_ms": round(t_plain * 1e3, 3),
                             "speedup_vs_plain": round(t_plain / t_graph, 2),

@@ -288,9 +288,9 @@ typedef enum {
     JWF_KERNEL_TILED_FUSED = 5 /* tiled, probabilities from the terrain      */
 } jwf_kernel;
 /* Choose the step kernel; threads_per_env = 0 picks a block size by env size
- * (resident kernels) or 256 threads a tile (tiled kernels); else 32, 64, 128
- * or 256 threads per env (resident kernels) or 128, 256 or 512 threads a tile
- * (tiled kernels).  Other values return JWF_EINVAL. */
+ * (resident kernels) or 256 threads a tile (tiled kernels); else 32, 64, 128,
+ * 256, 512 or 1024 threads per env (resident kernels) or 128, 256 or 512
+ * threads a tile (tiled kernels).  Other values return JWF_EINVAL. */
 JWF_API jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_env);
 
 /* Resident envs run as up to four size classes by their longer side (<= 64,
@@ -298,7 +298,9 @@ JWF_API jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threa
  * side on forked streams.  jwf_size_classes writes the classes present to
  * h_classes (host, up to 4 entries, may be NULL) and returns their number;
  * jwf_set_class_threads sets the block size of one class (0: by size; 32,
- * 64, 128 or 256), e.g. from an autotuner.  jwf_set_kernel's explicit
+ * 64, 128, 256, 512 or 1024), e.g. from an autotuner; a block size whose
+ * shared memory (it grows with the warps) does not fit the class's largest env
+ * returns JWF_EINVAL and changes nothing.  jwf_set_kernel's explicit
  * threads_per_env overrides both. */
 JWF_API int32_t jwf_size_classes(const jwf_ctx* ctx, int32_t* h_classes);
 JWF_API jwf_status jwf_set_class_threads(jwf_ctx* ctx, int32_t size_class, int32_t threads);

@@ -19,7 +19,7 @@ import torch
 
 from . import jwf
 
-THREADS = (32, 64, 128, 256)
+THREADS = (32, 64, 128, 256, 512, 1024)
 TILE_THREADS = (128, 256, 512)
 ROUND_STEPS = (4, 8, 16)
 
@@ -124,7 +124,10 @@ def tune(sim: jwf.Sim, F0: torch.Tensor, drops: torch.Tensor | None = None, kern
             for c in classes:
                 best = None
                 for th in THREADS:
-                    sim.set_class_threads(c, th)
+                    try:
+                        sim.set_class_threads(c, th)
+                    except jwf.JwfError:
+                        continue            # that block size does not fit this class's envs
                     t = _time(probe)
                     if best is None or t < best[0]:
                         best = (t, th)

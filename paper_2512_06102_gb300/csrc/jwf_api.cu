@@ -668,8 +668,8 @@ jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_e
     const int t = threads_per_env;
     if (tiled && !(t == 0 || t == 128 || t == 256 || t == 512))
         return fail(ctx, JWF_EINVAL, "jwf_set_kernel: tiled kernels take 0, 128, 256 or 512 threads a tile");
-    if (!tiled && !(t == 0 || t == 32 || t == 64 || t == 128 || t == 256))
-        return fail(ctx, JWF_EINVAL, "jwf_set_kernel: threads_per_env must be 0, 32, 64, 128 or 256");
+    if (!tiled && !(t == 0 || t == 32 || t == 64 || t == 128 || t == 256 || t == 512 || t == 1024))
+        return fail(ctx, JWF_EINVAL, "jwf_set_kernel: threads_per_env must be 0, 32, 64, 128, 256, 512 or 1024");
     ctx->kernel = kernel;
     ctx->threads_per_env = threads_per_env;
     return JWF_OK;
@@ -678,8 +678,16 @@ jwf_status jwf_set_kernel(jwf_ctx* ctx, jwf_kernel kernel, int32_t threads_per_e
 jwf_status jwf_set_class_threads(jwf_ctx* ctx, int32_t size_class, int32_t threads) {
     if (ctx == nullptr) return JWF_EINVAL;
     if (size_class < 0 || size_class > 3) return fail(ctx, JWF_EINVAL, "jwf_set_class_threads: class must be 0..3");
-    if (threads != 0 && threads != 32 && threads != 64 && threads != 128 && threads != 256)
-        return fail(ctx, JWF_EINVAL, "jwf_set_class_threads: threads must be 0, 32, 64, 128 or 256");
+    if (threads != 0 && threads != 32 && threads != 64 && threads != 128 && threads != 256 && threads != 512 &&
+        threads != 1024)
+        return fail(ctx, JWF_EINVAL, "jwf_set_class_threads: threads must be 0, 32, 64, 128, 256, 512 or 1024");
+    int limit = 0;
+    cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    for (const JwfGroup& G : ctx->groups)
+        if (G.size_class == size_class && threads > 0 &&
+            jwf_resident_smem(G.maxH, G.maxW, threads) + 64 > (size_t)limit)
+            return fail(ctx, JWF_EINVAL, "jwf_set_class_threads: the class's envs and that block size do not fit "
+                                         "shared memory");
     for (JwfGroup& G : ctx->groups)
         if (G.size_class == size_class) G.threads = threads;
     return JWF_OK;

@@ -710,6 +710,8 @@ cudaError_t launch_v(const jwf_ctx* c, int threads, const ResArgs& a, const Rate
         case 64: return launch_t<64, FUSED>(c, a, K, smem, s, nq);
         case 128: return launch_t<128, FUSED>(c, a, K, smem, s, nq);
         case 256: return launch_t<256, FUSED>(c, a, K, smem, s, nq);
+        case 512: return launch_t<512, FUSED>(c, a, K, smem, s, nq);
+        case 1024: return launch_t<1024, FUSED>(c, a, K, smem, s, nq);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -870,7 +872,7 @@ cudaError_t launch_resident_part(jwf_ctx* c, int32_t k, const int32_t* drops, in
         const JwfGroup& G = c->groups[g];
         int threads = c->threads_per_env > 0 ? c->threads_per_env
                                              : (G.threads > 0 ? G.threads : jwf_resident_threads(G.maxH, G.maxW));
-        if (threads != 32 && threads != 64 && threads != 128) threads = 256;
+        if (threads != 32 && threads != 64 && threads != 128 && threads != 512 && threads != 1024) threads = 256;
         const size_t smem = jwf_resident_smem(G.maxH, G.maxW, threads);
         cudaStream_t gs = s;
         if (ng > 1) {

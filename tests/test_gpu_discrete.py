@@ -78,7 +78,7 @@ def test_batched_with_drops(kernel):
     _run_both(scn, q32, 200, drops=drops, seed=0, kernel=kernel)
 
 
-@pytest.mark.parametrize("threads", [32, 64, 128, 256])
+@pytest.mark.parametrize("threads", [32, 64, 128, 256, 512, 1024])
 def test_resident_thread_counts(threads):
     require_gpu()
     scn = scenarios.make_scenario(96, 80, N=5, seed=9)
@@ -453,11 +453,14 @@ def test_tiled_copy_wait_runs_out_and_context_recovers():
     sim.close()
 
 
+@pytest.mark.parametrize("threads", [0, 1024])
 @pytest.mark.parametrize("kernel", [jwf.KERNEL_RESIDENT, jwf.KERNEL_FUSED])
-def test_resident_maximum_size(kernel):
+def test_resident_maximum_size(kernel, threads):
     """The largest grids the resident kernels hold in shared memory (longer
     side 512, the top size class; 512 x 500 leaves a partial word in every
-    row) next to a small one, with drops, against the oracle bit for bit."""
+    row) next to a small one, with drops, against the oracle bit for bit; by
+    default and with 1024 threads a grid (the largest block whose warp
+    scratch still fits beside the grid)."""
     require_gpu()
     H = [512, 512, 33]
     W = [512, 500, 512]
@@ -467,7 +470,7 @@ def test_resident_maximum_size(kernel):
     k = 30
     drops = _fire_drops(scn, k, 35)
     sim = make_sim(scn, seed=6)
-    sim.set_kernel(kernel)
+    sim.set_kernel(kernel, threads)
     if kernel == jwf.KERNEL_FUSED:
         sim.set_terrain(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
         fused = sim
