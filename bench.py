@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-tanker", action="store_true")
     ap.add_argument("--no-calibrate", action="store_true")
-    ap.add_argument("--profile", choices=["resident", "relaxed", "tiled", "plain"], default=None,
+    ap.add_argument("--profile", choices=["resident", "relaxed", "tiled", "plain", "prob"], default=None,
                     help="run one small case of a kernel family once (for ncu captures); prints no bench line")
     return ap.parse_args()
 
@@ -1166,7 +1166,8 @@ def run_profile(case: str):
     grids of 128^2, one tiled relaxed forward step, one two-step forward pass,
     two one-step adjoints, sixteen adjoint steps in two-step passes and one 16-step rate-adjoint accumulation; 'tiled' = 2 grids of 4096^2, 800 steps with
     drops on the fused tiled kernel (256 threads a tile, 16 steps a round); 'plain' = the batched
-    workload (4096 grids of 128^2, probability table) for 20 steps of the plain one-launch-per-step path."""
+    workload (4096 grids of 128^2, probability table) for 20 steps of the plain one-launch-per-step path;
+    'prob' = the probability table of 1024 grids of 128^2."""
     import torch
 
     from paper_2512_06102_gb300 import build, jwf, scenarios
@@ -1174,7 +1175,15 @@ def run_profile(case: str):
     build.build()
     dev = torch.device("cuda", 0)
     to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    if case == "plain":
+    if case == "prob":
+        # the probability table of 1024 grids of 128^2 (q: 537 MB, larger than L2)
+        scn = scenarios.make_scenario(SIDE, SIDE, N=1024, seed=0)
+        sim = jwf.Sim(SIDE, SIDE, n_envs=1024, n_classes=scenarios.N_CLASSES, seed=0)
+        sim.set_params(scn.params)
+        sim.precompute_probs(to(scn.cls), to(scn.dem), to(scn.wind_speed), to(scn.wind_dir))
+        torch.cuda.synchronize()
+        print(f"profile case prob: mean q {float(sim.probs()[0].mean()):.6f}")
+    elif case == "plain":
         # the plain one-launch-per-step comparator on the batched workload (table path)
         scn = scenarios.make_scenario(SIDE, SIDE, N=N_ENVS, seed=0)
         drops = scenarios.drops(20, scn.H, scn.W, seed=0)
