@@ -11,6 +11,18 @@
 namespace {
 
 constexpr int kListCap = 256;      // active cells shared out per warp pass
+
+// Division of a word index by the words per row WW (a grid's or region's row
+// length in 32-cell words), by a multiply-high with the rounded-up reciprocal
+// m = ceil(2^32 / WW): floor(n m / 2^32) = floor(n / WW) whenever n (m WW -
+// 2^32) < 2^32, which holds for the word indices of these kernels (below
+// 2^16, with WW <= 64).  A few instructions instead of an integer division.
+struct WordDiv {
+    uint32_t m;     // 0 for WW == 1
+    __device__ __forceinline__ explicit WordDiv(int WW)
+        : m(WW == 1 ? 0u : (uint32_t)((0xffffffffull + (unsigned long long)WW) / (unsigned long long)WW)) {}
+    __device__ __forceinline__ int div(int n) const { return m == 0u ? n : (int)__umulhi((uint32_t)n, m); }
+};
 // per warp: item list, ign and out words, pair list (fused variant)
 constexpr int kWarpScratch = kListCap + 64 + 256;
 
@@ -54,7 +66,7 @@ __device__ __forceinline__ void fused_pairs(const Args& a, const RateConsts& K, 
         const int ol = (int)(itm >> 5) & 31;
         const int j = (int)itm & 31;
         const int ii = base + ol;
-        const int ry = ii / WW;
+        const int ry = WordDiv(WW).div(ii);
         const int yy = oy + ry;
         const int xx = ox + ((ii - ry * WW) << 5) + j;
         if (pair_ignites(a, K, e, off, W, yy, xx, d, tt, ep4)) atomicOr(&ignw[ol], 1u << j);

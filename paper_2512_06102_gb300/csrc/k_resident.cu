@@ -80,8 +80,9 @@ __host__ __device__ __forceinline__ int res_plane_words(int H, int W) {
 __device__ void res_load(const uint8_t* __restrict__ Fe, int H, int W, int WW, bool vec,
                          uint32_t* Bp, uint32_t* C, uint32_t* D) {
     const int words = H * WW;
+    const WordDiv wd(WW);
     for (int i = threadIdx.x; i < words; i += blockDim.x) {
-        const int y = i / WW, w = i - (i / WW) * WW;
+        const int y = wd.div(i), w = i - y * WW;
         const int x0 = w << 5;
         const uint8_t* src = Fe + (int64_t)y * W + x0;
         uint32_t b = 0, c = 0, dd = 0;
@@ -113,8 +114,9 @@ __device__ void res_load(const uint8_t* __restrict__ Fe, int H, int W, int WW, b
 __device__ void res_store(uint8_t* __restrict__ Fe, int H, int W, int WW, bool vec,
                           const uint32_t* Bp, const uint32_t* C, const uint32_t* D) {
     const int words = H * WW;
+    const WordDiv wd(WW);
     for (int i = threadIdx.x; i < words; i += blockDim.x) {
-        const int y = i / WW, w = i - (i / WW) * WW;
+        const int y = wd.div(i), w = i - y * WW;
         const int x0 = w << 5;
         uint8_t* dst = Fe + (int64_t)y * W + x0;
         const uint32_t b = Bp[(y + 1) * WW + w], c = C[i], dd = D[i];
@@ -154,8 +156,9 @@ __device__ __forceinline__ uint64_t spread_bits(uint32_t v) {
 __device__ void res_store2(uint32_t* __restrict__ P, int64_t off, int H, int W, int WW, bool aligned,
                            const uint32_t* Bp, const uint32_t* C, const uint32_t* D) {
     const int words = H * WW;
+    const WordDiv wd(WW);
     for (int i = threadIdx.x; i < words; i += blockDim.x) {
-        const int y = i / WW, w = i - (i / WW) * WW;
+        const int y = wd.div(i), w = i - y * WW;
         const int x0 = w << 5;
         const int n = min(32, W - x0);
         const uint32_t m = n == 32 ? 0xffffffffu : ((1u << n) - 1u);
@@ -272,6 +275,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
 
         const int H = a.H[e], W = a.W[e];
         const int WW = (W + 31) >> 5;
+        const WordDiv wd(WW);
         const int pw = (H + 2) * WW;
         const int words = H * WW;
         const int nchunks = (words + 31) >> 5;
@@ -384,7 +388,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 uint32_t burn = 0, cand = 0;
                 uint32_t sd[8];
                 if (i < words) {
-                    const int w = i - (i / WW) * WW;
+                    const int w = i - wd.div(i) * WW;
                     const uint32_t* bp = &Bc[WW + i];             // row y + 1 of the padded plane
                     const bool hl = w > 0, hr = w + 1 < WW;
                     const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
@@ -497,7 +501,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                         const int ol = (int)(item >> 5) & 31;
                         const int j = (int)item & 31;
                         const int ii = base + ol;
-                        const int yy = ii / WW;
+                        const int yy = wd.div(ii);
                         const int xx = ((ii - yy * WW) << 5) + j;
                         const uint32_t cell = (uint32_t)(yy * W + xx);
                         if (item & (1u << 18)) {
@@ -525,7 +529,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 for (int q = threadIdx.x; q < qn; q += NT) {
                     const uint32_t it = Q[q];
                     const int ii = (int)(it >> 18), j = (int)(it >> 13) & 31;
-                    const int yy = ii / WW;
+                    const int yy = wd.div(ii);
                     const int xx = ((ii - yy * WW) << 5) + j;
                     const uint32_t cell = (uint32_t)(yy * W + xx);
                     if (!(it & (1u << 12))) {
@@ -548,7 +552,7 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                     const int i = (c << 5) + lane;
                     uint32_t nb = 0u;
                     if (i < words) {
-                        const int y = i / WW, w = i - (i / WW) * WW;
+                        const int y = wd.div(i), w = i - y * WW;
                         const uint32_t burn = Bc[WW + i];
                         const uint32_t ig = Bn[WW + i];
                         const uint32_t ou = D[i] & burn;          // burning cells that burned out

@@ -356,6 +356,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     const int oy = ty0 - kb, ox = tx0 - 32;
     const int RH = TY + 2 * kb;
     const int WW = (TX + 64 + 31) >> 5;
+    const WordDiv wd(WW);
     const int pw = (RH + 2) * WW;
     const int words = RH * WW;
     const int nchunks = (words + 31) >> 5;
@@ -407,7 +408,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
     if (use_tma) ph ^= 1u;
     // load the region (cells outside the grid read as no fuel)
     for (int i = threadIdx.x; i < words; i += NT) {
-        const int ry = i / WW, w = i - (i / WW) * WW;
+        const int ry = wd.div(i), w = i - ry * WW;
         const int gy = oy + ry, gx0 = ox + (w << 5);
         uint32_t b = 0, c = 0, dd = 0;
         if (use_tma) {
@@ -465,7 +466,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             const int i1 = min(words, (c + 1) << 5);
             for (int i = c << 5; i < i1; ++i) {
                 any |= B0[WW + i];
-                const int y = i / WW, w = i - (i / WW) * WW;
+                const int y = wd.div(i), w = i - y * WW;
                 if (y >= kb && y < kb + TY) nd0 += __popc(D[i] & col_bits(w, 32, 32 + TX));
             }
             fl_c[c] = any != 0u;
@@ -528,7 +529,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             uint32_t burn = 0, cand = 0;
             uint32_t sd[8];
             if (i < words) {
-                const int w = i - (i / WW) * WW;
+                const int w = i - wd.div(i) * WW;
                 const uint32_t* bp = &Bc[WW + i];
                 const bool hl = w > 0, hr = w + 1 < WW;
                 const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
@@ -635,7 +636,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
                     const int ol = (int)(item >> 5) & 31;
                     const int j = (int)item & 31;
                     const int ii = base + ol;
-                    const int ry = ii / WW;
+                    const int ry = wd.div(ii);
                     const int gy = oy + ry, gx = ox + ((ii - ry * WW) << 5) + j;
                     const uint32_t cell = (uint32_t)(gy * W + gx);
                     if (item & (1u << 18)) {
@@ -668,7 +669,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
                     const int q = q0 + k * NT;
                     const uint32_t it = Q[q < qn ? q : q0];
                     const int ii = (int)(it >> 20), j = (int)(it >> 15) & 31;
-                    const int ry = ii / WW;
+                    const int ry = wd.div(ii);
                     yy[k] = oy + ry;
                     xx[k] = ox + ((ii - ry * WW) << 5) + j;
                     kind[k] = q < qn ? ((it & (1u << 14)) ? 2 : 1) : 0;
@@ -689,7 +690,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             for (int q = threadIdx.x; q < qn; q += NT) {
                 const uint32_t it = Q[q];
                 const int ii = (int)(it >> 20), j = (int)(it >> 15) & 31;
-                const int ry = ii / WW;
+                const int ry = wd.div(ii);
                 const int gy = oy + ry, gx = ox + ((ii - ry * WW) << 5) + j;
                 const uint32_t cell = (uint32_t)(gy * W + gx);
                 if (!(it & (1u << 14))) {
@@ -709,7 +710,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             const int i = (c << 5) + lane;
             uint32_t nbw = 0u;
             if (i < words) {
-                const int y = i / WW, w = i - (i / WW) * WW;
+                const int y = wd.div(i), w = i - y * WW;
                 const uint32_t burn = Bc[WW + i];
                 const uint32_t ig = IG[i], ou = OU[i];
                 uint32_t nb = (burn & ~ou) | ig;
