@@ -747,7 +747,7 @@ def bench_large(args, D, dev, rank):
             best = min(best, D.max(e0.elapsed_time(e1) / 1e3))
         return best
 
-    choice = autotune.tune(sim, F0, dr, kernel=jwf.KERNEL_TILED_FUSED, probe_steps=64, use_cache=False)
+    choice = autotune.tune(sim, F0, dr, kernel=jwf.KERNEL_TILED_FUSED, probe_steps=256, use_cache=False)
     th = int(choice.get("tile_threads", 0))
     sim.set_kernel(jwf.KERNEL_TILED_FUSED, th)
     t_fused = timed(lambda: sim.step(BIG_T, dr), max(2, args.steps))
