@@ -58,6 +58,11 @@ def lib():
                                                i32p, i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                i32p, i32p, u8p, i32p]
             L.orc_discrete_rollout.restype = None
+            L.orc_discrete_rollout_masks.argtypes = [ctypes.c_int, i32p, i32p, i64p, u8p, u8p, f32p,
+                                                     ctypes.c_float, u8p, ctypes.c_int64, ctypes.c_uint64,
+                                                     i32p, i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                     i32p, i32p, u8p, i32p]
+            L.orc_discrete_rollout_masks.restype = None
             L.orc_mc_outcomes.argtypes = [ctypes.c_int, ctypes.c_int, u8p, f32p, ctypes.c_float, u8p,
                                           ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_int64, u8p]
@@ -165,6 +170,26 @@ class Rollout:
             _ptr(self.off, ctypes.c_int64), _ptr(self.F, ctypes.c_uint8), _ptr(self.F0, ctypes.c_uint8),
             _ptr(self.q, ctypes.c_float), ctypes.c_float(self.p_continue), _ptr(dr, ctypes.c_int32),
             self.radius, ctypes.c_uint64(self.seed), _ptr(self.t, ctypes.c_int32),
+            _ptr(self.episode, ctypes.c_int32), k, self.t_max, int(self.auto_reset),
+            _ptr(burning, ctypes.c_int32), _ptr(burnt, ctypes.c_int32), _ptr(done, ctypes.c_uint8),
+            _ptr(self.env_ids, ctypes.c_int32))
+        return burning, burnt, done
+
+    def step_masks(self, masks: np.ndarray):
+        """Advance k steps with the tanker action of each step as a cell mask:
+        masks uint8 [k, cells] of this batch (nonzero = water).  Returns
+        (burning [k, N], burnt [k, N], done [k, N])."""
+        m = np.ascontiguousarray(masks, dtype=np.uint8)
+        k = int(m.shape[0])
+        assert m.size == k * self.F.size
+        burning = np.zeros((k, self.N), dtype=np.int32)
+        burnt = np.zeros((k, self.N), dtype=np.int32)
+        done = np.zeros((k, self.N), dtype=np.uint8)
+        lib().orc_discrete_rollout_masks(
+            self.N, _ptr(self.H, ctypes.c_int32), _ptr(self.W, ctypes.c_int32),
+            _ptr(self.off, ctypes.c_int64), _ptr(self.F, ctypes.c_uint8), _ptr(self.F0, ctypes.c_uint8),
+            _ptr(self.q, ctypes.c_float), ctypes.c_float(self.p_continue), _ptr(m, ctypes.c_uint8),
+            ctypes.c_int64(self.F.size), ctypes.c_uint64(self.seed), _ptr(self.t, ctypes.c_int32),
             _ptr(self.episode, ctypes.c_int32), k, self.t_max, int(self.auto_reset),
             _ptr(burning, ctypes.c_int32), _ptr(burnt, ctypes.c_int32), _ptr(done, ctypes.c_uint8),
             _ptr(self.env_ids, ctypes.c_int32))

@@ -25,6 +25,8 @@
  *                       k steps of a batch of (possibly ragged) grids with
  *                       per-step drops, per-env counts, done flags and
  *                       optional auto-reset.
+ *   orc_discrete_rollout_masks
+ *                       the same with each step's action as a cell mask.
  *
  * Cell states (uint8): 0 no fuel (an unburned cell with mu_den = -1, which can
  * never ignite), 1 can burn (unburned, fuel present), 2 burning, 3 burned.
@@ -197,11 +199,11 @@ void orc_discrete_step(int H, int W, const uint8_t* F_in, uint8_t* F_out,
  *             draws the same numbers as in the full batch
  * Done also holds when the post-step grid has no burning cell.
  * ------------------------------------------------------------------------- */
-void orc_discrete_rollout(int N, const int32_t* H, const int32_t* W, const int64_t* off,
-                          uint8_t* F, const uint8_t* F0, const float* q, float p_continue,
-                          const int32_t* drops, int R, uint64_t seed,
-                          int32_t* t, int32_t* episode, int k, int t_max, int auto_reset,
-                          int32_t* burning, int32_t* burnt, uint8_t* done, const int32_t* env_ids)
+static void rollout(int N, const int32_t* H, const int32_t* W, const int64_t* off,
+                    uint8_t* F, const uint8_t* F0, const float* q, float p_continue,
+                    const int32_t* drops, const uint8_t* masks, int64_t cells, int R, uint64_t seed,
+                    int32_t* t, int32_t* episode, int k, int t_max, int auto_reset,
+                    int32_t* burning, int32_t* burnt, uint8_t* done, const int32_t* env_ids)
 {
     for (int step = 0; step < k; ++step) {
         for (int e = 0; e < N; ++e) {
@@ -213,6 +215,9 @@ void orc_discrete_rollout(int N, const int32_t* H, const int32_t* W, const int64
                 const int32_t* c = drops + ((size_t)step * N + e) * 2;
                 mask = (uint8_t*)malloc(n);
                 orc_drop_mask(H[e], W[e], c[0], c[1], R, mask);
+            } else if (masks != NULL) {
+                mask = (uint8_t*)malloc(n);
+                memcpy(mask, masks + (size_t)step * (size_t)cells + (size_t)off[e], n);
             }
             int32_t nb = 0, nd = 0;
             uint32_t env = env_ids != NULL ? (uint32_t)env_ids[e] : (uint32_t)e;
@@ -233,6 +238,29 @@ void orc_discrete_rollout(int N, const int32_t* H, const int32_t* W, const int64
             }
         }
     }
+}
+
+void orc_discrete_rollout(int N, const int32_t* H, const int32_t* W, const int64_t* off,
+                          uint8_t* F, const uint8_t* F0, const float* q, float p_continue,
+                          const int32_t* drops, int R, uint64_t seed,
+                          int32_t* t, int32_t* episode, int k, int t_max, int auto_reset,
+                          int32_t* burning, int32_t* burnt, uint8_t* done, const int32_t* env_ids)
+{
+    rollout(N, H, W, off, F, F0, q, p_continue, drops, NULL, 0, R, seed, t, episode, k, t_max, auto_reset,
+            burning, burnt, done, env_ids);
+}
+
+/* The same rollout with the tanker action of each step given as a cell mask:
+ * masks uint8 [k][cells] (cells = the batch's total), nonzero = water on the
+ * cell at that step (a burning cell there becomes burned before the spread). */
+void orc_discrete_rollout_masks(int N, const int32_t* H, const int32_t* W, const int64_t* off,
+                                uint8_t* F, const uint8_t* F0, const float* q, float p_continue,
+                                const uint8_t* masks, int64_t cells, uint64_t seed,
+                                int32_t* t, int32_t* episode, int k, int t_max, int auto_reset,
+                                int32_t* burning, int32_t* burnt, uint8_t* done, const int32_t* env_ids)
+{
+    rollout(N, H, W, off, F, F0, q, p_continue, NULL, masks, cells, 1, seed, t, episode, k, t_max, auto_reset,
+            burning, burnt, done, env_ids);
 }
 
 /* ---------------------------------------------------------------------------
