@@ -236,6 +236,27 @@ JWF_API jwf_status jwf_apply_action(jwf_ctx* ctx, const uint8_t* d_mask, void* s
 JWF_API jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
                     int32_t* d_burnt, uint8_t* d_done, void* stream);
 
+/* Tanker actions as cell masks (Section 4: water turns a burning cell into a
+ * burned one; any footprint, not only square drops).  A mask travels as a bit
+ * row of jwf_mask_words(n_cells) uint32 words: cell g of the context (the
+ * concatenated envs) at bit g % 32 of word g / 32, set = water on the cell.
+ * jwf_pack_masks turns uint8 masks [n_rows][n_cells] (device, nonzero =
+ * water) into n_rows such rows at d_bits (device, caller-owned,
+ * n_rows * jwf_mask_words(n_cells) words); JWF_EINVAL for negative sizes or
+ * null pointers with n_rows, n_cells > 0. */
+JWF_API int64_t jwf_mask_words(int64_t n_cells);
+JWF_API jwf_status jwf_pack_masks(int32_t n_rows, int64_t n_cells, const uint8_t* d_masks, uint32_t* d_bits,
+                                  void* stream);
+
+/* jwf_step with the action of step s given by mask row s of d_mask_bits
+ * (uint32 [k][jwf_mask_words(cells)], device, read-only): step 1 of every env
+ * turns its burning cells with a set bit into burned ones, then the spread
+ * and the counts are those of jwf_step.  Every step kernel (resident, tiled,
+ * plain) takes the masks inside its k-step launches.  Errors as jwf_step;
+ * JWF_EINVAL when d_mask_bits is NULL. */
+JWF_API jwf_status jwf_step_masked(jwf_ctx* ctx, int32_t k, const uint32_t* d_mask_bits, int32_t* d_burning,
+                                   int32_t* d_burnt, uint8_t* d_done, void* stream);
+
 /* jwf_step that also records the state after every step: d_history is uint8
  * [k][cells] on the device (row s = the state after step s, after an
  * auto-reset the restarted state; caller-owned).  The trajectory is the one

@@ -529,8 +529,10 @@ jwf_status jwf_step_record_packed(jwf_ctx* ctx, int32_t k, const int32_t* d_drop
     return st;
 }
 
-jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
-                    int32_t* d_burnt, uint8_t* d_done, void* stream) {
+namespace {
+// k steps with the actions as drop centres or as mask bit rows (not both)
+jwf_status step_impl(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, const uint32_t* d_masks, int32_t* d_burning,
+                     int32_t* d_burnt, uint8_t* d_done, void* stream) {
     if (ctx == nullptr) return JWF_EINVAL;
     if (k < 1) return fail(ctx, JWF_EINVAL, "jwf_step: k < 1");
     if (!ctx->have_params) return fail(ctx, JWF_ESTATE, "jwf_step: no parameters set");
@@ -563,16 +565,39 @@ jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_
         ctx->wexp_stale = false;
     }
     if (tiled) {
-        err = jwf_launch_step_tiled(ctx, k, d_drops, d_burning, d_burnt, d_done, fused, S(stream));
+        err = jwf_launch_step_tiled(ctx, k, d_drops, d_masks, d_burning, d_burnt, d_done, fused, S(stream));
     } else {
         ctx->tiles_valid = false;
         if (plain)
-            err = jwf_launch_step_plain(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
+            err = jwf_launch_step_plain(ctx, k, d_drops, d_masks, d_burning, d_burnt, d_done, S(stream));
         else
-            err = jwf_launch_step_resident(ctx, k, d_drops, d_burning, d_burnt, d_done, S(stream));
+            err = jwf_launch_step_resident(ctx, k, d_drops, d_masks, d_burning, d_burnt, d_done, S(stream));
     }
     if (err != cudaSuccess) return cuda_fail(ctx, err, "jwf_step");
     return JWF_OK;
+}
+}  // namespace
+
+jwf_status jwf_step(jwf_ctx* ctx, int32_t k, const int32_t* d_drops, int32_t* d_burning,
+                    int32_t* d_burnt, uint8_t* d_done, void* stream) {
+    return step_impl(ctx, k, d_drops, nullptr, d_burning, d_burnt, d_done, stream);
+}
+
+jwf_status jwf_step_masked(jwf_ctx* ctx, int32_t k, const uint32_t* d_mask_bits, int32_t* d_burning,
+                           int32_t* d_burnt, uint8_t* d_done, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    if (d_mask_bits == nullptr) return fail(ctx, JWF_EINVAL, "jwf_step_masked: d_mask_bits is null");
+    return step_impl(ctx, k, nullptr, d_mask_bits, d_burning, d_burnt, d_done, stream);
+}
+
+int64_t jwf_mask_words(int64_t n_cells) { return n_cells < 0 ? 0 : jwf_mask_row_words(n_cells); }
+
+jwf_status jwf_pack_masks(int32_t n_rows, int64_t n_cells, const uint8_t* d_masks, uint32_t* d_bits,
+                          void* stream) {
+    if (n_rows < 0 || n_cells < 0) return JWF_EINVAL;
+    if (n_rows == 0 || n_cells == 0) return JWF_OK;
+    if (d_masks == nullptr || d_bits == nullptr) return JWF_EINVAL;
+    return jwf_launch_pack_masks(n_rows, n_cells, d_masks, d_bits, S(stream)) == cudaSuccess ? JWF_OK : JWF_ECUDA;
 }
 
 namespace {

@@ -45,6 +45,20 @@ __device__ __forceinline__ uint4 jwf_philox(uint4 c, uint32_t k0, uint32_t k1) {
     return c;
 }
 
+// Tanker action masks travel bit-packed: a row of jwf_mask_row_words(cells)
+// 32-bit words per step, cell g of the context at bit g % 32 of word g / 32.
+inline __host__ __device__ int64_t jwf_mask_row_words(int64_t cells) { return (cells + 31) / 32; }
+
+// bits of a mask row for cells [g, g + n) of the context (0 < n <= 32), cell
+// g + i at bit i; reads only words that hold those cells
+__device__ __forceinline__ uint32_t mask_run(const uint32_t* __restrict__ row, int64_t g, int n) {
+    const int64_t w = g >> 5;
+    const int sh = (int)(g & 31);
+    uint32_t v = __ldg(row + w) >> sh;
+    if (sh + n > 32) v |= __ldg(row + w + 1) << (32 - sh);
+    return n >= 32 ? v : v & ((1u << n) - 1u);
+}
+
 // Uniform in [0,1) with 24 random bits; exact in float.
 __device__ __forceinline__ float jwf_u24(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
 
@@ -323,13 +337,17 @@ cudaError_t jwf_launch_load_packed(jwf_ctx* c, const uint8_t* P0, cudaStream_t s
 cudaError_t jwf_record_row(jwf_ctx* c, int64_t row, cudaStream_t s);
 cudaError_t jwf_launch_reset(jwf_ctx* c, const uint8_t* env_mask, cudaStream_t s);
 cudaError_t jwf_launch_action(jwf_ctx* c, const uint8_t* mask, cudaStream_t s);
-cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
-                                  int32_t* burnt, uint8_t* done, cudaStream_t s);
-cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops,
+// the step launchers take the steps' actions as drop centres [k][N][2] or as
+// mask bit rows [k][jwf_mask_row_words(cells)] (at most one of the two)
+cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, const uint32_t* masks,
+                                  int32_t* burning, int32_t* burnt, uint8_t* done, cudaStream_t s);
+cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops, const uint32_t* masks,
                                      int32_t* burning, int32_t* burnt, uint8_t* done,
                                      cudaStream_t s);
-cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
-                                  int32_t* burnt, uint8_t* done, bool fused, cudaStream_t s);
+cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, const uint32_t* masks,
+                                  int32_t* burning, int32_t* burnt, uint8_t* done, bool fused, cudaStream_t s);
+cudaError_t jwf_launch_pack_masks(int32_t n_rows, int64_t cells, const uint8_t* masks, uint32_t* bits,
+                                  cudaStream_t s);
 // tensor maps of the tiled step's TMA copies (c->d_tmaps, c->d_tma_ok,
 // c->tma); envs that do not qualify, or a driver without the encoder, keep
 // the plain loads

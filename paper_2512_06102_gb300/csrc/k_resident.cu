@@ -47,6 +47,8 @@ struct ResArgs {
     const float2* wexp;         // [N][8] (hi, lo), or [wser_n][N][8] for a wind series
     int32_t wser_n;             // steps of the wind series (0: static wind)
     const int32_t* drops;       // [k][N][2] or null
+    const uint32_t* mask;       // [k][mask_words] bit rows of the steps' action masks, or null
+    int64_t mask_words;
     int32_t* t;
     int32_t* episode;
     int32_t* out_burning;       // [k][N] or null
@@ -224,6 +226,25 @@ __device__ void res_action(int H, int W, int WW, uint32_t* Bp, uint32_t* D, int 
     }
 }
 
+// Apply an action mask row (bit g % 32 of word g / 32 = water on cell g of the
+// context) to the env's planes, all threads; adds the doused cells to *count
+// when count is not null.
+__device__ void res_action_mask(const uint32_t* __restrict__ mrow, int64_t off, int H, int W, int WW,
+                                uint32_t* Bp, uint32_t* D, int* count = nullptr) {
+    const int words = H * WW;
+    const WordDiv wd(WW);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) {
+        const int y = wd.div(i), w = i - y * WW;
+        uint32_t* bp = &Bp[(y + 1) * WW + w];
+        if (*bp == 0u) continue;
+        const uint32_t m = mask_run(mrow, off + (int64_t)y * W + (w << 5), min(32, W - (w << 5)));
+        const uint32_t doused = *bp & m;
+        *bp &= ~m;
+        D[i] |= doused;
+        if (count != nullptr && doused != 0u) atomicAdd(count, __popc(doused));
+    }
+}
+
 // Chunk activity after a (re)load: flag[c] = chunk c of B holds a burning
 // cell; the other buffer's flags get `other` (0 after zeroing, 1 when it may
 // hold stale words).  Adds popc(D) to *burnt.  All threads; caller syncs.
@@ -312,6 +333,9 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
         if (a.drops != nullptr && a.k > 0) {
             res_action(H, W, WW, B0, D, a.drops[(int64_t)e * 2], a.drops[(int64_t)e * 2 + 1], a.R);
             __syncthreads();
+        } else if (a.mask != nullptr && a.k > 0) {
+            res_action_mask(a.mask, off, H, W, WW, B0, D);
+            __syncthreads();
         }
         res_init_flags(B0, D, WW, words, nchunks, flag0, flag1, 0, &s_burnt);
         __syncthreads();
@@ -342,6 +366,10 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                                a.drops[((int64_t)s * a.N + e) * 2 + 1], a.R, &s_dous);
                     __syncthreads();
                     burnt_now += s_dous;
+                } else if (a.mask != nullptr) {
+                    res_action_mask(a.mask + (int64_t)s * a.mask_words, off, H, W, WW, Bc, D, &s_dous);
+                    __syncthreads();
+                    burnt_now += s_dous;
                 }
             }
             if (threadIdx.x == 0) {
@@ -357,6 +385,8 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 cxn = a.drops[((int64_t)(s + 1) * a.N + e) * 2];
                 cyn = a.drops[((int64_t)(s + 1) * a.N + e) * 2 + 1];
             }
+            const uint32_t* mrow =
+                (a.mask != nullptr && s + 1 < a.k && !rec) ? a.mask + (int64_t)(s + 1) * a.mask_words : nullptr;
             int my_b = 0, my_o = 0, my_x = 0;
             uint32_t my_pairs = 0, my_blocks = 0, my_burn = 0, my_chunks = 0;
             // phase A: the chunks that can change are dealt to the warps,
@@ -559,7 +589,9 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                         nb = (burn & ~ou) | ig;
                         my_b += __popc(nb);
                         my_o += __popc(ou);
-                        const uint32_t m = drop_bits(y, w, W, cxn, cyn, a.R);
+                        const uint32_t m = mrow != nullptr
+                                               ? mask_run(mrow, off + (int64_t)y * W + (w << 5), min(32, W - (w << 5)))
+                                               : drop_bits(y, w, W, cxn, cyn, a.R);
                         const uint32_t doused = nb & m;
                         my_x += __popc(doused);
                         nb &= ~m;
@@ -622,6 +654,9 @@ k_step_resident(const ResArgs a, const RateConsts Kc) {
                 __syncthreads();
                 if (cxn >= 0) {
                     res_action(H, W, WW, Bc, D, cxn, cyn, a.R);
+                    __syncthreads();
+                } else if (mrow != nullptr) {
+                    res_action_mask(mrow, off, H, W, WW, Bc, D);
                     __syncthreads();
                 }
                 // the other buffer may hold stale burning words: mark it active
@@ -789,21 +824,22 @@ __global__ void __launch_bounds__(1024) k_reorder(const int32_t* __restrict__ or
     }
 }
 
-cudaError_t launch_resident_part(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning, int32_t* burnt,
-                                 uint8_t* done, const int32_t* order, int32_t* last_burning, cudaStream_t s);
+cudaError_t launch_resident_part(jwf_ctx* c, int32_t k, const int32_t* drops, const uint32_t* masks,
+                                 int32_t* burning, int32_t* burnt, uint8_t* done, const int32_t* order,
+                                 int32_t* last_burning, cudaStream_t s);
 
-cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
-                                     int32_t* burnt, uint8_t* done, cudaStream_t s) {
+cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops, const uint32_t* masks,
+                                     int32_t* burning, int32_t* burnt, uint8_t* done, cudaStream_t s) {
     const int32_t k1 = c->reorder_steps;
     const int ng = (int)c->groups.size();
     // (one size class only: with several, the classes run on forked streams
     // and the reorder would join them between the two parts)
     if (k1 <= 0 || k < 2 * k1 || c->hist != nullptr || c->d_lastb == nullptr || ng != 1)
-        return launch_resident_part(c, k, drops, burning, burnt, done, c->d_order, nullptr, s);
+        return launch_resident_part(c, k, drops, masks, burning, burnt, done, c->d_order, nullptr, s);
     // two launches: k1 steps in the creation order, then the rest with the
     // envs whose fires are largest after k1 steps first (the longest fires
     // set the end of the launch, so they should not start last)
-    cudaError_t err = launch_resident_part(c, k1, drops, burning, burnt, done, c->d_order, c->d_lastb, s);
+    cudaError_t err = launch_resident_part(c, k1, drops, masks, burning, burnt, done, c->d_order, c->d_lastb, s);
     if (err != cudaSuccess) return err;
     int st[4] = {0, 0, 0, 0}, cn[4] = {0, 0, 0, 0};
     for (int g = 0; g < ng; ++g) {
@@ -815,12 +851,14 @@ cudaError_t jwf_launch_step_resident(jwf_ctx* c, int32_t k, const int32_t* drops
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const int64_t o = (int64_t)k1 * c->N;
-    return launch_resident_part(c, k - k1, drops ? drops + 2 * o : nullptr, burning ? burning + o : nullptr,
+    const uint32_t* m2 = masks ? masks + (int64_t)k1 * jwf_mask_row_words(c->cells) : nullptr;
+    return launch_resident_part(c, k - k1, drops ? drops + 2 * o : nullptr, m2, burning ? burning + o : nullptr,
                                 burnt ? burnt + o : nullptr, done ? done + o : nullptr, c->d_order_dyn, nullptr, s);
 }
 
-cudaError_t launch_resident_part(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning, int32_t* burnt,
-                                 uint8_t* done, const int32_t* order, int32_t* last_burning, cudaStream_t s) {
+cudaError_t launch_resident_part(jwf_ctx* c, int32_t k, const int32_t* drops, const uint32_t* masks,
+                                 int32_t* burning, int32_t* burnt, uint8_t* done, const int32_t* order,
+                                 int32_t* last_burning, cudaStream_t s) {
     const bool fused = c->kernel == JWF_KERNEL_FUSED;
     ResArgs a;
     a.last_burning = last_burning;
@@ -836,6 +874,8 @@ cudaError_t launch_resident_part(jwf_ctx* c, int32_t k, const int32_t* drops, in
     a.wexp = c->wser_n > 0 ? c->d_wser : c->d_wexp;
     a.wser_n = c->wser_n;
     a.drops = drops;
+    a.mask = masks;
+    a.mask_words = jwf_mask_row_words(c->cells);
     a.t = c->d_t;
     a.episode = c->d_episode;
     a.out_burning = burning;

@@ -111,6 +111,21 @@ __global__ void k_unpack(const int64_t n, const uint8_t* __restrict__ P, uint8_t
         }
 }
 
+// uint8 masks [n_rows][cells] (nonzero = water) -> bit rows of
+// jwf_mask_row_words(cells) words: one ballot per 32 cells
+__global__ void k_pack_masks(int32_t n_rows, int64_t cells, int64_t words, const uint8_t* __restrict__ m,
+                             uint32_t* __restrict__ bits) {
+    const int64_t total = (int64_t)n_rows * words * 32;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps walk the cells 32 at a time (the loop bound is a multiple of 32)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - (threadIdx.x & 31) < total; i += stride) {
+        const int64_t r = i / (words * 32), g = i - r * words * 32;
+        const bool on = g < cells && m[r * cells + g] != 0;
+        const uint32_t b = __ballot_sync(0xffffffffu, on);
+        if ((threadIdx.x & 31) == 0) bits[r * words + (g >> 5)] = b;
+    }
+}
+
 unsigned pack_blocks(int64_t work) {
     int64_t b = (work + 255) / 256;
     if (b < 1) b = 1;
@@ -206,11 +221,20 @@ __device__ __forceinline__ uint32_t drop_mask(int y, int x0, int cx, int cy, int
     return ((hi - lo == 31) ? 0xffffffffu : ((1u << (hi - lo + 1)) - 1u)) << lo;
 }
 
+// the action mask row's bits for columns x0 - 1 .. x0 + n of row y (the bit
+// layout of row_bits), columns and rows outside the grid 0
+__device__ __forceinline__ uint32_t mask_bits(const uint32_t* __restrict__ mrow, int64_t off, int y, int x0, int n,
+                                              int H, int W) {
+    if (y < 0 || y >= H) return 0u;
+    const int c0 = max(x0 - 1, 0), c1 = min(x0 + n, W - 1);
+    return mask_run(mrow, off + (int64_t)y * W + c0, c1 - c0 + 1) << (c0 - x0 + 1);
+}
+
 __global__ void __launch_bounds__(JWF_TILE)
 k_step_plain(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
              const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs, int32_t N,
              const uint8_t* __restrict__ Fin, uint8_t* __restrict__ Fout,
-             const float* __restrict__ q, const int32_t* __restrict__ drops,
+             const float* __restrict__ q, const int32_t* __restrict__ drops, const uint32_t* __restrict__ mrow,
              const int32_t* __restrict__ tcur, const int32_t* __restrict__ episode,
              uint32_t key0, uint32_t key1, float p_continue, int R, int32_t* __restrict__ cnt) {
     __shared__ int32_t s_n[2];
@@ -244,11 +268,13 @@ k_step_plain(const int2* __restrict__ tiles, const int32_t* __restrict__ Hs,
         const RowBits ru = row_bits(Fe, y - 1, x0, n, H, W, vec);
         const RowBits rc = row_bits(Fe, y, x0, n, H, W, vec);
         const RowBits rd = row_bits(Fe, y + 1, x0, n, H, W, vec);
-        // burning sources after the step's drop (burning under it -> burned)
-        const uint32_t mu = ru.b & ~drop_mask(y - 1, x0, cx, cy, R);
-        const uint32_t mdr = drop_mask(y, x0, cx, cy, R);
+        // burning sources after the step's action (burning under water -> burned)
+        const uint32_t mdu = mrow ? mask_bits(mrow, off, y - 1, x0, n, H, W) : drop_mask(y - 1, x0, cx, cy, R);
+        const uint32_t mdr = mrow ? mask_bits(mrow, off, y, x0, n, H, W) : drop_mask(y, x0, cx, cy, R);
+        const uint32_t mdd = mrow ? mask_bits(mrow, off, y + 1, x0, n, H, W) : drop_mask(y + 1, x0, cx, cy, R);
+        const uint32_t mu = ru.b & ~mdu;
         const uint32_t mc = rc.b & ~mdr;
-        const uint32_t md = rd.b & ~drop_mask(y + 1, x0, cx, cy, R);
+        const uint32_t md = rd.b & ~mdd;
         // the segment's own cells (bit k = column x0 + k)
         const uint32_t own_c = (rc.c >> 1) & nmask;
         const uint32_t own_b = (mc >> 1) & nmask;                           // burning after the drop
@@ -400,8 +426,9 @@ cudaError_t jwf_launch_action(jwf_ctx* c, const uint8_t* mask, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
-                                  int32_t* burnt, uint8_t* done, cudaStream_t s) {
+cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, const uint32_t* masks,
+                                  int32_t* burning, int32_t* burnt, uint8_t* done, cudaStream_t s) {
+    const int64_t mw = jwf_mask_row_words(c->cells);
     const uint32_t key0 = (uint32_t)(c->seed & 0xffffffffu), key1 = (uint32_t)(c->seed >> 32);
     const int auto_reset = (c->flags & JWF_AUTO_RESET) ? 1 : 0;
     for (int32_t st = 0; st < k; ++st) {
@@ -409,7 +436,8 @@ cudaError_t jwf_launch_step_plain(jwf_ctx* c, int32_t k, const int32_t* drops, i
         uint8_t* Fout = c->d_state[c->cur ^ 1];
         k_step_plain<<<(unsigned)c->n_ptiles, JWF_TILE, 0, s>>>(
             c->d_ptiles, c->d_H, c->d_W, c->d_off, c->N, Fin, Fout, c->d_q,
-            drops ? drops + (int64_t)st * c->N * 2 : nullptr, c->d_t, c->d_episode, key0, key1,
+            drops ? drops + (int64_t)st * c->N * 2 : nullptr, masks ? masks + (int64_t)st * mw : nullptr, c->d_t,
+            c->d_episode, key0, key1,
             c->P.p_continue, c->drop_radius, c->d_cnt);
         const int64_t o = (int64_t)st * c->N;
         k_finalize<<<(c->N + 255) / 256, 256, 0, s>>>(
@@ -443,5 +471,13 @@ cudaError_t jwf_launch_state_planes(int64_t n, const uint8_t* states, float* pun
     int64_t blocks = (n + 255) / 256;
     if (blocks > 65536) blocks = 65536;
     k_state_planes<<<(unsigned)blocks, 256, 0, s>>>(n, states, pun, pburn);
+    return cudaGetLastError();
+}
+
+cudaError_t jwf_launch_pack_masks(int32_t n_rows, int64_t cells, const uint8_t* masks, uint32_t* bits,
+                                  cudaStream_t s) {
+    const int64_t words = jwf_mask_row_words(cells);
+    if (n_rows <= 0 || words == 0) return cudaSuccess;
+    k_pack_masks<<<pack_blocks((int64_t)n_rows * words * 32), 256, 0, s>>>(n_rows, cells, words, masks, bits);
     return cudaGetLastError();
 }

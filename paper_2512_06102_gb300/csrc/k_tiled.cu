@@ -52,6 +52,8 @@ struct TileArgs {
     const float2* wexp;
     int32_t wser_n;
     const int32_t* drops;        // [kb][N][2] of this round, or null
+    const uint32_t* mask;        // [kb][mask_words] action mask bit rows of this round, or null
+    int64_t mask_words;
     const int32_t* t;            // step counters at the start of the round
     const int32_t* episode;
     int32_t* cnt;                // [kb][2][N] per-step counts (zeroed before the round)
@@ -120,6 +122,16 @@ __device__ void res_action_rel(int RH, int WW, uint32_t* Bp, uint32_t* D, int cx
         *bp &= ~m;
         D[y * WW + w] |= doused;
     }
+}
+
+// Action mask bits of region word (row gy, columns gx0 .. gx0 + 31 of the
+// grid), columns and rows outside the grid 0.
+__device__ __forceinline__ uint32_t region_mask(const uint32_t* __restrict__ mrow, int64_t off, int gy, int gx0,
+                                                int H, int W) {
+    if (gy < 0 || gy >= H) return 0u;
+    const int c0 = max(gx0, 0), c1 = min(gx0 + 31, W - 1);
+    if (c0 > c1) return 0u;
+    return mask_run(mrow, off + (int64_t)gy * W + c0, c1 - c0 + 1) << (c0 - gx0);
 }
 
 // Tile activity after a round: kActAny = a burning interior cell; the other
@@ -457,6 +469,16 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
         const int gcx = a.drops[(int64_t)e * 2], gcy = a.drops[(int64_t)e * 2 + 1];
         res_action_rel(RH, WW, B0, D, gcx - ox, gcy - oy, a.R, gcx >= 0 && gcy >= 0);
         __syncthreads();
+    } else if (a.mask != nullptr) {
+        for (int i = threadIdx.x; i < words; i += NT) {
+            const int y = wd.div(i), w = i - y * WW;
+            uint32_t* bp = &B0[(y + 1) * WW + w];
+            if (*bp == 0u) continue;
+            const uint32_t m = region_mask(a.mask, off, oy + y, ox + (w << 5), H, W);
+            D[i] |= *bp & m;
+            *bp &= ~m;
+        }
+        __syncthreads();
     }
     // initial chunk flags and burned interior cells (after the round's first drop)
     {
@@ -490,6 +512,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             s_cnt[(s + 1) % 3][3] = 0;
             s_qn[(s + 1) % 3] = 0;
         }
+        const uint32_t* mrow = (a.mask != nullptr && s + 1 < kb) ? a.mask + (int64_t)(s + 1) * a.mask_words : nullptr;
         bool hasn = false;
         int cxn = 0, cyn = 0;
         if (a.drops != nullptr && s + 1 < kb) {
@@ -718,7 +741,8 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
                 my_r += __popc(nb);
                 my_b += __popc(nb & im);
                 my_o += __popc(ou & im);
-                const uint32_t m = drop_bits_rel(y, w, cxn, cyn, a.R, hasn);
+                const uint32_t m = mrow != nullptr ? region_mask(mrow, off, oy + y, ox + (w << 5), H, W)
+                                                   : drop_bits_rel(y, w, cxn, cyn, a.R, hasn);
                 const uint32_t doused = nb & m;
                 my_x += __popc(doused & im);
                 nb &= ~m;
@@ -892,8 +916,9 @@ void jwf_rate_consts(const jwf_ctx* c, RateConsts* K);
 int jwf_tile_rows() { return kTileRows; }
 int jwf_tile_cols() { return kTileCols; }
 
-cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, int32_t* burning,
-                                  int32_t* burnt, uint8_t* done, bool fused, cudaStream_t s) {
+cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, const uint32_t* masks,
+                                  int32_t* burning, int32_t* burnt, uint8_t* done, bool fused, cudaStream_t s) {
+    const int64_t mw = jwf_mask_row_words(c->cells);
     cudaError_t err;
     if (!c->tiles_valid) {
         // the state changed outside the tiled path: each tile's activity and
@@ -938,6 +963,8 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, i
         a.wexp = c->wser_n > 0 ? c->d_wser : c->d_wexp;
         a.wser_n = c->wser_n;
         a.drops = drops ? drops + (int64_t)s0 * c->N * 2 : nullptr;
+        a.mask = masks ? masks + (int64_t)s0 * mw : nullptr;
+        a.mask_words = mw;
         a.t = c->d_t;
         a.episode = c->d_episode;
         a.cnt = c->d_tcnt;

@@ -100,6 +100,9 @@ _SIGS = {
     "jwf_relaxed_fwd_steps": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 6),
     "jwf_relaxed_bwd_steps": (ctypes.c_int, [_VP, ctypes.c_int32] + [_VP] * 10),
     "jwf_rates_contract": (ctypes.c_int, [_VP] * 8),
+    "jwf_mask_words": (ctypes.c_int64, [ctypes.c_int64]),
+    "jwf_pack_masks": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP]),
+    "jwf_step_masked": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP]),
     "jwf_step_relaxed_bwd_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP,
                                                     ctypes.c_float] + [_VP] * 9),
 }
@@ -161,6 +164,25 @@ def unpack_states(packed: torch.Tensor, n_cells: int, out: torch.Tensor | None =
     st = lib().jwf_unpack_states(int(n_cells), _ptr(packed), _ptr(out), _stream(stream))
     if st != 0:
         raise RuntimeError(f"jwf_unpack_states: {lib().jwf_status_string(st).decode()}")
+    return out
+
+
+def mask_words(n_cells: int) -> int:
+    """uint32 words of one bit-packed action mask row of n cells."""
+    return int(lib().jwf_mask_words(int(n_cells)))
+
+
+def pack_masks(masks: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """uint8 action masks [k, cells] (device, nonzero = water) -> bit rows
+    int32 [k, mask_words(cells)] (cell g at bit g % 32 of word g // 32)."""
+    if masks.dim() != 2 or masks.dtype != torch.uint8:
+        raise ValueError("masks must be uint8 [k, cells]")
+    k, n = masks.shape
+    if out is None:
+        out = torch.empty((k, mask_words(n)), dtype=torch.int32, device=masks.device)
+    st = lib().jwf_pack_masks(int(k), int(n), _ptr(masks.contiguous()), _ptr(out), _stream(stream))
+    if st != 0:
+        raise RuntimeError(f"jwf_pack_masks: {lib().jwf_status_string(st).decode()}")
     return out
 
 
@@ -415,6 +437,24 @@ class Sim:
         """counter: int64 device tensor of four elements (pairs compared,
         candidate Philox blocks, remain-burning draws, words scanned), or None."""
         self._check(lib().jwf_set_pair_counter(self._h, _ptr(counter)), "jwf_set_pair_counter")
+
+    def step_masked(self, k: int, mask_bits, burning=None, burnt=None, done=None, stream=None):
+        """Advance k steps with each step's action as a bit-packed cell mask
+        (pack_masks): int32 [k, mask_words(cells)].  Returns (burning, burnt,
+        done) [k, N]."""
+        if (mask_bits.dtype != torch.int32 or mask_bits.dim() != 2
+                or tuple(mask_bits.shape) != (k, mask_words(self.cells))):
+            raise ValueError("mask_bits must be int32 [k, mask_words(cells)]")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if burning is None:
+            burning = torch.empty((k, self.N), dtype=torch.int32, device=dev)
+        if burnt is None:
+            burnt = torch.empty((k, self.N), dtype=torch.int32, device=dev)
+        if done is None:
+            done = torch.empty((k, self.N), dtype=torch.uint8, device=dev)
+        self._check(lib().jwf_step_masked(self._h, int(k), _ptr(mask_bits), _ptr(burning), _ptr(burnt), _ptr(done),
+                                          _stream(stream)), "jwf_step_masked")
+        return burning, burnt, done
 
     def step(self, k: int = 1, drops=None, burning=None, burnt=None, done=None, stream=None, history=None,
              packed: bool = False):
