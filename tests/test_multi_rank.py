@@ -146,3 +146,14 @@ def test_sharded_step_without_process_group_is_the_whole_batch():
     g = torch.tensor([1.0, -2.0], dtype=f64)
     assert shard.reduce_loss_and_grad_(g, torch.tensor(3.5, dtype=f64)) == 3.5
     assert g.tolist() == [1.0, -2.0]
+
+
+def test_fit_on_an_empty_shard_takes_part_without_a_simulator():
+    """A rank whose shard holds no grids calls calibrate.fit without a
+    simulator: it contributes a zero loss and gradient, and (with no other
+    rank) its parameters stay where they started."""
+    from paper_2512_06102_gb300 import calibrate
+    theta0 = calibrate.theta_of(scenarios.Params(), scenarios.N_CLASSES)
+    theta, losses = calibrate.fit(None, None, None, None, theta0, T=3, iters=2)
+    assert losses == [0.0, 0.0]
+    assert torch.equal(theta, theta0)
