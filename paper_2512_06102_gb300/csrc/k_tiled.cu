@@ -551,8 +551,13 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             const int i = base + lane;
             uint32_t burn = 0, cand = 0;
             uint32_t sd[8];
-            if (i < words) {
-                const int w = i - wd.div(i) * WW;
+            // rows of the region that can still reach the interior by the
+            // round's end: at step s, those within kb - 1 - s rows of it
+            // (fire moves one cell a step); the others keep their state
+            // (stale, never read by a row that matters)
+            const int ry = wd.div(i);
+            if (i < words && ry > s && ry < RH - 1 - s) {
+                const int w = i - ry * WW;
                 const uint32_t* bp = &Bc[WW + i];
                 const bool hl = w > 0, hr = w + 1 < WW;
                 const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
