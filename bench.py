@@ -115,7 +115,49 @@ class Dist:
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
+class _Nvml:
+    """Read-only NVML queries through ctypes (the library ships with the driver):
+    the SM clock, its maximum and the active clock event reasons."""
+    SM = 1                                   # NVML_CLOCK_SM
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_index: int):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(torch_index).uuid)
+            ok = self.lib.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode(), ctypes.byref(self.h)) == 0
+        except Exception:
+            ok = False
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(torch_index, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sm(self) -> int:
+        v = self.c.c_uint()
+        return v.value if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, self.c.byref(v)) == 0 else -1
+
+    def sm_max(self) -> int:
+        v = self.c.c_uint()
+        return v.value if self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, self.c.byref(v)) == 0 else -1
+
+    def reasons(self) -> int:
+        v = self.c.c_ulonglong()
+        return v.value if self.reasons_fn(self.h, self.c.byref(v)) == 0 else 0
+
+
 class Clocks:
+    """SM clock and clock event reasons sampled every millisecond (NVML) while
+    the timed region runs; only samples between begin() and end() count.
+    Falls back to nvidia-smi at 200 ms when NVML cannot be loaded."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -124,8 +166,18 @@ class Clocks:
         self.index = index
         self.rows = []
         self.proc = None
+        self.nvml = None
+        self.window = [None, None]
+        self.halt = threading.Event()
 
     def start(self):
+        try:
+            self.nvml = _Nvml(self.index)
+            self.th = threading.Thread(target=self._poll, daemon=True)
+            self.th.start()
+            return
+        except (OSError, AttributeError):
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -135,11 +187,31 @@ class Clocks:
         except OSError:
             self.proc = None
 
+    def begin(self):
+        self.window[0] = time.perf_counter()
+
+    def end(self):
+        self.window[1] = time.perf_counter()
+
+    def _poll(self):
+        while not self.halt.is_set():
+            self.rows.append((time.perf_counter(), self.nvml.sm(), self.nvml.reasons()))
+            self.halt.wait(0.001)
+
     def _read(self):
         for line in self.proc.stdout:
             self.rows.append([x.strip() for x in line.split(",")])
 
     def stop(self):
+        if self.nvml is not None:
+            self.halt.set()
+            self.th.join(timeout=2)
+            t0, t1 = self.window
+            rows = [r for r in self.rows if (t0 is None or r[0] >= t0) and (t1 is None or r[0] <= t1)]
+            sm = [r[1] for r in rows if r[1] > 0]
+            reasons = sorted({n for r in rows for bit, n in _Nvml.REASONS.items() if r[2] & bit})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.nvml.sm_max(),
+                    "reasons": reasons, "samples": len(sm), "source": "NVML, 1 ms"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -158,7 +230,7 @@ class Clocks:
                     if v.lower() == "active":
                         reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 def peaks():
@@ -251,11 +323,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     D.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk.begin()
     e0.record(stream)
     for _ in range(args.steps):
         episode(record=True)
     e1.record(stream)
     torch.cuda.synchronize()
+    clk.end()
     D.barrier()
     t_dev = e0.elapsed_time(e1) / 1e3
     t_kernel = statistics.mean(a.elapsed_time(b) for a, b in ev_k) / 1e3
@@ -509,17 +583,24 @@ def bench_relaxed(args, D, dev, rank):
         loss.backward()
         return th.grad
 
+    clock_rec = {}
+
     def timed(T, ckpt, steps, warmup):
         for _ in range(max(1, warmup)):
             fwd_bwd(T, ckpt)
         torch.cuda.synchronize()
         D.barrier()
+        clk = Clocks(torch.cuda.current_device())
+        clk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk.begin()
         e0.record(stream)
         for _ in range(steps):
             fwd_bwd(T, ckpt)
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.end()
+        clock_rec.setdefault((T, ckpt), clk.stop())
         D.barrier()
         return D.max(e0.elapsed_time(e1) / 1e3) / steps
 
@@ -585,7 +666,7 @@ def bench_relaxed(args, D, dev, rank):
     sim.close()
     return {"metric": "fwd+bwd cell-steps/s at 256x128^2, T=100",
             "value": rate, "unit": "fwd+bwd cell-steps/s",
-            "ms_per_step": t_keep * 1e3, "dtype": "f32",
+            "ms_per_step": t_keep * 1e3, "dtype": "f32", "clocks": clock_rec.get((REL_T, None)),
             "memory_policy": "every state kept" if keep_all == 0 else "sqrt(T) checkpoints",
             "path_bytes_model": f"{fwd_b + bwd_b + acc_b} B/cell-step ({fwd_b} two-step fwd + {bwd_b} two-step "
                                 f"fused adjoint + {acc_b} rate-adjoint accumulation)",
@@ -733,18 +814,26 @@ def bench_large(args, D, dev, rank):
     stream = torch.cuda.current_stream()
     cells = BIG_ENVS * BIG_SIDE * BIG_SIDE
 
+    clock_rec = {}
+
     def timed(fn, reps):
         best = float("inf")
+        clk = Clocks(torch.cuda.current_device())
+        clk.start()
         for _ in range(reps):
             sim.load_state(F0)
             torch.cuda.synchronize()
             D.barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if clk.window[0] is None:
+                clk.begin()
             e0.record(stream)
             fn()
             e1.record(stream)
             torch.cuda.synchronize()
+            clk.end()
             best = min(best, D.max(e0.elapsed_time(e1) / 1e3))
+        clock_rec[best] = clk.stop()
         return best
 
     choice = autotune.tune(sim, F0, dr, kernel=jwf.KERNEL_TILED_FUSED, probe_steps=256, use_cache=False)
@@ -803,6 +892,7 @@ def bench_large(args, D, dev, rank):
     peak_ops = 152 * 128 * 2.07e9 / 1e12
     return {"metric": "CA cell-updates/s at 8x4096^2 (1000-step episode with tanker drops)",
             "value": D.world * cells * BIG_T / best, "unit": "cell-updates/s", "ms_per_episode": round(best * 1e3, 3),
+            "clocks": clock_rec.get(best),
             "kernel": "tiled table (table build included)" if t_table <= t_fused else "tiled fused",
             "fused_ms": round(t_fused * 1e3, 3), "table_with_build_ms": round(t_table * 1e3, 3),
             "round_steps": choice.get("round_steps"), "tile_threads": th,
