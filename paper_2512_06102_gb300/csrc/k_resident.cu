@@ -77,13 +77,37 @@ __host__ __device__ __forceinline__ int res_plane_words(int H, int W) {
     return 2 * (H + 2) * WW + 2 * H * WW;
 }
 
+// Scalars of the threads that step one env, at the start of its shared
+// region.
+struct ResEnvShared {
+    int32_t env;
+    int32_t cnt[3][3];      // burning, new burn-outs, doused (per step, three steps in flight)
+    int32_t qn[3];          // queued work items (per step)
+    int32_t ncl[3];         // chunks that can change (per step)
+    int32_t burnt;
+    int32_t dous;           // cells doused by a drop applied at a step's start
+    int32_t drop[2];        // the next step's drop centre (x, y), -1 for none
+    int32_t burnt_now;      // burned cells after the last step and the next drop (thread 0)
+    int32_t last_burnt;     // burned cells after the last step
+    int32_t last_nb;        // burning cells after the last step
+    int32_t pad;
+};
+constexpr int kEnvScalarWords = (int)(sizeof(ResEnvShared) / 4);
+
+// words of an env's region: its scalars, the planes, two chunk-flag byte
+// arrays, the dealt-chunk list and the work queue
+__host__ __device__ __forceinline__ int res_region_words(int H, int W) {
+    const int nchunks = (H * ((W + 31) >> 5) + 31) >> 5;
+    return kEnvScalarWords + res_plane_words(H, W) + 2 * ((nchunks + 3) >> 2) + nchunks + kResQCap;
+}
+
 
 // Load env into planes: one word (32 cells) per thread iteration.
 __device__ void res_load(const uint8_t* __restrict__ Fe, int H, int W, int WW, bool vec,
-                         uint32_t* Bp, uint32_t* C, uint32_t* D) {
+                         uint32_t* Bp, uint32_t* C, uint32_t* D, int tid, int nth) {
     const int words = H * WW;
     const WordDiv wd(WW);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) {
+    for (int i = tid; i < words; i += nth) {
         const int y = wd.div(i), w = i - y * WW;
         const int x0 = w << 5;
         const uint8_t* src = Fe + (int64_t)y * W + x0;
@@ -114,10 +138,10 @@ __device__ void res_load(const uint8_t* __restrict__ Fe, int H, int W, int WW, b
 }
 
 __device__ void res_store(uint8_t* __restrict__ Fe, int H, int W, int WW, bool vec,
-                          const uint32_t* Bp, const uint32_t* C, const uint32_t* D) {
+                          const uint32_t* Bp, const uint32_t* C, const uint32_t* D, int tid, int nth) {
     const int words = H * WW;
     const WordDiv wd(WW);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) {
+    for (int i = tid; i < words; i += nth) {
         const int y = wd.div(i), w = i - y * WW;
         const int x0 = w << 5;
         uint8_t* dst = Fe + (int64_t)y * W + x0;
@@ -156,10 +180,10 @@ __device__ __forceinline__ uint64_t spread_bits(uint32_t v) {
 // otherwise words share bytes with their neighbours and OR their bits into a
 // row the caller zeroed.
 __device__ void res_store2(uint32_t* __restrict__ P, int64_t off, int H, int W, int WW, bool aligned,
-                           const uint32_t* Bp, const uint32_t* C, const uint32_t* D) {
+                           const uint32_t* Bp, const uint32_t* C, const uint32_t* D, int tid, int nth) {
     const int words = H * WW;
     const WordDiv wd(WW);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) {
+    for (int i = tid; i < words; i += nth) {
         const int y = wd.div(i), w = i - y * WW;
         const int x0 = w << 5;
         const int n = min(32, W - x0);
@@ -186,12 +210,14 @@ __device__ void res_store2(uint32_t* __restrict__ P, int64_t off, int H, int W, 
 
 // history row `row` of the env: one byte a cell, or 2-bit packed
 __device__ __forceinline__ void res_record(const ResArgs& a, int64_t row, int64_t off, int H, int W, int WW,
-                                           bool vec, const uint32_t* Bp, const uint32_t* C, const uint32_t* D) {
+                                           bool vec, const uint32_t* Bp, const uint32_t* C, const uint32_t* D,
+                                           int tid, int nth) {
     const int64_t ho = row * a.hist_stride;
     if (a.hist_packed)
-        res_store2(reinterpret_cast<uint32_t*>(a.history + ho), off, H, W, WW, a.packed_aligned != 0, Bp, C, D);
+        res_store2(reinterpret_cast<uint32_t*>(a.history + ho), off, H, W, WW, a.packed_aligned != 0, Bp, C, D,
+                   tid, nth);
     else
-        res_store(a.history + ho + off, H, W, WW, vec && (ho & 15) == 0, Bp, C, D);
+        res_store(a.history + ho + off, H, W, WW, vec && (ho & 15) == 0, Bp, C, D, tid, nth);
 }
 
 // Bits of word w (cells 32w .. 32w+31) of row y covered by a drop of radius R
@@ -207,15 +233,15 @@ __device__ __forceinline__ uint32_t drop_bits(int y, int w, int W, int cx, int c
 
 // Apply a drop to the planes (burning under it -> burned), all threads; adds
 // the number of doused cells to *count when count is not null.
-__device__ void res_action(int H, int W, int WW, uint32_t* Bp, uint32_t* D, int cx, int cy, int R,
-                           int* count = nullptr) {
+__device__ void res_action(int H, int W, int WW, uint32_t* Bp, uint32_t* D, int cx, int cy, int R, int tid,
+                           int nth, int* count = nullptr) {
     if (cx < 0 || cy < 0) return;
     const int y0 = max(cy - R, 0), y1 = min(cy + R, H - 1);
     if (y0 > y1) return;
     const int w0 = max(cx - R, 0) >> 5, w1 = min(cx + R, W - 1) >> 5;
     const int nw = w1 - w0 + 1;
     const int total = (y1 - y0 + 1) * nw;
-    for (int j = threadIdx.x; j < total; j += blockDim.x) {
+    for (int j = tid; j < total; j += nth) {
         const int y = y0 + j / nw, w = w0 + j % nw;
         const uint32_t m = drop_bits(y, w, W, cx, cy, R);
         uint32_t* bp = &Bp[(y + 1) * WW + w];
@@ -230,10 +256,10 @@ __device__ void res_action(int H, int W, int WW, uint32_t* Bp, uint32_t* D, int 
 // context) to the env's planes, all threads; adds the doused cells to *count
 // when count is not null.
 __device__ void res_action_mask(const uint32_t* __restrict__ mrow, int64_t off, int H, int W, int WW,
-                                uint32_t* Bp, uint32_t* D, int* count = nullptr) {
+                                uint32_t* Bp, uint32_t* D, int tid, int nth, int* count = nullptr) {
     const int words = H * WW;
     const WordDiv wd(WW);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) {
+    for (int i = tid; i < words; i += nth) {
         const int y = wd.div(i), w = i - y * WW;
         uint32_t* bp = &Bp[(y + 1) * WW + w];
         if (*bp == 0u) continue;
@@ -249,9 +275,9 @@ __device__ void res_action_mask(const uint32_t* __restrict__ mrow, int64_t off, 
 // cell; the other buffer's flags get `other` (0 after zeroing, 1 when it may
 // hold stale words).  Adds popc(D) to *burnt.  All threads; caller syncs.
 __device__ void res_init_flags(const uint32_t* Bp, const uint32_t* D, int WW, int words, int nchunks,
-                               uint8_t* fl_cur, uint8_t* fl_other, uint8_t other, int* burnt) {
+                               uint8_t* fl_cur, uint8_t* fl_other, uint8_t other, int* burnt, int tid, int nth) {
     int nd = 0;
-    for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
+    for (int c = tid; c < nchunks; c += nth) {
         uint32_t any = 0u;
         const int i1 = min(words, (c + 1) << 5);
         for (int i = c << 5; i < i1; ++i) {
@@ -264,432 +290,449 @@ __device__ void res_init_flags(const uint32_t* Bp, const uint32_t* D, int WW, in
     atomicAdd(burnt, nd);
 }
 
-// at most 64 registers a thread: 1024 threads fit an SM
+
+// One env stepped a.k times by the NT threads of the CTA, its planes and
+// queues in the shared region Rg (its ResEnvShared first), wsc = the per-warp
+// scratch of the calling warp.
+template <int NT, bool FUSED>
+__device__ __forceinline__ void res_env(const ResArgs& a, const RateConsts& sK, const int e, uint32_t* Rg,
+                                        uint32_t* wsc) {
+    const int tid = threadIdx.x;
+    ResEnvShared& T = *reinterpret_cast<ResEnvShared*>(Rg);
+    const int H = a.H[e], W = a.W[e];
+    const int WW = (W + 31) >> 5;
+    const WordDiv wd(WW);
+    const int pw = (H + 2) * WW;
+    const int words = H * WW;
+    const int nchunks = (words + 31) >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int nw = NT / 32;
+    uint32_t* B0 = Rg + kEnvScalarWords;
+    uint32_t* B1 = B0 + pw;
+    uint32_t* C = B1 + pw;
+    uint32_t* D = C + words;
+    uint32_t* list = wsc;                                   // per-warp scratch
+    uint32_t* ignw = list + kListCap;
+    uint32_t* outw = ignw + 32;
+    uint32_t* plist = outw + 32;
+    // chunk activity flags of the two burning buffers
+    uint8_t* flag0 = reinterpret_cast<uint8_t*>(D + words);
+    uint8_t* flag1 = flag0 + nchunks;
+    // chunks dealt this step and the block-wide queue of work items
+    int* clist = reinterpret_cast<int*>(flag0 + 2 * ((nchunks + 3) & ~3));
+    uint32_t* Q = reinterpret_cast<uint32_t*>(clist + nchunks);
+    const int reach = (WW + 1 + 31) >> 5;                 // chunks a word's neighbours span
+    const int64_t off = a.off[e];
+    uint8_t* Fe = a.F + off;
+    const bool vec = ((W & 31) == 0) && ((off & 15) == 0);
+
+    // zero both burning planes (the padding rows must read as 0), then load
+    for (int i = tid; i < 2 * pw; i += NT) B0[i] = 0u;
+    if (tid < 9) T.cnt[tid / 3][tid % 3] = 0;
+    if (tid < 3) {
+        T.qn[tid] = 0;
+        T.ncl[tid] = 0;
+    }
+    if (tid == 0) T.burnt = 0;
+    __syncthreads();
+    res_load(Fe, H, W, WW, vec, B0, C, D, tid, NT);
+    __syncthreads();
+    if (a.drops != nullptr && a.k > 0) {
+        res_action(H, W, WW, B0, D, a.drops[(int64_t)e * 2], a.drops[(int64_t)e * 2 + 1], a.R, tid, NT);
+        __syncthreads();
+    } else if (a.mask != nullptr && a.k > 0) {
+        res_action_mask(a.mask, off, H, W, WW, B0, D, tid, NT);
+        __syncthreads();
+    }
+    res_init_flags(B0, D, WW, words, nchunks, flag0, flag1, 0, &T.burnt, tid, NT);
+    __syncthreads();
+    if (tid == 0) {
+        T.burnt_now = T.burnt;
+        T.last_burnt = 0;
+        T.last_nb = 0;
+    }
+    uint8_t* fl_c = flag0;
+    uint8_t* fl_n = flag1;
+
+    int32_t t = a.t[e];
+    int32_t ep = a.episode[e];
+    uint32_t* Bc = B0;
+    uint32_t* Bn = B1;
+    int hist_done = 0;          // history rows written
+    const bool rec = a.history != nullptr;
+    for (int s = 0; s < a.k; ++s) {
+        const uint32_t tt = (uint32_t)t;
+        const uint32_t ep4 = 4u * (uint32_t)ep;
+        if (rec && s > 0) {
+            // record the state after step s - 1, then apply step s's drop
+            // (when recording it is not folded into the previous write-back)
+            res_record(a, s - 1, off, H, W, WW, vec, Bc, C, D, tid, NT);
+            hist_done = s;
+            if (tid == 0) T.dous = 0;
+            __syncthreads();
+            if (a.drops != nullptr) {
+                res_action(H, W, WW, Bc, D, a.drops[((int64_t)s * a.N + e) * 2],
+                           a.drops[((int64_t)s * a.N + e) * 2 + 1], a.R, tid, NT, &T.dous);
+                __syncthreads();
+                if (tid == 0) T.burnt_now += T.dous;
+            } else if (a.mask != nullptr) {
+                res_action_mask(a.mask + (int64_t)s * a.mask_words, off, H, W, WW, Bc, D, tid, NT, &T.dous);
+                __syncthreads();
+                if (tid == 0) T.burnt_now += T.dous;
+            }
+        }
+        // the next step's drop is applied while the new planes are written:
+        // its centre is copied to shared memory while phases A and B run
+        const bool next_act = s + 1 < a.k && !rec;
+        if (tid == 0) {
+            T.cnt[(s + 1) % 3][0] = 0;
+            T.cnt[(s + 1) % 3][1] = 0;
+            T.cnt[(s + 1) % 3][2] = 0;
+            T.qn[(s + 1) % 3] = 0;
+            T.ncl[(s + 1) % 3] = 0;
+            if (a.drops != nullptr && next_act) {
+                const int32_t* dsrc = a.drops + ((int64_t)(s + 1) * a.N + e) * 2;
+                jwf_cp_async4(reinterpret_cast<float*>(&T.drop[0]), reinterpret_cast<const float*>(dsrc));
+                jwf_cp_async4(reinterpret_cast<float*>(&T.drop[1]), reinterpret_cast<const float*>(dsrc + 1));
+            } else {
+                T.drop[0] = -1;
+                T.drop[1] = -1;
+            }
+        }
+        int my_b = 0, my_o = 0, my_x = 0;
+        // phase A: the chunks that can change are dealt to the warps,
+        // which clear their words of the write buffer and queue their
+        // work items.  A chunk with no burning cell within reach, whose
+        // write buffer holds no burning word, cannot change: it is
+        // skipped.  Every warp finds the needed chunks of a group of 32
+        // with one ballot (lane = chunk); the k-th needed chunk goes to
+        // warp k mod (warps), which also lists it for the write-back.
+        int n_need = 0;                       // needed chunks before this group
+        for (int g0 = 0; g0 < nchunks; g0 += 32) {
+            const int cl = g0 + lane;
+            bool nd = false;
+            if (cl < nchunks) {
+                nd = fl_n[cl] != 0;
+                for (int cc = max(cl - reach, 0); cc <= min(cl + reach, nchunks - 1); ++cc) nd |= fl_c[cc] != 0;
+            }
+            const uint32_t need_m = __ballot_sync(0xffffffffu, nd);
+            const int rk = n_need + __popc(need_m & ((1u << lane) - 1u));
+            const bool take = nd && (rk & (nw - 1)) == warp;
+            if (take) clist[rk] = cl;
+            n_need += __popc(need_m);
+            for (uint32_t mine = __ballot_sync(0xffffffffu, take); mine != 0u;) {
+            const int c = g0 + __ffs(mine) - 1;
+            mine &= mine - 1u;
+            const int base = c << 5;
+            const int i = base + lane;
+            uint32_t burn = 0, cand = 0;
+            uint32_t sd[8];
+            if (i < words) {
+                const int w = i - wd.div(i) * WW;
+                const uint32_t* bp = &Bc[WW + i];             // row y + 1 of the padded plane
+                const bool hl = w > 0, hr = w + 1 < WW;
+                const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
+                const uint32_t uc = bp[-WW], ul = hl ? bp[-WW - 1] : 0u, ur = hr ? bp[-WW + 1] : 0u;
+                const uint32_t dc = bp[WW], dl = hl ? bp[WW - 1] : 0u, dr = hr ? bp[WW + 1] : 0u;
+                // source of direction d for target (y, x) sits at (y - DR[d], x - DX[d])
+                sd[0] = (bc << 1) | (bl >> 31);   // E : (y,   x-1)
+                sd[1] = (dc << 1) | (dl >> 31);   // NE: (y+1, x-1)
+                sd[2] = dc;                       // N : (y+1, x)
+                sd[3] = (dc >> 1) | (dr << 31);   // NW: (y+1, x+1)
+                sd[4] = (bc >> 1) | (br << 31);   // W : (y,   x+1)
+                sd[5] = (uc >> 1) | (ur << 31);   // SW: (y-1, x+1)
+                sd[6] = uc;                       // S : (y-1, x)
+                sd[7] = (uc << 1) | (ul >> 31);   // SE: (y-1, x-1)
+                const uint32_t any = sd[0] | sd[1] | sd[2] | sd[3] | sd[4] | sd[5] | sd[6] | sd[7];
+                cand = C[i] & any;
+                burn = bc;
+                Bn[WW + i] = 0u;                  // collects this step's ignitions
+            } else {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) sd[d] = 0u;
+            }
+            __syncwarp();
+            uint32_t np = 0;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) np += __popc(sd[d] & cand);
+            if (a.counts != nullptr) {
+                // work of the chunk: pairs compared, candidate Philox blocks, burning-cell draws
+                const uint32_t cp = __reduce_add_sync(0xffffffffu, np);
+                const uint32_t cb = __reduce_add_sync(0xffffffffu, __popc(cand & (sd[0] | sd[1] | sd[2] | sd[3])) +
+                                                                       __popc(cand & (sd[4] | sd[5] | sd[6] | sd[7])));
+                const uint32_t cd = __reduce_add_sync(0xffffffffu, __popc(burn));
+                if (lane == 0) {
+                    atomicAdd(&a.counts[0], (unsigned long long)cp);
+                    atomicAdd(&a.counts[1], (unsigned long long)cb);
+                    atomicAdd(&a.counts[2], (unsigned long long)cd);
+                    atomicAdd(&a.counts[3], 32ull);
+                }
+            }
+            const int n_items = __popc(burn) + (int)(FUSED ? np : __popc(cand));
+            int incl = n_items;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total == 0) continue;
+            int pos = -1;
+            if (lane == 0) {
+                int old = T.qn[s % 3];
+                while (old + total <= kResQCap) {
+                    const int prev = atomicCAS(&T.qn[s % 3], old, old + total);
+                    if (prev == old) {
+                        pos = old;
+                        break;
+                    }
+                    old = prev;
+                }
+            }
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (pos >= 0) {
+                uint32_t* q = Q + pos + (incl - n_items);
+                const uint32_t hi = (uint32_t)i << 18;
+                for (uint32_t m = burn; m != 0u; m &= m - 1u) *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 13);
+                if (FUSED) {
+#pragma unroll
+                    for (int d = 0; d < 8; ++d)
+                        for (uint32_t m = sd[d] & cand; m != 0u; m &= m - 1u)
+                            *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 13) | (1u << 12) | (uint32_t)d;
+                } else {
+                    for (uint32_t m = cand; m != 0u; m &= m - 1u) {
+                        const int j = __ffs(m) - 1;
+                        uint32_t dm = 0;
+#pragma unroll
+                        for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
+                        *q++ = hi | ((uint32_t)j << 13) | (1u << 12) | dm;
+                    }
+                }
+                continue;
+            }
+            // the queue is full: this warp evaluates the chunk itself
+            // (ignitions into the cleared write-buffer words, burn-outs
+            // into the burned plane)
+            uint32_t* ignw_c = Bn + WW + base;
+            uint32_t* outw_c = D + base;
+            const uint32_t act = cand | burn;
+            const int n_act = __popc(act);
+            int inca = n_act;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inca, o);
+                if (lane >= o) inca += v;
+            }
+            const int tot_a = __shfl_sync(0xffffffffu, inca, 31);
+            const int excl = inca - n_act;
+            for (int pass = 0; pass < tot_a; pass += kListCap) {
+                uint32_t rem = act;
+                int idx = excl;
+                while (rem != 0u) {
+                    const int j = __ffs(rem) - 1;
+                    rem &= rem - 1u;
+                    if (idx >= pass && idx < pass + kListCap) {
+                        uint32_t item = ((uint32_t)lane << 5) | (uint32_t)j;
+                        if ((cand >> j) & 1u) {
+                            uint32_t dm = 0;
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
+                            item |= (dm << 10) | (1u << 18);
+                        }
+                        list[idx - pass] = item;
+                    }
+                    ++idx;
+                }
+                __syncwarp();
+                const int n_pass = min(kListCap, tot_a - pass);
+                for (int it = lane; it < n_pass; it += 32) {
+                    const uint32_t item = list[it];
+                    const int ol = (int)(item >> 5) & 31;
+                    const int j = (int)item & 31;
+                    const int ii = base + ol;
+                    const int yy = wd.div(ii);
+                    const int xx = ((ii - yy * WW) << 5) + j;
+                    const uint32_t cell = (uint32_t)(yy * W + xx);
+                    if (item & (1u << 18)) {
+                        if (!FUSED && ignites(a, e, off, cell, (item >> 10) & 0xFFu, tt, ep4))
+                            atomicOr(&ignw_c[ol], 1u << j);
+                    } else {
+                        const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
+                        if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&outw_c[ol], 1u << j);
+                    }
+                }
+                if (FUSED) {
+                    for (int it0 = 0; it0 < n_pass; it0 += 32)
+                        fused_pairs(a, sK, list, plist, ignw_c, it0, n_pass, base, e, off, W, WW, 0, 0, tt,
+                                    ep4, lane);
+                }
+                __syncwarp();
+            }
+            }
+        }
+        if (tid == 0) T.ncl[s % 3] = n_need;
+        __syncthreads();
+        // phase B: every thread of the CTA evaluates queued items
+        {
+            const int qn = min(T.qn[s % 3], kResQCap);
+            for (int q = tid; q < qn; q += NT) {
+                const uint32_t it = Q[q];
+                const int ii = (int)(it >> 18), j = (int)(it >> 13) & 31;
+                const int yy = wd.div(ii);
+                const int xx = ((ii - yy * WW) << 5) + j;
+                const uint32_t cell = (uint32_t)(yy * W + xx);
+                if (!(it & (1u << 12))) {
+                    const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
+                    if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&D[ii], 1u << j);
+                } else if (FUSED) {
+                    if (pair_ignites(a, sK, e, off, W, yy, xx, (int)(it & 7u), tt, ep4))
+                        atomicOr(&Bn[WW + ii], 1u << j);
+                } else {
+                    if (ignites(a, e, off, cell, it & 0xFFu, tt, ep4)) atomicOr(&Bn[WW + ii], 1u << j);
+                }
+            }
+        }
+        if (tid == 0) asm volatile("cp.async.wait_all;\n" ::: "memory");    // the next step's drop
+        __syncthreads();
+        // phase C: the dealt chunks are written back, round-robin over the warps
+        {
+            const int ncl = T.ncl[s % 3];
+            const int cxn = T.drop[0], cyn = T.drop[1];
+            const uint32_t* mrow =
+                (a.mask != nullptr && next_act) ? a.mask + (int64_t)(s + 1) * a.mask_words : nullptr;
+            for (int k = warp; k < ncl; k += nw) {
+                const int c = clist[k];
+                const int i = (c << 5) + lane;
+                uint32_t nb = 0u;
+                if (i < words) {
+                    const int y = wd.div(i), w = i - y * WW;
+                    const uint32_t burn = Bc[WW + i];
+                    const uint32_t ig = Bn[WW + i];
+                    const uint32_t ou = D[i] & burn;          // burning cells that burned out
+                    nb = (burn & ~ou) | ig;
+                    my_b += __popc(nb);
+                    my_o += __popc(ou);
+                    const uint32_t m = mrow != nullptr
+                                           ? mask_run(mrow, off + (int64_t)y * W + (w << 5), min(32, W - (w << 5)))
+                                           : drop_bits(y, w, W, cxn, cyn, a.R);
+                    const uint32_t doused = nb & m;
+                    my_x += __popc(doused);
+                    nb &= ~m;
+                    Bn[WW + i] = nb;
+                    D[i] |= doused;
+                    C[i] &= ~ig;
+                }
+                const uint32_t any_nb = __ballot_sync(0xffffffffu, nb != 0u);
+                if (lane == 0) fl_n[c] = any_nb != 0u;
+            }
+        }
+        my_b = __reduce_add_sync(0xffffffffu, my_b);
+        my_o = __reduce_add_sync(0xffffffffu, my_o);
+        my_x = __reduce_add_sync(0xffffffffu, my_x);
+        if (lane == 0) {
+            atomicAdd(&T.cnt[s % 3][0], my_b);
+            atomicAdd(&T.cnt[s % 3][1], my_o);
+            atomicAdd(&T.cnt[s % 3][2], my_x);
+        }
+        __syncthreads();
+        const int32_t nb = T.cnt[s % 3][0];
+        uint32_t* tmp = Bc;
+        Bc = Bn;
+        Bn = tmp;
+        uint8_t* ftmp = fl_c;
+        fl_c = fl_n;
+        fl_n = ftmp;
+        t += 1;
+        const bool done = (nb == 0) || (a.t_max > 0 && t >= a.t_max);
+        if (tid == 0) {
+            const int32_t nd = T.burnt_now + T.cnt[s % 3][1];     // burned after the step
+            T.burnt_now = nd + T.cnt[s % 3][2];                  // and after the next drop
+            T.last_burnt = nd;
+            T.last_nb = nb;
+            const int64_t o = (int64_t)s * a.N + e;
+            if (a.out_burning) a.out_burning[o] = nb;
+            if (a.out_burnt) a.out_burnt[o] = nd;
+            if (a.out_done) a.out_done[o] = done ? 1 : 0;
+        }
+        if (done && a.auto_reset) {
+            // restart from the initial state with a fresh random stream
+            t = 0;
+            ep += 1;
+            for (int i2 = tid; i2 < pw; i2 += NT) Bc[i2] = 0u;
+            if (tid == 0) T.burnt = 0;
+            __syncthreads();
+            res_load(a.F0 + off, H, W, WW, vec, Bc, C, D, tid, NT);
+            __syncthreads();
+            if (T.drop[0] >= 0) {
+                res_action(H, W, WW, Bc, D, T.drop[0], T.drop[1], a.R, tid, NT);
+                __syncthreads();
+            } else if (a.mask != nullptr && next_act) {
+                res_action_mask(a.mask + (int64_t)(s + 1) * a.mask_words, off, H, W, WW, Bc, D, tid, NT);
+                __syncthreads();
+            }
+            // the other buffer may hold stale burning words: mark it active
+            res_init_flags(Bc, D, WW, words, nchunks, fl_c, fl_n, 1, &T.burnt, tid, NT);
+            __syncthreads();
+            if (tid == 0) T.burnt_now = T.burnt;
+            continue;
+        }
+        if (nb == 0) {
+            // fire out: nothing can change any more; fill the remaining steps
+            __syncthreads();
+            const int32_t last_burnt = T.last_burnt;
+            for (int s2 = s + 1 + tid; s2 < a.k; s2 += NT) {
+                const int64_t o = (int64_t)s2 * a.N + e;
+                if (a.out_burning) a.out_burning[o] = 0;
+                if (a.out_burnt) a.out_burnt[o] = last_burnt;
+                if (a.out_done) a.out_done[o] = 1;
+            }
+            t += a.k - (s + 1);
+            break;
+        }
+    }
+    __syncthreads();
+    res_store(Fe, H, W, WW, vec, Bc, C, D, tid, NT);
+    if (a.history != nullptr) {
+        // the last step's state, and the unchanged state of the steps after the fire went out
+        for (int j = hist_done; j < a.k; ++j) res_record(a, j, off, H, W, WW, vec, Bc, C, D, tid, NT);
+    }
+    if (tid == 0) {
+        a.t[e] = t;
+        a.episode[e] = ep;
+        if (a.last_burning != nullptr) a.last_burning[e] = T.last_nb;
+    }
+    __syncthreads();
+}
+
+// Persistent CTAs pull envs from the work queue and step each one with all
+// NT threads.  At most 64 registers a thread: 1024 threads fit an SM.
 template <int NT, bool FUSED>
 __global__ void __launch_bounds__(NT, 1024 / NT)
 k_step_resident(const ResArgs a, const RateConsts Kc) {
     extern __shared__ uint32_t sm[];
-    __shared__ int32_t s_env;
-    __shared__ int32_t s_cnt[3][3];     // burning, new burn-outs, doused (per step)
-    __shared__ int32_t s_qn[3];         // queued work items (per step)
-    __shared__ int32_t s_ncl[3];        // chunks that can change (per step)
-    __shared__ int32_t s_burnt;
-    __shared__ int32_t s_dous;          // cells doused by a drop applied at a step's start
     // the rate constants live in shared memory only in the fused variant
     __shared__ typename std::conditional<FUSED, RateConsts, int>::type sK_store;
     const RateConsts& sK = *reinterpret_cast<const RateConsts*>(&sK_store);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (FUSED) {
         for (int i = threadIdx.x; i < (int)(sizeof(RateConsts) / 4); i += NT)
             reinterpret_cast<float*>(&sK_store)[i] = reinterpret_cast<const float*>(&Kc)[i];
     }
-
+    // per-warp scratch first, then the env's region (its ResEnvShared first)
+    uint32_t* wsc = sm + (threadIdx.x >> 5) * kWarpScratch;
+    uint32_t* Rg = sm + (NT / 32) * kWarpScratch;
+    ResEnvShared& T = *reinterpret_cast<ResEnvShared*>(Rg);
     for (;;) {
         if (threadIdx.x == 0) {
             const uint32_t slot = atomicAdd(&a.queue[0], 1u);
-            s_env = (slot < (uint32_t)a.nq) ? a.order[slot] : -1;
+            T.env = slot < (uint32_t)a.nq ? a.order[slot] : -1;
         }
         __syncthreads();
-        const int e = s_env;
+        const int e = T.env;
         __syncthreads();
         if (e < 0) break;
-
-        const int H = a.H[e], W = a.W[e];
-        const int WW = (W + 31) >> 5;
-        const WordDiv wd(WW);
-        const int pw = (H + 2) * WW;
-        const int words = H * WW;
-        const int nchunks = (words + 31) >> 5;
-        uint32_t* B0 = sm;
-        uint32_t* B1 = B0 + pw;
-        uint32_t* C = B1 + pw;
-        uint32_t* D = C + words;
-        uint32_t* list = D + words + warp * kWarpScratch;      // per-warp scratch
-        uint32_t* ignw = list + kListCap;
-        uint32_t* outw = ignw + 32;
-        uint32_t* plist = outw + 32;
-        // chunk activity flags of the two burning buffers
-        uint8_t* flag0 = reinterpret_cast<uint8_t*>(D + words + (NT / 32) * kWarpScratch);
-        uint8_t* flag1 = flag0 + nchunks;
-        // chunks dealt this step and the block-wide queue of work items
-        int* clist = reinterpret_cast<int*>(flag0 + 2 * ((nchunks + 3) & ~3));
-        uint32_t* Q = reinterpret_cast<uint32_t*>(clist + nchunks);
-        const int reach = (WW + 1 + 31) >> 5;                 // chunks a word's neighbours span
-        const int64_t off = a.off[e];
-        uint8_t* Fe = a.F + off;
-        const bool vec = ((W & 31) == 0) && ((off & 15) == 0);
-
-        // zero both burning planes (the padding rows must read as 0), then load
-        for (int i = threadIdx.x; i < 2 * pw; i += NT) B0[i] = 0u;
-        if (threadIdx.x < 9) s_cnt[threadIdx.x / 3][threadIdx.x % 3] = 0;
-        if (threadIdx.x < 3) {
-            s_qn[threadIdx.x] = 0;
-            s_ncl[threadIdx.x] = 0;
-        }
-        if (threadIdx.x == 0) s_burnt = 0;
-        __syncthreads();
-        res_load(Fe, H, W, WW, vec, B0, C, D);
-        __syncthreads();
-        if (a.drops != nullptr && a.k > 0) {
-            res_action(H, W, WW, B0, D, a.drops[(int64_t)e * 2], a.drops[(int64_t)e * 2 + 1], a.R);
-            __syncthreads();
-        } else if (a.mask != nullptr && a.k > 0) {
-            res_action_mask(a.mask, off, H, W, WW, B0, D);
-            __syncthreads();
-        }
-        res_init_flags(B0, D, WW, words, nchunks, flag0, flag1, 0, &s_burnt);
-        __syncthreads();
-        int32_t burnt_now = s_burnt;
-        uint8_t* fl_c = flag0;
-        uint8_t* fl_n = flag1;
-
-        int32_t t = a.t[e];
-        int32_t ep = a.episode[e];
-        uint32_t* Bc = B0;
-        uint32_t* Bn = B1;
-        int32_t last_burnt = 0;
-        int32_t last_nb = 0;
-        int hist_done = 0;          // history rows written
-        const bool rec = a.history != nullptr;
-        for (int s = 0; s < a.k; ++s) {
-            const uint32_t tt = (uint32_t)t;
-            const uint32_t ep4 = 4u * (uint32_t)ep;
-            if (rec && s > 0) {
-                // record the state after step s - 1, then apply step s's drop
-                // (when recording it is not folded into the previous write-back)
-                res_record(a, s - 1, off, H, W, WW, vec, Bc, C, D);
-                hist_done = s;
-                if (threadIdx.x == 0) s_dous = 0;
-                __syncthreads();
-                if (a.drops != nullptr) {
-                    res_action(H, W, WW, Bc, D, a.drops[((int64_t)s * a.N + e) * 2],
-                               a.drops[((int64_t)s * a.N + e) * 2 + 1], a.R, &s_dous);
-                    __syncthreads();
-                    burnt_now += s_dous;
-                } else if (a.mask != nullptr) {
-                    res_action_mask(a.mask + (int64_t)s * a.mask_words, off, H, W, WW, Bc, D, &s_dous);
-                    __syncthreads();
-                    burnt_now += s_dous;
-                }
-            }
-            if (threadIdx.x == 0) {
-                s_cnt[(s + 1) % 3][0] = 0;
-                s_cnt[(s + 1) % 3][1] = 0;
-                s_cnt[(s + 1) % 3][2] = 0;
-                s_qn[(s + 1) % 3] = 0;
-                s_ncl[(s + 1) % 3] = 0;
-            }
-            // the next step's drop is applied while the new planes are written
-            int cxn = -1, cyn = -1;
-            if (a.drops != nullptr && s + 1 < a.k && !rec) {
-                cxn = a.drops[((int64_t)(s + 1) * a.N + e) * 2];
-                cyn = a.drops[((int64_t)(s + 1) * a.N + e) * 2 + 1];
-            }
-            const uint32_t* mrow =
-                (a.mask != nullptr && s + 1 < a.k && !rec) ? a.mask + (int64_t)(s + 1) * a.mask_words : nullptr;
-            int my_b = 0, my_o = 0, my_x = 0;
-            uint32_t my_pairs = 0, my_blocks = 0, my_burn = 0, my_chunks = 0;
-            // phase A: the chunks that can change are dealt to the warps,
-            // which clear their words of the write buffer and queue their
-            // work items.  A chunk with no burning cell within reach, whose
-            // write buffer holds no burning word, cannot change: it is
-            // skipped.  Every warp finds the needed chunks of a group of 32
-            // with one ballot (lane = chunk); the k-th needed chunk goes to
-            // warp k mod (warps), which also lists it for the write-back.
-            int n_need = 0;                       // needed chunks before this group
-            for (int g0 = 0; g0 < nchunks; g0 += 32) {
-                const int cl = g0 + lane;
-                bool nd = false;
-                if (cl < nchunks) {
-                    nd = fl_n[cl] != 0;
-                    for (int cc = max(cl - reach, 0); cc <= min(cl + reach, nchunks - 1); ++cc) nd |= fl_c[cc] != 0;
-                }
-                const uint32_t need_m = __ballot_sync(0xffffffffu, nd);
-                const int rk = n_need + __popc(need_m & ((1u << lane) - 1u));
-                const bool take = nd && (rk % (NT / 32)) == warp;
-                if (take) clist[rk] = cl;
-                n_need += __popc(need_m);
-                for (uint32_t mine = __ballot_sync(0xffffffffu, take); mine != 0u;) {
-                const int c = g0 + __ffs(mine) - 1;
-                mine &= mine - 1u;
-                ++my_chunks;
-                const int base = c << 5;
-                const int i = base + lane;
-                uint32_t burn = 0, cand = 0;
-                uint32_t sd[8];
-                if (i < words) {
-                    const int w = i - wd.div(i) * WW;
-                    const uint32_t* bp = &Bc[WW + i];             // row y + 1 of the padded plane
-                    const bool hl = w > 0, hr = w + 1 < WW;
-                    const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
-                    const uint32_t uc = bp[-WW], ul = hl ? bp[-WW - 1] : 0u, ur = hr ? bp[-WW + 1] : 0u;
-                    const uint32_t dc = bp[WW], dl = hl ? bp[WW - 1] : 0u, dr = hr ? bp[WW + 1] : 0u;
-                    // source of direction d for target (y, x) sits at (y - DR[d], x - DX[d])
-                    sd[0] = (bc << 1) | (bl >> 31);   // E : (y,   x-1)
-                    sd[1] = (dc << 1) | (dl >> 31);   // NE: (y+1, x-1)
-                    sd[2] = dc;                       // N : (y+1, x)
-                    sd[3] = (dc >> 1) | (dr << 31);   // NW: (y+1, x+1)
-                    sd[4] = (bc >> 1) | (br << 31);   // W : (y,   x+1)
-                    sd[5] = (uc >> 1) | (ur << 31);   // SW: (y-1, x+1)
-                    sd[6] = uc;                       // S : (y-1, x)
-                    sd[7] = (uc << 1) | (ul >> 31);   // SE: (y-1, x-1)
-                    const uint32_t any = sd[0] | sd[1] | sd[2] | sd[3] | sd[4] | sd[5] | sd[6] | sd[7];
-                    cand = C[i] & any;
-                    burn = bc;
-                    Bn[WW + i] = 0u;                  // collects this step's ignitions
-                } else {
-#pragma unroll
-                    for (int d = 0; d < 8; ++d) sd[d] = 0u;
-                }
-                __syncwarp();
-                uint32_t np = 0;
-#pragma unroll
-                for (int d = 0; d < 8; ++d) np += __popc(sd[d] & cand);
-                my_pairs += np;
-                my_blocks += __popc(cand & (sd[0] | sd[1] | sd[2] | sd[3])) +
-                             __popc(cand & (sd[4] | sd[5] | sd[6] | sd[7]));
-                my_burn += __popc(burn);
-                const int n_items = __popc(burn) + (int)(FUSED ? np : __popc(cand));
-                int incl = n_items;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                if (total == 0) continue;
-                int pos = -1;
-                if (lane == 0) {
-                    int old = s_qn[s % 3];
-                    while (old + total <= kResQCap) {
-                        const int prev = atomicCAS(&s_qn[s % 3], old, old + total);
-                        if (prev == old) {
-                            pos = old;
-                            break;
-                        }
-                        old = prev;
-                    }
-                }
-                pos = __shfl_sync(0xffffffffu, pos, 0);
-                if (pos >= 0) {
-                    uint32_t* q = Q + pos + (incl - n_items);
-                    const uint32_t hi = (uint32_t)i << 18;
-                    for (uint32_t m = burn; m != 0u; m &= m - 1u) *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 13);
-                    if (FUSED) {
-#pragma unroll
-                        for (int d = 0; d < 8; ++d)
-                            for (uint32_t m = sd[d] & cand; m != 0u; m &= m - 1u)
-                                *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 13) | (1u << 12) | (uint32_t)d;
-                    } else {
-                        for (uint32_t m = cand; m != 0u; m &= m - 1u) {
-                            const int j = __ffs(m) - 1;
-                            uint32_t dm = 0;
-#pragma unroll
-                            for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
-                            *q++ = hi | ((uint32_t)j << 13) | (1u << 12) | dm;
-                        }
-                    }
-                    continue;
-                }
-                // the queue is full: this warp evaluates the chunk itself
-                // (ignitions into the cleared write-buffer words, burn-outs
-                // into the burned plane)
-                uint32_t* ignw_c = Bn + WW + base;
-                uint32_t* outw_c = D + base;
-                const uint32_t act = cand | burn;
-                const int n_act = __popc(act);
-                int inca = n_act;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, inca, o);
-                    if (lane >= o) inca += v;
-                }
-                const int tot_a = __shfl_sync(0xffffffffu, inca, 31);
-                const int excl = inca - n_act;
-                for (int pass = 0; pass < tot_a; pass += kListCap) {
-                    uint32_t rem = act;
-                    int idx = excl;
-                    while (rem != 0u) {
-                        const int j = __ffs(rem) - 1;
-                        rem &= rem - 1u;
-                        if (idx >= pass && idx < pass + kListCap) {
-                            uint32_t item = ((uint32_t)lane << 5) | (uint32_t)j;
-                            if ((cand >> j) & 1u) {
-                                uint32_t dm = 0;
-#pragma unroll
-                                for (int d = 0; d < 8; ++d) dm |= ((sd[d] >> j) & 1u) << d;
-                                item |= (dm << 10) | (1u << 18);
-                            }
-                            list[idx - pass] = item;
-                        }
-                        ++idx;
-                    }
-                    __syncwarp();
-                    const int n_pass = min(kListCap, tot_a - pass);
-                    for (int it = lane; it < n_pass; it += 32) {
-                        const uint32_t item = list[it];
-                        const int ol = (int)(item >> 5) & 31;
-                        const int j = (int)item & 31;
-                        const int ii = base + ol;
-                        const int yy = wd.div(ii);
-                        const int xx = ((ii - yy * WW) << 5) + j;
-                        const uint32_t cell = (uint32_t)(yy * W + xx);
-                        if (item & (1u << 18)) {
-                            if (!FUSED && ignites(a, e, off, cell, (item >> 10) & 0xFFu, tt, ep4))
-                                atomicOr(&ignw_c[ol], 1u << j);
-                        } else {
-                            const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
-                            if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&outw_c[ol], 1u << j);
-                        }
-                    }
-                    if (FUSED) {
-                        for (int it0 = 0; it0 < n_pass; it0 += 32)
-                            fused_pairs(a, sK, list, plist, ignw_c, it0, n_pass, base, e, off, W, WW, 0, 0, tt,
-                                        ep4, lane);
-                    }
-                    __syncwarp();
-                }
-                }
-            }
-            if (threadIdx.x == 0) s_ncl[s % 3] = n_need;
-            __syncthreads();
-            // phase B: every thread of the CTA evaluates queued items
-            {
-                const int qn = min(s_qn[s % 3], kResQCap);
-                for (int q = threadIdx.x; q < qn; q += NT) {
-                    const uint32_t it = Q[q];
-                    const int ii = (int)(it >> 18), j = (int)(it >> 13) & 31;
-                    const int yy = wd.div(ii);
-                    const int xx = ((ii - yy * WW) << 5) + j;
-                    const uint32_t cell = (uint32_t)(yy * W + xx);
-                    if (!(it & (1u << 12))) {
-                        const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
-                        if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&D[ii], 1u << j);
-                    } else if (FUSED) {
-                        if (pair_ignites(a, sK, e, off, W, yy, xx, (int)(it & 7u), tt, ep4))
-                            atomicOr(&Bn[WW + ii], 1u << j);
-                    } else {
-                        if (ignites(a, e, off, cell, it & 0xFFu, tt, ep4)) atomicOr(&Bn[WW + ii], 1u << j);
-                    }
-                }
-            }
-            __syncthreads();
-            // phase C: the dealt chunks are written back, round-robin over the warps
-            {
-                const int ncl = s_ncl[s % 3];
-                for (int k = warp; k < ncl; k += NT / 32) {
-                    const int c = clist[k];
-                    const int i = (c << 5) + lane;
-                    uint32_t nb = 0u;
-                    if (i < words) {
-                        const int y = wd.div(i), w = i - y * WW;
-                        const uint32_t burn = Bc[WW + i];
-                        const uint32_t ig = Bn[WW + i];
-                        const uint32_t ou = D[i] & burn;          // burning cells that burned out
-                        nb = (burn & ~ou) | ig;
-                        my_b += __popc(nb);
-                        my_o += __popc(ou);
-                        const uint32_t m = mrow != nullptr
-                                               ? mask_run(mrow, off + (int64_t)y * W + (w << 5), min(32, W - (w << 5)))
-                                               : drop_bits(y, w, W, cxn, cyn, a.R);
-                        const uint32_t doused = nb & m;
-                        my_x += __popc(doused);
-                        nb &= ~m;
-                        Bn[WW + i] = nb;
-                        D[i] |= doused;
-                        C[i] &= ~ig;
-                    }
-                    const uint32_t any_nb = __ballot_sync(0xffffffffu, nb != 0u);
-                    if (lane == 0) fl_n[c] = any_nb != 0u;
-                }
-            }
-            // counts of this step (before the next drop)
-            if (a.counts != nullptr && my_chunks) {
-                my_pairs = __reduce_add_sync(0xffffffffu, my_pairs);
-                my_blocks = __reduce_add_sync(0xffffffffu, my_blocks);
-                my_burn = __reduce_add_sync(0xffffffffu, my_burn);
-                if (lane == 0) {
-                    atomicAdd(&a.counts[0], (unsigned long long)my_pairs);
-                    atomicAdd(&a.counts[1], (unsigned long long)my_blocks);
-                    atomicAdd(&a.counts[2], (unsigned long long)my_burn);
-                    atomicAdd(&a.counts[3], 32ull * my_chunks);
-                }
-            }
-            my_b = __reduce_add_sync(0xffffffffu, my_b);
-            my_o = __reduce_add_sync(0xffffffffu, my_o);
-            my_x = __reduce_add_sync(0xffffffffu, my_x);
-            if (lane == 0) {
-                atomicAdd(&s_cnt[s % 3][0], my_b);
-                atomicAdd(&s_cnt[s % 3][1], my_o);
-                atomicAdd(&s_cnt[s % 3][2], my_x);
-            }
-            __syncthreads();
-            const int32_t nb = s_cnt[s % 3][0];
-            const int32_t nd = burnt_now + s_cnt[s % 3][1];      // burned after the step
-            burnt_now = nd + s_cnt[s % 3][2];                   // and after the next drop
-            uint32_t* tmp = Bc;
-            Bc = Bn;
-            Bn = tmp;
-            uint8_t* ftmp = fl_c;
-            fl_c = fl_n;
-            fl_n = ftmp;
-            t += 1;
-            const bool done = (nb == 0) || (a.t_max > 0 && t >= a.t_max);
-            if (threadIdx.x == 0) {
-                const int64_t o = (int64_t)s * a.N + e;
-                if (a.out_burning) a.out_burning[o] = nb;
-                if (a.out_burnt) a.out_burnt[o] = nd;
-                if (a.out_done) a.out_done[o] = done ? 1 : 0;
-            }
-            last_burnt = nd;
-            last_nb = nb;
-            if (done && a.auto_reset) {
-                // restart from the initial state with a fresh random stream
-                t = 0;
-                ep += 1;
-                for (int i2 = threadIdx.x; i2 < pw; i2 += NT) Bc[i2] = 0u;
-                if (threadIdx.x == 0) s_burnt = 0;
-                __syncthreads();
-                res_load(a.F0 + off, H, W, WW, vec, Bc, C, D);
-                __syncthreads();
-                if (cxn >= 0) {
-                    res_action(H, W, WW, Bc, D, cxn, cyn, a.R);
-                    __syncthreads();
-                } else if (mrow != nullptr) {
-                    res_action_mask(mrow, off, H, W, WW, Bc, D);
-                    __syncthreads();
-                }
-                // the other buffer may hold stale burning words: mark it active
-                res_init_flags(Bc, D, WW, words, nchunks, fl_c, fl_n, 1, &s_burnt);
-                __syncthreads();
-                burnt_now = s_burnt;
-                continue;
-            }
-            if (nb == 0) {
-                // fire out: nothing can change any more; fill the remaining steps
-                for (int s2 = s + 1 + (int)threadIdx.x; s2 < a.k; s2 += NT) {
-                    const int64_t o = (int64_t)s2 * a.N + e;
-                    if (a.out_burning) a.out_burning[o] = 0;
-                    if (a.out_burnt) a.out_burnt[o] = last_burnt;
-                    if (a.out_done) a.out_done[o] = 1;
-                }
-                t += a.k - (s + 1);
-                break;
-            }
-        }
-        __syncthreads();
-        res_store(Fe, H, W, WW, vec, Bc, C, D);
-        if (a.history != nullptr) {
-            // the last step's state, and the unchanged state of the steps after the fire went out
-            for (int j = hist_done; j < a.k; ++j) res_record(a, j, off, H, W, WW, vec, Bc, C, D);
-        }
-        if (threadIdx.x == 0) {
-            a.t[e] = t;
-            a.episode[e] = ep;
-            if (a.last_burning != nullptr) a.last_burning[e] = last_nb;
-        }
-        __syncthreads();
+        res_env<NT, FUSED>(a, sK, e, Rg, wsc);
     }
+    __syncthreads();
     // the last CTA to leave resets the queue for the next launch
     if (threadIdx.x == 0) {
         __threadfence();
@@ -761,13 +804,9 @@ void jwf_rate_consts(const jwf_ctx* c, RateConsts* K);
 
 
 size_t jwf_resident_smem(int32_t H, int32_t W, int threads) {
-    const int nwarps = threads / 32;
     // queued work items address words with 14 bits
     if ((int64_t)H * ((W + 31) / 32) >= (int64_t)1 << 14) return (size_t)1 << 40;
-    const int64_t nchunks = ((int64_t)H * ((W + 31) / 32) + 31) / 32;
-    // two chunk-flag byte arrays, the dealt-chunk list and the work queue
-    const int64_t flag_words = 2 * ((nchunks + 3) / 4) + nchunks + kResQCap;
-    return (size_t)(res_plane_words(H, W) + nwarps * kWarpScratch + flag_words) * sizeof(uint32_t);
+    return (size_t)(res_region_words(H, W) + (threads / 32) * kWarpScratch) * sizeof(uint32_t);
 }
 
 int jwf_resident_threads(int32_t H, int32_t W) {
