@@ -173,6 +173,22 @@ JWF_API jwf_status jwf_set_probs(jwf_ctx* ctx, const float* d_q, const float* d_
 /* Borrowed device views of the tables (valid until jwf_destroy). */
 JWF_API jwf_status jwf_get_probs(jwf_ctx* ctx, float** d_q, float** d_r);
 
+/* Diagnostics of the fused step kernels' ignition test (Section 3
+ * "Stochastic update", Eqs. 1-4).  Those kernels compare a pair's draw u with
+ * a plain-float probability p_f and a bound B on |p_f - p|, p the probability
+ * jwf_precompute_probs writes; only a draw within B of p_f takes the exact
+ * double-float rate, so the outcome is always u < p.  For n tuples (target
+ * class d_class_v[i], source class d_class_u[i], elevations d_z_v[i] and
+ * d_z_u[i] in m, the wind part of the exponent at the source as hi + lo in
+ * d_wexp[2i], d_wexp[2i + 1], direction d_dir[i] in 0..7 as in jwf_step) and
+ * the context's parameters, writes d_out[3i .. 3i + 2] = p_f, B, p (float).
+ * All pointers are device memory of n (d_wexp 2n, d_out 3n) elements, read or
+ * written on the stream.  Errors: JWF_ESTATE (no parameters), JWF_EINVAL (null
+ * pointer with n > 0, n < 0). */
+JWF_API jwf_status jwf_check_prob_bound(const jwf_ctx* ctx, int64_t n, const uint8_t* d_class_v,
+                                        const uint8_t* d_class_u, const float* d_z_v, const float* d_z_u,
+                                        const float* d_wexp, const int32_t* d_dir, float* d_out, void* stream);
+
 /* ---- discrete (stochastic) simulation (Section 3, "Stochastic update") --- */
 
 /* Start a run: the initial states d_F0 (uint8 [cells], values 0..3) are

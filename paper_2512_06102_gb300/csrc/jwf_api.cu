@@ -374,6 +374,22 @@ jwf_status jwf_precompute_probs(jwf_ctx* ctx, const uint8_t* d_class, const floa
     return JWF_OK;
 }
 
+jwf_status jwf_check_prob_bound(const jwf_ctx* ctx, int64_t n, const uint8_t* d_class_v, const uint8_t* d_class_u,
+                                const float* d_z_v, const float* d_z_u, const float* d_wexp, const int32_t* d_dir,
+                                float* d_out, void* stream) {
+    if (ctx == nullptr) return JWF_EINVAL;
+    jwf_ctx* c = const_cast<jwf_ctx*>(ctx);
+    if (!ctx->have_params) return fail(c, JWF_ESTATE, "jwf_check_prob_bound: no parameters set");
+    if (n < 0) return fail(c, JWF_EINVAL, "jwf_check_prob_bound: n < 0");
+    if (n > 0 && (d_class_v == nullptr || d_class_u == nullptr || d_z_v == nullptr || d_z_u == nullptr ||
+                  d_wexp == nullptr || d_dir == nullptr || d_out == nullptr))
+        return fail(c, JWF_EINVAL, "jwf_check_prob_bound: null pointer");
+    JWF_CUDA_TRY(c, jwf_launch_prob_check(ctx, n, d_class_v, d_class_u, d_z_v, d_z_u, d_wexp, d_dir, d_out,
+                                          S(stream)),
+                 "jwf_check_prob_bound");
+    return JWF_OK;
+}
+
 jwf_status jwf_set_terrain(jwf_ctx* ctx, const uint8_t* d_class, const float* d_dem,
                            const float* d_wind_speed, const float* d_wind_dir, void* stream) {
     if (ctx == nullptr) return JWF_EINVAL;

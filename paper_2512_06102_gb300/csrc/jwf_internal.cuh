@@ -314,6 +314,9 @@ cudaError_t jwf_launch_agent_warp(const jwf_ctx* c, bool fused, const int32_t* a
                                   int32_t water0, int random_fire, float burn_penalty, float* reward, uint8_t* done,
                                   int32_t obs_k, uint8_t* obs, cudaStream_t s);
 cudaError_t jwf_launch_state_planes(int64_t n, const uint8_t* states, float* pun, float* pburn, cudaStream_t s);
+cudaError_t jwf_launch_prob_check(const jwf_ctx* c, int64_t n, const uint8_t* cv, const uint8_t* cu,
+                                  const float* zv, const float* zu, const float* wexp, const int32_t* dir,
+                                  float* out, cudaStream_t s);
 cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const float* dem,
                                   const float* ws, const float* wd, cudaStream_t s);
 cudaError_t jwf_launch_rates_accumulate(const jwf_ctx* c, int32_t n_steps, const float* glam,

@@ -131,6 +131,26 @@ k_prob_table(const int2* __restrict__ tiles, int64_t n_tiles, const int32_t* __r
     }
 }
 
+// Diagnostics of the step kernels' two-level probability (below_prob): for
+// each tuple i (target and source class, elevations, wind part of the
+// exponent as hi + lo, direction), out[3i .. 3i+2] = p_f, its bound B and the
+// double-float probability.
+__global__ void k_prob_check(int64_t n, const uint8_t* __restrict__ cv, const uint8_t* __restrict__ cu,
+                             const float* __restrict__ zv, const float* __restrict__ zu,
+                             const float2* __restrict__ wexp, const int32_t* __restrict__ dir, const RateConsts K,
+                             float* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int d = dir[i] & 7;
+        const float G = K.G[cv[i] & 15][cu[i] & 15];
+        const float2 w2 = wexp[i];
+        float B = 0.f;
+        const float pf = prob_fast(G, zv[i], zu[i], w2.x, d, K, &B);
+        out[3 * i] = pf;
+        out[3 * i + 1] = B;
+        out[3 * i + 2] = G == 0.f ? 0.f : prob_of(rate_of(G, zv[i], zu[i], {w2.x, w2.y}, d, K));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Deterministic block reduction of NV doubles per thread into out[NV]
 // (valid in thread 0 .. NV-1 of the block after the call).
@@ -470,6 +490,18 @@ void jwf_rate_consts(const jwf_ctx* c, RateConsts* K) {
                                 (1.0 + (double)c->P.mu_den[b]);
             K->G[a][b] = (float)(gamma * base);
         }
+}
+
+cudaError_t jwf_launch_prob_check(const jwf_ctx* c, int64_t n, const uint8_t* cv, const uint8_t* cu,
+                                  const float* zv, const float* zu, const float* wexp, const int32_t* dir,
+                                  float* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    RateConsts K;
+    jwf_rate_consts(c, &K);
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
+    k_prob_check<<<(unsigned)blocks, 256, 0, s>>>(n, cv, cu, zv, zu, reinterpret_cast<const float2*>(wexp), dir, K,
+                                                   out);
+    return cudaGetLastError();
 }
 
 cudaError_t jwf_launch_wind_exponent(const jwf_ctx* c, const float* ws, const float* wd, cudaStream_t s) {

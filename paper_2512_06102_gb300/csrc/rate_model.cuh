@@ -94,3 +94,51 @@ __device__ __forceinline__ float rate_of(float G, float z_v, float z_u, df wexp_
 
 // 1 - exp(-r)
 __device__ __forceinline__ float prob_of(float r) { return -expm1f(-r); }
+
+// The ignition probability in plain float: the steps of rate_of without the
+// lo parts, the exponentials by __expf.  Returns p_f and sets *B to a bound on
+// |p_f - prob_of(rate_of(...))| (four times the sum of the steps' errors):
+//   slope angle                   within 1e-6 rad (reciprocal and quotient by
+//                                 __fdividef, 2 ulp; the node table's hi parts;
+//                                 series truncated at u^7/7 < 1e-14)
+//   exponent E                    within 1.3e-6 |alpha_s 180/pi| + 1.2e-7 |E|
+//   __expf(E)                     within (2 + 1.16 |E|) ulp (its documented bound)
+//   1 - __expf(-r)                within 4e-7 absolute
+//   prob_of(rate_of(...))         within 1e-6 relative of the exact value
+// so |p_f - p| <= |p_f| (1.3e-6 |c_s| + 2.6e-7 |E| + 1.7e-6) + 5e-7.
+__device__ __forceinline__ float prob_fast(float G, float z_v, float z_u, float wexp_hi, int d, const RateConsts& K,
+                                           float* B) {
+    const float x = __fmul_rn(__fsub_rn(z_v, z_u), K.inv_run[d].hi);
+    const float ax = fabsf(x);
+    const bool inv = ax > 1.0f;
+    const float b = inv ? __fdividef(1.0f, ax) : ax;
+    const float est = __fdividef(b, __fmaf_rn(0.28f, __fmul_rn(b, b), 1.0f));
+    int k = __float2int_rn(__fmul_rn(est, 81.48733086305042f));       // 256 / pi
+    k = min(max(k, 0), 64);
+    const float t = K.atan_tan[k].hi;
+    const float v = __fdividef(__fsub_rn(b, t), __fmaf_rn(b, t, 1.0f));
+    const float v2 = __fmul_rn(v, v);
+    float at = __fadd_rn(K.atan_th[k].hi, __fmaf_rn(__fmul_rn(v, v2), __fmaf_rn(v2, 0.2f, -0.33333334f), v));
+    if (inv) at = __fsub_rn(K.half_pi.hi, at);
+    const float slope = x < 0.f ? -at : at;
+    const float E = __fmaf_rn(K.slope_coef.hi, slope, wexp_hi);
+    const float r = __fmul_rn(G, __expf(E));
+    const float p = __fsub_rn(1.0f, __expf(-r));
+    const float rel = __fmaf_rn(5.2e-6f, fabsf(K.slope_coef.hi), __fmaf_rn(1.04e-6f, fabsf(E), 6.8e-6f));
+    *B = __fmaf_rn(fabsf(p), rel, 2.0e-6f);
+    return p;
+}
+
+// u < prob_of(rate_of(G, z_v, z_u, wexp_d, d, K)), for a draw u in [0, 1):
+// decided by prob_fast when u is farther than its bound from p_f (all but a
+// fraction of about 1e-5 of the draws), else by the double-float rate.  The
+// answer is the same either way.
+__device__ __forceinline__ bool below_prob(float u, float G, float z_v, float z_u, df wexp_d, int d,
+                                           const RateConsts& K) {
+    if (G == 0.f) return false;                 // rate 0: probability 0
+    float B;
+    const float p = prob_fast(G, z_v, z_u, wexp_d.hi, d, K, &B);
+    if (u < __fsub_rn(p, B)) return true;
+    if (u >= __fadd_rn(p, B)) return false;
+    return u < prob_of(rate_of(G, z_v, z_u, wexp_d, d, K));
+}

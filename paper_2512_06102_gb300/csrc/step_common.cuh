@@ -50,8 +50,7 @@ __device__ __forceinline__ bool pair_ignites(const Args& a, const RateConsts& K,
     const float2 w2 = a.wexp[((int64_t)ts * a.N + e) * 8 + d];
     const uint4 u4 = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + (uint32_t)(d >> 2)), a.key0, a.key1);
     const uint32_t uw = (d & 3) == 0 ? u4.x : (d & 3) == 1 ? u4.y : (d & 3) == 2 ? u4.z : u4.w;
-    const float r = rate_of(K.G[cv][cu], zv, zu, {w2.x, w2.y}, d, K);
-    return jwf_u24(uw) < prob_of(r);
+    return below_prob(jwf_u24(uw), K.G[cv][cu], zv, zu, {w2.x, w2.y}, d, K);
 }
 
 // Fused variant, up to ILP work items of one thread at once: kind 1 is a
@@ -95,9 +94,9 @@ __device__ __forceinline__ void eval_items(const Args& a, const RateConsts& K, i
     }
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
-        float p = a.p_continue;
-        if (kind[k] == 2) p = prob_of(rate_of(K.G[cv[k]][cu[k]], zv[k], zu[k], {w2[k].x, w2[k].y}, dd[k], K));
-        below[k] = jwf_u24(uw[k]) < p;
+        const float u = jwf_u24(uw[k]);
+        below[k] = kind[k] == 2 ? below_prob(u, K.G[cv[k]][cu[k]], zv[k], zu[k], {w2[k].x, w2[k].y}, dd[k], K)
+                                : u < a.p_continue;
     }
 }
 

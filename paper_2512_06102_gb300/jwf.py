@@ -64,6 +64,7 @@ _SIGS = {
     "jwf_set_probs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "jwf_set_terrain": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_get_probs": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "jwf_check_prob_bound": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "jwf_load_state": (ctypes.c_int, [_VP, _VP, _VP]),
     "jwf_reset": (ctypes.c_int, [_VP, _VP, _VP]),
     "jwf_apply_action": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -363,6 +364,22 @@ class Sim:
         qt = _view(q.value, (self.cells, 8), torch.float32)
         rt = _view(r.value, (self.cells, 8), torch.float32) if r.value else None
         return qt, rt
+
+    def check_prob_bound(self, class_v, class_u, z_v, z_u, wexp, direction, stream=None):
+        """jwf_check_prob_bound: (p_f, B, p) float32 [n, 3] of the fused step's
+        two-level ignition probability for n pair tuples (wexp float32 [n, 2]
+        as hi, lo)."""
+        n = int(class_v.numel())
+        for name, t, k, dt in (("class_v", class_v, n, torch.uint8), ("class_u", class_u, n, torch.uint8),
+                               ("z_v", z_v, n, torch.float32), ("z_u", z_u, n, torch.float32),
+                               ("wexp", wexp, 2 * n, torch.float32), ("direction", direction, n, torch.int32)):
+            if not isinstance(t, torch.Tensor) or t.dtype != dt or t.numel() != k:
+                raise ValueError(f"{name} must be a {dt} tensor of {k} elements")
+        out = torch.empty((n, 3), dtype=torch.float32, device=class_v.device)
+        self._check(lib().jwf_check_prob_bound(self._h, n, _ptr(class_v), _ptr(class_u), _ptr(z_v), _ptr(z_u),
+                                               _ptr(wexp), _ptr(direction), _ptr(out), _stream(stream)),
+                    "jwf_check_prob_bound")
+        return out
 
     # -- discrete simulation -----------------------------------------------
     def load_state(self, F0, stream=None):
