@@ -31,6 +31,7 @@
 namespace {
 
 constexpr int kResQCap = 1024;     // block-wide work items per step (resident step)
+constexpr uint32_t kResVoid = 0xffffffffu;   // a voided queue slot (real items have bits 8..11 clear)
 
 struct ResArgs {
     const int32_t* H;
@@ -477,20 +478,16 @@ __device__ __forceinline__ void res_env(const ResArgs& a, const RateConsts& sK, 
             }
             const int total = __shfl_sync(0xffffffffu, incl, 31);
             if (total == 0) continue;
-            int pos = -1;
-            if (lane == 0) {
-                int old = T.qn[s % 3];
-                while (old + total <= kResQCap) {
-                    const int prev = atomicCAS(&T.qn[s % 3], old, old + total);
-                    if (prev == old) {
-                        pos = old;
-                        break;
-                    }
-                    old = prev;
-                }
-            }
-            pos = __shfl_sync(0xffffffffu, pos, 0);
-            if (pos >= 0) {
+            // one reservation of `total` slots; one that runs past the
+            // capacity voids the slots it got and the warp evaluates the
+            // chunk itself
+            int old = 0;
+            if (lane == 0) old = atomicAdd(&T.qn[s % 3], total);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            const int pos = old + total <= kResQCap ? old : -1;
+            if (pos < 0) {
+                for (int j = old + lane; j < min(kResQCap, old + total); j += 32) Q[j] = kResVoid;
+            } else {
                 uint32_t* q = Q + pos + (incl - n_items);
                 const uint32_t hi = (uint32_t)i << 18;
                 for (uint32_t m = burn; m != 0u; m &= m - 1u) *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 13);
@@ -577,6 +574,7 @@ __device__ __forceinline__ void res_env(const ResArgs& a, const RateConsts& sK, 
             const int qn = min(T.qn[s % 3], kResQCap);
             for (int q = tid; q < qn; q += NT) {
                 const uint32_t it = Q[q];
+                if (it == kResVoid) continue;
                 const int ii = (int)(it >> 18), j = (int)(it >> 13) & 31;
                 const int yy = wd.div(ii);
                 const int xx = ((ii - yy * WW) << 5) + j;
