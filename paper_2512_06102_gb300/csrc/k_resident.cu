@@ -578,15 +578,19 @@ __device__ __forceinline__ void res_env(const ResArgs& a, const RateConsts& sK, 
                 const int ii = (int)(it >> 18), j = (int)(it >> 13) & 31;
                 const int yy = wd.div(ii);
                 const int xx = ((ii - yy * WW) << 5) + j;
-                const uint32_t cell = (uint32_t)(yy * W + xx);
-                if (!(it & (1u << 12))) {
-                    const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
-                    if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&D[ii], 1u << j);
-                } else if (FUSED) {
-                    if (pair_ignites(a, sK, e, off, W, yy, xx, (int)(it & 7u), tt, ep4))
-                        atomicOr(&Bn[WW + ii], 1u << j);
+                const bool pair = (it & (1u << 12)) != 0u;
+                if (FUSED) {
+                    const bool below = item_below(a, sK, e, off, W, yy, xx, pair, (int)(it & 7u), tt, ep4);
+                    if (pair && below) atomicOr(&Bn[WW + ii], 1u << j);
+                    if (!pair && !below) atomicOr(&D[ii], 1u << j);
                 } else {
-                    if (ignites(a, e, off, cell, it & 0xFFu, tt, ep4)) atomicOr(&Bn[WW + ii], 1u << j);
+                    const uint32_t cell = (uint32_t)(yy * W + xx);
+                    if (!pair) {
+                        const uint4 u = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + 2u), a.key0, a.key1);
+                        if (!(jwf_u24(u.x) < a.p_continue)) atomicOr(&D[ii], 1u << j);
+                    } else if (ignites(a, e, off, cell, it & 0xFFu, tt, ep4)) {
+                        atomicOr(&Bn[WW + ii], 1u << j);
+                    }
                 }
             }
         }

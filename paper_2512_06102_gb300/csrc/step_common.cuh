@@ -33,24 +33,44 @@ __device__ __forceinline__ bool ignites(const Args& a, int e, int64_t off, uint3
     return ign;
 }
 
+// Fused variant, one work item: a compared (target, source) pair in
+// direction d (pair = true: does the burning source ignite can-burn cell
+// (yy, xx) of env e this step?) or a burning cell's remain-burning draw (pair
+// = false: does cell (yy, xx) keep burning?).  Both kinds take one Philox
+// block (a warp whose items mix the kinds runs it once); a pair's rate of
+// Eqs. 1-4 is evaluated on the spot (rate_model.cuh, as the table kernel
+// does) and compared with the Philox word of its direction.
+template <class Args>
+__device__ __forceinline__ bool item_below(const Args& a, const RateConsts& K, int e, int64_t off, int W, int yy,
+                                           int xx, bool pair, int d, uint32_t tt, uint32_t ep4) {
+    const uint32_t cell = (uint32_t)(yy * W + xx);
+    int cv = 0, cu = 0;
+    float zv = 0.f, zu = 0.f;
+    float2 w2 = make_float2(0.f, 0.f);
+    if (pair) {
+        const int64_t v = off + cell;
+        const int64_t u = off + (int64_t)(yy - jwf_dr(d)) * W + (xx - jwf_dx(d));
+        cv = a.cls[v];
+        cu = a.cls[u];
+        zv = a.dem[v];
+        zu = a.dem[u];
+        // a wind series is indexed by the step within the episode (held at its last entry)
+        const int ts = a.wser_n > 0 ? min((int)tt, a.wser_n - 1) : 0;
+        w2 = a.wexp[((int64_t)ts * a.N + e) * 8 + d];
+    }
+    const uint4 u4 =
+        jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + (pair ? (uint32_t)(d >> 2) : 2u)), a.key0, a.key1);
+    const uint32_t uw = !pair ? u4.x : (d & 3) == 0 ? u4.x : (d & 3) == 1 ? u4.y : (d & 3) == 2 ? u4.z : u4.w;
+    const float u = jwf_u24(uw);
+    return pair ? below_prob(u, K.G[cv][cu], zv, zu, {w2.x, w2.y}, d, K) : u < a.p_continue;
+}
+
 // Fused variant, one (target, source) pair: does the burning source in
-// direction d ignite can-burn cell (yy, xx) of env e this step?  The rate of
-// Eqs. 1-4 is evaluated on the spot (rate_model.cuh, as the table kernel does)
-// and compared with the Philox word of that direction.
+// direction d ignite can-burn cell (yy, xx) of env e this step?
 template <class Args>
 __device__ __forceinline__ bool pair_ignites(const Args& a, const RateConsts& K, int e, int64_t off, int W, int yy,
                                              int xx, int d, uint32_t tt, uint32_t ep4) {
-    const uint32_t cell = (uint32_t)(yy * W + xx);
-    const int64_t v = off + cell;
-    const int64_t u = off + (int64_t)(yy - jwf_dr(d)) * W + (xx - jwf_dx(d));
-    const int cv = a.cls[v], cu = a.cls[u];
-    const float zv = a.dem[v], zu = a.dem[u];
-    // a wind series is indexed by the step within the episode (held at its last entry)
-    const int ts = a.wser_n > 0 ? min((int)tt, a.wser_n - 1) : 0;
-    const float2 w2 = a.wexp[((int64_t)ts * a.N + e) * 8 + d];
-    const uint4 u4 = jwf_philox(make_uint4(cell, tt, (uint32_t)e, ep4 + (uint32_t)(d >> 2)), a.key0, a.key1);
-    const uint32_t uw = (d & 3) == 0 ? u4.x : (d & 3) == 1 ? u4.y : (d & 3) == 2 ? u4.z : u4.w;
-    return below_prob(jwf_u24(uw), K.G[cv][cu], zv, zu, {w2.x, w2.y}, d, K);
+    return item_below(a, K, e, off, W, yy, xx, true, d, tt, ep4);
 }
 
 // Fused variant, up to ILP work items of one thread at once: kind 1 is a
