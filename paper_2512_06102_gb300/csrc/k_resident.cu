@@ -429,7 +429,7 @@ __device__ __forceinline__ void res_env(const ResArgs& a, const RateConsts& sK, 
             uint32_t burn = 0, cand = 0;
             uint32_t sd[8];
             if (i < words) {
-                const int w = i - wd.div(i) * WW;
+                const int yw = wd.div(i), w = i - yw * WW;
                 const uint32_t* bp = &Bc[WW + i];             // row y + 1 of the padded plane
                 const bool hl = w > 0, hr = w + 1 < WW;
                 const uint32_t bc = bp[0], bl = hl ? bp[-1] : 0u, br = hr ? bp[1] : 0u;
@@ -446,6 +446,21 @@ __device__ __forceinline__ void res_env(const ResArgs& a, const RateConsts& sK, 
                 sd[7] = (uc << 1) | (ul >> 31);   // SE: (y-1, x-1)
                 const uint32_t any = sd[0] | sd[1] | sd[2] | sd[3] | sd[4] | sd[5] | sd[6] | sd[7];
                 cand = C[i] & any;
+                if (FUSED && cand != 0u) {
+                    // the landcover and elevation of the candidates and of their
+                    // sources' rows, wanted by phase B
+                    const int64_t g = off + (int64_t)yw * W + (w << 5);
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(a.dem + g));
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(a.cls + g));
+                    if (yw > 0) {
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.dem + g - W));
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.cls + g - W));
+                    }
+                    if (yw + 1 < H) {
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.dem + g + W));
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.cls + g + W));
+                    }
+                }
                 burn = bc;
                 Bn[WW + i] = 0u;                  // collects this step's ignitions
             } else {
