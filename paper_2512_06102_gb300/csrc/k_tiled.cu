@@ -36,6 +36,7 @@ constexpr int kTileFlagBytes = (kRegionChunks + 3) / 4 * 4;
 // block-wide queue of the step's work items (burning-cell draws and compared
 // pairs); a chunk whose items do not fit is evaluated by its own warp
 constexpr int kQCap = 4096;
+constexpr uint32_t kTileVoid = 0xffffffffu;   // a voided queue slot (real items have bits 8..13 clear)
 
 struct TileArgs {
     const int32_t* H;
@@ -593,20 +594,16 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             }
             const int total = __shfl_sync(0xffffffffu, incl, 31);
             if (total == 0) continue;
-            int pos = -1;
-            if (lane == 0) {
-                int old = s_qn[s % 3];
-                while (old + total <= kQCap) {
-                    const int prev = atomicCAS(&s_qn[s % 3], old, old + total);
-                    if (prev == old) {
-                        pos = old;
-                        break;
-                    }
-                    old = prev;
-                }
-            }
-            pos = __shfl_sync(0xffffffffu, pos, 0);
-            if (pos >= 0) {
+            // one reservation of `total` slots; one that runs past the
+            // capacity voids the slots it got and the warp evaluates the
+            // chunk itself
+            int old = 0;
+            if (lane == 0) old = atomicAdd(&s_qn[s % 3], total);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            const int pos = old + total <= kQCap ? old : -1;
+            if (pos < 0) {
+                for (int j = old + lane; j < min(kQCap, old + total); j += 32) Q[j] = kTileVoid;
+            } else {
                 uint32_t* q = Q + pos + (incl - n_items);
                 const uint32_t hi = (uint32_t)i << 20;
                 for (uint32_t m = burn; m != 0u; m &= m - 1u) *q++ = hi | ((uint32_t)(__ffs(m) - 1) << 15);
@@ -695,12 +692,22 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
 #pragma unroll
                 for (int k = 0; k < ILP; ++k) {
                     const int q = q0 + k * NT;
-                    const uint32_t it = Q[q < qn ? q : q0];
+                    const uint32_t it = q < qn ? Q[q] : kTileVoid;
+                    if (it == kTileVoid) {
+                        // no item: the tile's first cell, nothing loaded for it
+                        yy[k] = ty0;
+                        xx[k] = tx0;
+                        kind[k] = 0;
+                        dd[k] = 0;
+                        iis[k] = 0;
+                        js[k] = 0;
+                        continue;
+                    }
                     const int ii = (int)(it >> 20), j = (int)(it >> 15) & 31;
                     const int ry = wd.div(ii);
                     yy[k] = oy + ry;
                     xx[k] = ox + ((ii - ry * WW) << 5) + j;
-                    kind[k] = q < qn ? ((it & (1u << 14)) ? 2 : 1) : 0;
+                    kind[k] = (it & (1u << 14)) ? 2 : 1;
                     dd[k] = (int)(it & 7u);
                     iis[k] = ii;
                     js[k] = j;
@@ -717,6 +724,7 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
             const int qn = min(s_qn[s % 3], kQCap);
             for (int q = threadIdx.x; q < qn; q += NT) {
                 const uint32_t it = Q[q];
+                if (it == kTileVoid) continue;
                 const int ii = (int)(it >> 20), j = (int)(it >> 15) & 31;
                 const int ry = wd.div(ii);
                 const int gy = oy + ry, gx = ox + ((ii - ry * WW) << 5) + j;

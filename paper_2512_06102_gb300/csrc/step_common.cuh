@@ -75,8 +75,7 @@ __device__ __forceinline__ bool pair_ignites(const Args& a, const RateConsts& K,
 
 // Fused variant, up to ILP work items of one thread at once: kind 1 is a
 // burning cell's remain-burning draw, kind 2 a compared (target, source)
-// pair in direction d, kind 0 no item (its coordinates must still be a cell
-// of the env).  The items' memory loads, Philox blocks and rates are issued
+// pair in direction d, kind 0 no item.  Terrain is loaded for pairs only.  The items' memory loads, Philox blocks and rates are issued
 // stage by stage across the items, so that their latencies overlap.  below[k]
 // = the item's uniform is below its probability: for a pair the source
 // ignites the target (as pair_ignites), for a draw the cell keeps burning.
@@ -93,15 +92,19 @@ __device__ __forceinline__ void eval_items(const Args& a, const RateConsts& K, i
 #pragma unroll
     for (int k = 0; k < ILP; ++k) {
         cell[k] = (uint32_t)(yy[k] * W + xx[k]);
-        const bool pair = kind[k] == 2;
-        const int d = pair ? dd[k] : 0;
-        const int64_t v = off + cell[k];
-        const int64_t u = pair ? off + (int64_t)(yy[k] - jwf_dr(d)) * W + (xx[k] - jwf_dx(d)) : v;
-        cv[k] = a.cls[v];
-        cu[k] = a.cls[u];
-        zv[k] = a.dem[v];
-        zu[k] = a.dem[u];
-        w2[k] = wx[d];
+        cv[k] = cu[k] = 0;
+        zv[k] = zu[k] = 0.f;
+        w2[k] = make_float2(0.f, 0.f);
+        if (kind[k] == 2) {
+            const int d = dd[k];
+            const int64_t v = off + cell[k];
+            const int64_t u = off + (int64_t)(yy[k] - jwf_dr(d)) * W + (xx[k] - jwf_dx(d));
+            cv[k] = a.cls[v];
+            cu[k] = a.cls[u];
+            zv[k] = a.dem[v];
+            zu[k] = a.dem[u];
+            w2[k] = wx[d];
+        }
     }
     uint32_t uw[ILP];
 #pragma unroll
