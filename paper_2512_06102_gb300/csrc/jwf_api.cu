@@ -242,9 +242,12 @@ jwf_status jwf_create(const jwf_config* cfg, jwf_ctx** out) {
     if (err == cudaSuccess) err = dev_alloc(&c->d_tact[1], tiles4.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_tsync, tiles4.size());
     if (err == cudaSuccess) err = dev_alloc(&c->d_tburnt, tiles4.size());
-    if (err == cudaSuccess) err = dev_alloc(&c->d_tcnt, (size_t)16 * 2 * N);
-    if (err == cudaSuccess) err = dev_alloc(&c->d_tplan, (size_t)4 + N + 2 * tiles4.size());
+    // two of each: a round's close and the next round's plan run in one launch
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tcnt, (size_t)2 * 16 * 2 * N);
+    const size_t plan_words = (size_t)4 + N + 2 * tiles4.size();
+    if (err == cudaSuccess) err = dev_alloc(&c->d_tplan, 2 * plan_words);
     if (err == cudaSuccess) err = cudaMemset(c->d_tplan, 0, ((size_t)4 + N) * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMemset(c->d_tplan + plan_words, 0, ((size_t)4 + N) * sizeof(int32_t));
     if (err == cudaSuccess)
         err = cudaMemcpy(c->d_tiles4, tiles4.data(), tiles4.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (err == cudaSuccess)

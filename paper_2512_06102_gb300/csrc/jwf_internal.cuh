@@ -251,6 +251,7 @@ struct jwf_ctx {
     int relaxed_kernel = 0;              // 0: tiled (fused adjoint), 1: plain (two-pass adjoint)
     uint16_t* d_tact[2] = {nullptr, nullptr};
     int tact_cur = 0;
+    int tplan_cur = 0;                   // which of the two round plans (and count scratch) the next round uses
     uint8_t* d_tsync = nullptr;
     // tensor maps of the tiled step, per env: [2 buffers][region box, tile box][N]
     // (built at creation for envs whose rows start 16-byte aligned), and the

@@ -159,12 +159,33 @@ __device__ __forceinline__ uint32_t col_bits(int w, int c0, int c1) {
 // its env's sum, its activity for the next round is none, and when the other
 // buffer does not hold its interior yet it goes to the copy list.  The plan
 // kernel also zeroes the round's per-step count scratch.
-__global__ void __launch_bounds__(256)
-k_tile_plan(int64_t n_tiles, const int4* __restrict__ tiles, const int4* __restrict__ env_tiles,
-            const uint16_t* __restrict__ act_in, uint16_t* __restrict__ act_out, const uint8_t* __restrict__ synced,
-            const int32_t* __restrict__ tile_burnt, int32_t N, int32_t* __restrict__ plan,
-            int32_t* __restrict__ cnt, int64_t n_cnt) {
-    const int64_t tix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+struct PlanArgs {
+    int64_t n_tiles;
+    const int4* tiles;
+    const int4* env_tiles;
+    const uint16_t* act_in;
+    uint16_t* act_out;
+    const uint8_t* synced;
+    const int32_t* tile_burnt;
+    int32_t N;
+    int32_t* plan;
+    int32_t* cnt;
+    int64_t n_cnt;
+};
+
+// The plan's work for tile tix (every thread of the grid, full warps).
+__device__ __forceinline__ void tile_plan_part(const PlanArgs& p, int64_t tix) {
+    const int64_t n_tiles = p.n_tiles;
+    const int4* __restrict__ tiles = p.tiles;
+    const int4* __restrict__ env_tiles = p.env_tiles;
+    const uint16_t* __restrict__ act_in = p.act_in;
+    uint16_t* __restrict__ act_out = p.act_out;
+    const uint8_t* __restrict__ synced = p.synced;
+    const int32_t* __restrict__ tile_burnt = p.tile_burnt;
+    const int32_t N = p.N;
+    int32_t* __restrict__ plan = p.plan;
+    int32_t* __restrict__ cnt = p.cnt;
+    const int64_t n_cnt = p.n_cnt;
     for (int64_t i = tix; i < n_cnt; i += (int64_t)gridDim.x * blockDim.x) cnt[i] = 0;
     const int lane = threadIdx.x & 31;
     bool active = false, copy = false;
@@ -200,6 +221,10 @@ k_tile_plan(int64_t n_tiles, const int4* __restrict__ tiles, const int4* __restr
     int32_t* act_list = plan + 4 + N;
     if (active) act_list[base_a + __popc(am & below)] = (int32_t)tix;
     if (copy) act_list[n_tiles + base_c + __popc(cm & below)] = (int32_t)tix;
+}
+
+__global__ void __launch_bounds__(256) k_tile_plan(const PlanArgs p) {
+    tile_plan_part(p, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Tile activity and burned interior cells from a state buffer, one CTA per
@@ -874,10 +899,25 @@ k_step_tiled(const TileArgs a, const RateConsts Kc) {
 // After a round: per-step outputs (burned = the active tiles' per-step
 // counts + the quiet tiles' cells), done flags and t += kb, one thread per
 // env; the plan's header and per-env sums are cleared for the next round.
-__global__ void k_round_finalize(int32_t N, int32_t kb, const int32_t* __restrict__ cnt, int32_t* __restrict__ plan,
-                                 int32_t* __restrict__ t, int32_t t_max, int32_t* __restrict__ burning,
-                                 int32_t* __restrict__ burnt, uint8_t* __restrict__ done) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+struct FinalArgs {
+    int32_t N, kb;
+    const int32_t* cnt;
+    int32_t* plan;
+    int32_t* t;
+    int32_t t_max;
+    int32_t* burning;
+    int32_t* burnt;
+    uint8_t* done;
+};
+
+__device__ __forceinline__ void round_finalize_part(const FinalArgs& f, int e) {
+    const int32_t N = f.N, kb = f.kb, t_max = f.t_max;
+    const int32_t* __restrict__ cnt = f.cnt;
+    int32_t* __restrict__ plan = f.plan;
+    int32_t* __restrict__ t = f.t;
+    int32_t* __restrict__ burning = f.burning;
+    int32_t* __restrict__ burnt = f.burnt;
+    uint8_t* __restrict__ done = f.done;
     if (e == 0) {
         plan[0] = 0;
         plan[1] = 0;
@@ -895,6 +935,16 @@ __global__ void k_round_finalize(int32_t N, int32_t kb, const int32_t* __restric
         if (done) done[o] = (nb == 0 || (t_max > 0 && t0 + s + 1 >= t_max)) ? 1 : 0;
     }
     t[e] = t0 + kb;
+}
+
+__global__ void k_round_finalize(const FinalArgs f) { round_finalize_part(f, blockIdx.x * blockDim.x + threadIdx.x); }
+
+// A round's close and the next round's plan in one launch: the two rounds'
+// plans and count scratch are separate buffers, so the parts share no data.
+__global__ void __launch_bounds__(256) k_round_next(const FinalArgs f, const PlanArgs p) {
+    const int64_t tix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tix < f.N) round_finalize_part(f, (int)tix);
+    tile_plan_part(p, tix);
 }
 
 constexpr int kMaxDev = 64;
@@ -951,16 +1001,37 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, c
         K = RateConsts{};
     int32_t rs = (c->round_steps >= 1 && c->round_steps <= kMaxRound) ? c->round_steps : kMaxRound;
     if (c->hist != nullptr) rs = 1;     // recording: the state after every step
-    for (int32_t s0 = 0; s0 < k; s0 += rs) {
-        const int32_t kb = (k - s0) < rs ? (k - s0) : rs;
-        // the plan: active tiles, quiet tiles to copy, the quiet tiles' burned
-        // cells per env (and the round's count scratch zeroed)
-        const int64_t n_cnt = (int64_t)kb * 2 * c->N;
-        k_tile_plan<<<(unsigned)((c->n_tiles4 + 255) / 256), 256, 0, s>>>(
-            c->n_tiles4, c->d_tiles4, c->d_env_tiles, c->d_tact[c->tact_cur], c->d_tact[c->tact_cur ^ 1],
-            c->d_tsync, c->d_tburnt, c->N, c->d_tplan, c->d_tcnt, n_cnt);
+    // rounds alternate between two plans and two count scratch buffers: the
+    // launch that closes a round also plans the next one
+    const int64_t plan_words = 4 + (int64_t)c->N + 2 * c->n_tiles4;
+    const int64_t cnt_words = (int64_t)kMaxRound * 2 * c->N;
+    const unsigned plan_blocks = (unsigned)((c->n_tiles4 + 255) / 256);
+    auto plan_args = [&](int buf, int32_t kb_r) {
+        PlanArgs p;
+        p.n_tiles = c->n_tiles4;
+        p.tiles = c->d_tiles4;
+        p.env_tiles = c->d_env_tiles;
+        // the round reads the activity the previous round left (tact_cur)
+        p.act_in = c->d_tact[c->tact_cur];
+        p.act_out = c->d_tact[c->tact_cur ^ 1];
+        p.synced = c->d_tsync;
+        p.tile_burnt = c->d_tburnt;
+        p.N = c->N;
+        p.plan = c->d_tplan + buf * plan_words;
+        p.cnt = c->d_tcnt + buf * cnt_words;
+        p.n_cnt = (int64_t)kb_r * 2 * c->N;
+        return p;
+    };
+    if (k > 0) {
+        // the first round's plan: active tiles, quiet tiles to copy, the quiet
+        // tiles' burned cells per env (and the round's count scratch zeroed)
+        k_tile_plan<<<plan_blocks, 256, 0, s>>>(plan_args(c->tplan_cur, k < rs ? k : rs));
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
+    }
+    for (int32_t s0 = 0; s0 < k; s0 += rs) {
+        const int32_t kb = (k - s0) < rs ? (k - s0) : rs;
+        const int pb = c->tplan_cur;
         TileArgs a;
         a.H = c->d_H;
         a.W = c->d_W;
@@ -980,7 +1051,7 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, c
         a.mask_words = mw;
         a.t = c->d_t;
         a.episode = c->d_episode;
-        a.cnt = c->d_tcnt;
+        a.cnt = c->d_tcnt + pb * cnt_words;
         a.act_in = c->d_tact[c->tact_cur];
         a.act_out = c->d_tact[c->tact_cur ^ 1];
         a.synced = c->d_tsync;
@@ -994,7 +1065,7 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, c
         a.status = c->d_status;
         a.wait_ns = c->tma_wait_ns;
         a.diag_no_copy = c->tma_diag_no_copy ? 1 : 0;
-        a.plan = c->d_tplan;
+        a.plan = c->d_tplan + pb * plan_words;
         a.n_tiles = c->n_tiles4;
         a.kb = kb;
         a.R = c->drop_radius;
@@ -1010,13 +1081,28 @@ cudaError_t jwf_launch_step_tiled(jwf_ctx* c, int32_t k, const int32_t* drops, c
             err = fused ? launch_tiled_t<256, true>(c, a, K, s) : launch_tiled_t<256, false>(c, a, K, s);
         if (err != cudaSuccess) return err;
         const int64_t o = (int64_t)s0 * c->N;
-        k_round_finalize<<<(c->N + 255) / 256, 256, 0, s>>>(c->N, kb, c->d_tcnt, c->d_tplan, c->d_t, c->t_max,
-                                                             burning ? burning + o : nullptr,
-                                                             burnt ? burnt + o : nullptr, done ? done + o : nullptr);
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
+        FinalArgs f;
+        f.N = c->N;
+        f.kb = kb;
+        f.cnt = c->d_tcnt + pb * cnt_words;
+        f.plan = c->d_tplan + pb * plan_words;
+        f.t = c->d_t;
+        f.t_max = c->t_max;
+        f.burning = burning ? burning + o : nullptr;
+        f.burnt = burnt ? burnt + o : nullptr;
+        f.done = done ? done + o : nullptr;
+        const int32_t s1 = s0 + kb;
         c->cur ^= 1;
         c->tact_cur ^= 1;
+        c->tplan_cur ^= 1;
+        if (s1 < k) {
+            // close this round and plan the next in one launch
+            k_round_next<<<plan_blocks, 256, 0, s>>>(f, plan_args(c->tplan_cur, (k - s1) < rs ? (k - s1) : rs));
+        } else {
+            k_round_finalize<<<(c->N + 255) / 256, 256, 0, s>>>(f);
+        }
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
         if (c->hist != nullptr) {
             err = jwf_record_row(c, s0, s);
             if (err != cudaSuccess) return err;
