@@ -287,20 +287,34 @@ constexpr int kR2H = JWF_R2_ROWS, kR2W = JWF_R2_COLS;
 constexpr int kF2T = 256;                                           // threads of the two-step CTA
 constexpr int kA1H = kR2H + 2, kA1W = kR2W + 2, kA1N = kA1H * kA1W;  // cells of step t (tile + 1)
 constexpr int kA0H = kR2H + 4, kA0W = kR2W + 4, kA0N = kA0H * kA0W;  // p_burn read by step t (tile + 2)
+// A stage's buffers; the masks' only when the pass has tanker masks (without
+// them a CTA needs less shared memory and more CTAs fit an SM).
+template <bool MASKED>
 struct Fwd2Stage {
     float r[kA1N * 8];
     float pu[kA1N];
     float pb[kA0N], m0[kA0N];
     float m1[kA1N];
 };
+template <>
+struct Fwd2Stage<false> {
+    float r[kA1N * 8];
+    float pu[kA1N];
+    float pb[kA0N];
+};
+template <bool MASKED>
 struct Fwd2Smem {
-    Fwd2Stage st[2];
+    Fwd2Stage<MASKED> st[2];
     float pb1[kA1N];    // p_burn after step t (masked for step t + 1 before use)
     float pu1[kA1N];    // p_un after step t
 };
-size_t fwd2_smem_bytes() { return sizeof(Fwd2Smem); }
+template <bool MASKED>
+size_t fwd2_smem_bytes() {
+    return sizeof(Fwd2Smem<MASKED>);
+}
 
-__device__ __forceinline__ void fwd2_stage(Fwd2Stage& b, const int4* __restrict__ tiles, int64_t ti,
+template <bool MASKED>
+__device__ __forceinline__ void fwd2_stage(Fwd2Stage<MASKED>& b, const int4* __restrict__ tiles, int64_t ti,
                                            const int32_t* __restrict__ Hs, const int32_t* __restrict__ Ws,
                                            const int64_t* __restrict__ offs, const float* __restrict__ r,
                                            const float* __restrict__ pun, const float* __restrict__ pburn,
@@ -313,34 +327,39 @@ __device__ __forceinline__ void fwd2_stage(Fwd2Stage& b, const int4* __restrict_
         const int y = y0 - 1 + i / kA1W, x = x0 - 1 + i % kA1W;
         if (y < 0 || y >= H || x < 0 || x >= W) {
             b.pu[i] = 0.f;
-            b.m1[i] = 0.f;
+            if constexpr (MASKED) b.m1[i] = 0.f;
             continue;
         }
         const int64_t v = off + (int64_t)y * W + x;
         jwf_cp_async16(&b.r[i * 8], r + v * 8);
         jwf_cp_async16(&b.r[i * 8 + 4], r + v * 8 + 4);
         jwf_cp_async4(&b.pu[i], pun + v);
-        if (mask1 != nullptr)
-            jwf_cp_async4(&b.m1[i], mask1 + v);
-        else
-            b.m1[i] = 0.f;
+        if constexpr (MASKED) {
+            if (mask1 != nullptr)
+                jwf_cp_async4(&b.m1[i], mask1 + v);
+            else
+                b.m1[i] = 0.f;
+        }
     }
     for (int i = threadIdx.x; i < kA0N; i += kF2T) {
         const int y = y0 - 2 + i / kA0W, x = x0 - 2 + i % kA0W;
         if (y < 0 || y >= H || x < 0 || x >= W) {
             b.pb[i] = 0.f;
-            b.m0[i] = 0.f;
+            if constexpr (MASKED) b.m0[i] = 0.f;
             continue;
         }
         const int64_t v = off + (int64_t)y * W + x;
         jwf_cp_async4(&b.pb[i], pburn + v);
-        if (mask0 != nullptr)
-            jwf_cp_async4(&b.m0[i], mask0 + v);
-        else
-            b.m0[i] = 0.f;
+        if constexpr (MASKED) {
+            if (mask0 != nullptr)
+                jwf_cp_async4(&b.m0[i], mask0 + v);
+            else
+                b.m0[i] = 0.f;
+        }
     }
 }
 
+template <bool MASKED>
 __global__ void __launch_bounds__(kF2T)
 k_relaxed_fwd2_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int32_t* __restrict__ Hs,
                      const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs,
@@ -349,7 +368,7 @@ k_relaxed_fwd2_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int3
                      const float* __restrict__ mask1, float p_continue, float* __restrict__ pun1,
                      float* __restrict__ pburn1, float* __restrict__ pun2, float* __restrict__ pburn2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Fwd2Smem& S = *reinterpret_cast<Fwd2Smem*>(smem_raw);
+    Fwd2Smem<MASKED>& S = *reinterpret_cast<Fwd2Smem<MASKED>*>(smem_raw);
     int cur = 0;
     if ((int64_t)blockIdx.x < n_tiles)
         fwd2_stage(S.st[0], tiles, blockIdx.x, Hs, Ws, offs, r, pun, pburn, mask0, mask1);
@@ -364,10 +383,12 @@ k_relaxed_fwd2_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int3
         const int64_t off = offs[e];
         jwf_cp_async_wait_prev();
         __syncthreads();
-        Fwd2Stage& b = S.st[cur];
-        if (mask0 != nullptr) {
-            for (int q = threadIdx.x; q < kA0N; q += kF2T) b.pb[q] = b.pb[q] * (1.0f - b.m0[q]);
-            __syncthreads();
+        Fwd2Stage<MASKED>& b = S.st[cur];
+        if constexpr (MASKED) {
+            if (mask0 != nullptr) {
+                for (int q = threadIdx.x; q < kA0N; q += kF2T) b.pb[q] = b.pb[q] * (1.0f - b.m0[q]);
+                __syncthreads();
+            }
         }
         // step t on the tile and its one-cell ring
         for (int j = threadIdx.x; j < kA1N; j += kF2T) {
@@ -398,9 +419,11 @@ k_relaxed_fwd2_tiled(const int4* __restrict__ tiles, int64_t n_tiles, const int3
             }
         }
         __syncthreads();
-        if (mask1 != nullptr) {
-            for (int q = threadIdx.x; q < kA1N; q += kF2T) S.pb1[q] = S.pb1[q] * (1.0f - b.m1[q]);
-            __syncthreads();
+        if constexpr (MASKED) {
+            if (mask1 != nullptr) {
+                for (int q = threadIdx.x; q < kA1N; q += kF2T) S.pb1[q] = S.pb1[q] * (1.0f - b.m1[q]);
+                __syncthreads();
+            }
         }
         // step t + 1 on the tile
         for (int j = threadIdx.x; j < kR2H * kR2W; j += kF2T) {
@@ -1012,25 +1035,36 @@ cudaError_t jwf_launch_relaxed_fwd(const jwf_ctx* c, const float* pun, const flo
 cudaError_t jwf_launch_relaxed_fwd2(const jwf_ctx* c, const float* pun, const float* pburn, const float* mask0,
                                     const float* mask1, float* pun1, float* pburn1, float* pun2, float* pburn2,
                                     cudaStream_t s) {
-    // persistent CTAs, as many as fit an SM (about three)
-    static int per_sm[64] = {};
-    const size_t smem = fwd2_smem_bytes();
+    // persistent CTAs, as many as fit an SM (three with masks, four without)
+    const bool masked = mask0 != nullptr || mask1 != nullptr;
+    static int per_sm[2][64] = {};
+    const size_t smem = masked ? fwd2_smem_bytes<true>() : fwd2_smem_bytes<false>();
     if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
-    if (per_sm[c->device] == 0) {
+    int& ps = per_sm[masked ? 1 : 0][c->device];
+    if (ps == 0) {
         cudaError_t err =
-            cudaFuncSetAttribute(k_relaxed_fwd2_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            masked ? cudaFuncSetAttribute(k_relaxed_fwd2_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)
+                   : cudaFuncSetAttribute(k_relaxed_fwd2_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem);
         if (err != cudaSuccess) return err;
         int b = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_fwd2_tiled, kF2T, smem);
+        err = masked ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_fwd2_tiled<true>, kF2T, smem)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_fwd2_tiled<false>, kF2T, smem);
         if (err != cudaSuccess) return err;
-        per_sm[c->device] = b > 0 ? b : 1;
+        ps = b > 0 ? b : 1;
     }
-    int64_t grid = (int64_t)c->num_sms * per_sm[c->device];
+    int64_t grid = (int64_t)c->num_sms * ps;
     if (grid > c->n_r2tiles) grid = c->n_r2tiles;
     if (grid < 1) grid = 1;
-    k_relaxed_fwd2_tiled<<<(unsigned)grid, kF2T, smem, s>>>(c->d_r2tiles, c->n_r2tiles, c->d_H, c->d_W, c->d_off,
-                                                             c->d_r, pun, pburn, mask0, mask1, c->P.p_continue,
-                                                             pun1, pburn1, pun2, pburn2);
+    if (masked)
+        k_relaxed_fwd2_tiled<true><<<(unsigned)grid, kF2T, smem, s>>>(
+            c->d_r2tiles, c->n_r2tiles, c->d_H, c->d_W, c->d_off, c->d_r, pun, pburn, mask0, mask1,
+            c->P.p_continue, pun1, pburn1, pun2, pburn2);
+    else
+        k_relaxed_fwd2_tiled<false><<<(unsigned)grid, kF2T, smem, s>>>(
+            c->d_r2tiles, c->n_r2tiles, c->d_H, c->d_W, c->d_off, c->d_r, pun, pburn, mask0, mask1,
+            c->P.p_continue, pun1, pburn1, pun2, pburn2);
     return cudaGetLastError();
 }
 
