@@ -55,18 +55,41 @@ __device__ __forceinline__ RateTerms rate_terms(const JwfDevParams& P, float z_s
     return t;
 }
 
+// sin and cos of d pi/8, d = 0..7, in double (made on the host)
+struct WindTrig {
+    double s[8], c[8];
+};
+
 __global__ void k_wind_exponent(int32_t N, const float* __restrict__ ws, const float* __restrict__ wd,
-                                double alpha_w1, double alpha_w2, float2* __restrict__ wexp) {
+                                double alpha_w1, double alpha_w2, const WindTrig T, float2* __restrict__ wexp) {
     // alpha_w1 V + alpha_w2 V (cos(d pi/4 - Theta) - 1) per env and direction, in
-    // double (cos - 1 written as -2 sin^2 to avoid cancellation), split hi + lo
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N * 8) return;
-    const int e = i >> 3, d = i & 7;
-    const double V = (double)ws[e], Th = (double)wd[e];
-    const double s = sin(0.5 * (d * 0.78539816339744830962 - Th));
-    const double w = alpha_w1 * V + alpha_w2 * V * (-2.0 * s * s);
-    const float hi = (float)w;
-    wexp[i] = make_float2(hi, (float)(w - (double)hi));
+    // double (cos - 1 written as -2 sin^2 to avoid cancellation), split hi + lo.
+    // One thread an env: sin(d pi/8 - Theta/2) = sin(d pi/8) cos(Theta/2) -
+    // cos(d pi/8) sin(Theta/2), so one sincos serves the eight directions.
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const double V = (double)ws[e];
+    double sh, ch;
+    sincos(0.5 * (double)wd[e], &sh, &ch);
+    float2* out = wexp + (int64_t)e * 8;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const double s = T.s[d] * ch - T.c[d] * sh;
+        const double w = alpha_w1 * V + alpha_w2 * V * (-2.0 * s * s);
+        const float hi = (float)w;
+        out[d] = make_float2(hi, (float)(w - (double)hi));
+    }
+}
+
+static WindTrig wind_trig() {
+    WindTrig T;
+    const double pi = 3.14159265358979323846;
+    for (int d = 0; d < 8; ++d) {
+        T.s[d] = std::sin(d * pi / 8.0);
+        T.c[d] = std::cos(d * pi / 8.0);
+    }
+    T.c[4] = 0.0;       // cos(pi/2) exactly
+    return T;
 }
 
 // wind exponent of one source cell with its own wind (per-cell mode), in double
@@ -505,8 +528,8 @@ cudaError_t jwf_launch_prob_check(const jwf_ctx* c, int64_t n, const uint8_t* cv
 }
 
 cudaError_t jwf_launch_wind_exponent(const jwf_ctx* c, const float* ws, const float* wd, cudaStream_t s) {
-    k_wind_exponent<<<(c->N * 8 + 255) / 256, 256, 0, s>>>(c->N, ws, wd, (double)c->P.alpha_w1,
-                                                             (double)c->P.alpha_w2, c->d_wexp);
+    k_wind_exponent<<<(c->N + 127) / 128, 128, 0, s>>>(c->N, ws, wd, (double)c->P.alpha_w1,
+                                                         (double)c->P.alpha_w2, wind_trig(), c->d_wexp);
     return cudaGetLastError();
 }
 
@@ -514,9 +537,9 @@ cudaError_t jwf_launch_wind_series(jwf_ctx* c, cudaStream_t s) {
     // the series is [steps][N]: the same kernel over steps x N "envs"
     const int64_t n = (int64_t)c->wser_n * c->N;
     if (n == 0) return cudaSuccess;
-    k_wind_exponent<<<(unsigned)((n * 8 + 255) / 256), 256, 0, s>>>((int32_t)n, c->s_ws, c->s_wd,
-                                                                   (double)c->P.alpha_w1, (double)c->P.alpha_w2,
-                                                                   c->d_wser);
+    k_wind_exponent<<<(unsigned)((n + 127) / 128), 128, 0, s>>>((int32_t)n, c->s_ws, c->s_wd,
+                                                               (double)c->P.alpha_w1, (double)c->P.alpha_w2,
+                                                               wind_trig(), c->d_wser);
     return cudaGetLastError();
 }
 
