@@ -718,6 +718,7 @@ struct __align__(16) Sw2Slot {
 };
 constexpr int kSw2Depth = 3;
 
+template <bool MASKED>
 __device__ __forceinline__ void sweep2_issue(Sw2Slot& sl, int lane, const float* __restrict__ r,
                                              const float* __restrict__ pun0, const float* __restrict__ pburn0,
                                              const float* __restrict__ mask0, const float* __restrict__ pun1,
@@ -740,35 +741,43 @@ __device__ __forceinline__ void sweep2_issue(Sw2Slot& sl, int lane, const float*
     }
     const bool row2 = (unsigned)(y + 2) < (unsigned)H;
     const int64_t v2 = v + 2 * (int64_t)W;
+    // (the mask fields are written, and read, only by the variant with masks)
     if (col && row2) {
         jwf_cp_async4(&sl.pbn1[lane], pburn1 + v2);
-        if (mask1 != nullptr) jwf_cp_async4(&sl.mn1[lane], mask1 + v2);
-        else sl.mn1[lane] = 0.f;
+        if constexpr (MASKED) {
+            if (mask1 != nullptr) jwf_cp_async4(&sl.mn1[lane], mask1 + v2);
+            else sl.mn1[lane] = 0.f;
+        }
     } else {
         sl.pbn1[lane] = 0.f;
-        sl.mn1[lane] = 0.f;
+        if constexpr (MASKED) sl.mn1[lane] = 0.f;
     }
     if (col_o && row2) {
         jwf_cp_async4(&sl.pbo1[lane], pburn1 + v2 + dxo);
-        if (mask1 != nullptr) jwf_cp_async4(&sl.mo1[lane], mask1 + v2 + dxo);
-        else sl.mo1[lane] = 0.f;
+        if constexpr (MASKED) {
+            if (mask1 != nullptr) jwf_cp_async4(&sl.mo1[lane], mask1 + v2 + dxo);
+            else sl.mo1[lane] = 0.f;
+        }
     } else {
         sl.pbo1[lane] = 0.f;
-        sl.mo1[lane] = 0.f;
+        if constexpr (MASKED) sl.mo1[lane] = 0.f;
     }
     if (col && (unsigned)(y - 1) < (unsigned)H) jwf_cp_async4(&sl.pu0[lane], pun0 + v - W);
     else sl.pu0[lane] = 0.f;
     if (col && (unsigned)(y + 1) < (unsigned)H) {
         jwf_cp_async4(&sl.pbn0[lane], pburn0 + v + W);
-        if (mask0 != nullptr) jwf_cp_async4(&sl.mn0[lane], mask0 + v + W);
-        else sl.mn0[lane] = 0.f;
+        if constexpr (MASKED) {
+            if (mask0 != nullptr) jwf_cp_async4(&sl.mn0[lane], mask0 + v + W);
+            else sl.mn0[lane] = 0.f;
+        }
     } else {
         sl.pbn0[lane] = 0.f;
-        sl.mn0[lane] = 0.f;
+        if constexpr (MASKED) sl.mn0[lane] = 0.f;
     }
     jwf_cp_async_commit();
 }
 
+template <bool MASKED>
 __global__ void __launch_bounds__(kSweepWarps * 32)
 k_relaxed_bwd_sweep2(const int4* __restrict__ items, int64_t n_items, const int32_t* __restrict__ Hs,
                      const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs, const float* __restrict__ r,
@@ -799,23 +808,23 @@ k_relaxed_bwd_sweep2(const int4* __restrict__ items, int64_t n_items, const int3
         const bool col = x >= 0 && x < W, col_o = edge && xo >= 0 && xo < W;
         const int yb = y0 - 2;                            // first target row of step t + 1
         // step t + 1: p_burn window rows y - 1, y, y + 1 (and the halo lanes' outer column)
-        float2 pa1 = sweep_pb(pburn1, mask1, off, yb - 1, x, H, W);
-        float2 pb1 = sweep_pb(pburn1, mask1, off, yb, x, H, W);
-        float2 pc1 = sweep_pb(pburn1, mask1, off, yb + 1, x, H, W);
+        float2 pa1 = sweep_pb(pburn1, MASKED ? mask1 : nullptr, off, yb - 1, x, H, W);
+        float2 pb1 = sweep_pb(pburn1, MASKED ? mask1 : nullptr, off, yb, x, H, W);
+        float2 pc1 = sweep_pb(pburn1, MASKED ? mask1 : nullptr, off, yb + 1, x, H, W);
         float oa = 0.f, ob = 0.f, oc = 0.f;
         if (edge) {
-            oa = sweep_pb(pburn1, mask1, off, yb - 1, xo, H, W).x;
-            ob = sweep_pb(pburn1, mask1, off, yb, xo, H, W).x;
-            oc = sweep_pb(pburn1, mask1, off, yb + 1, xo, H, W).x;
+            oa = sweep_pb(pburn1, MASKED ? mask1 : nullptr, off, yb - 1, xo, H, W).x;
+            ob = sweep_pb(pburn1, MASKED ? mask1 : nullptr, off, yb, xo, H, W).x;
+            oc = sweep_pb(pburn1, MASKED ? mask1 : nullptr, off, yb + 1, xo, H, W).x;
         }
         // step t (target row y - 1): window rows y - 2, y - 1, y
-        float2 pa0 = sweep_pb(pburn0, mask0, off, yb - 2, x, H, W);
-        float2 pb0 = sweep_pb(pburn0, mask0, off, yb - 1, x, H, W);
-        float2 pc0 = sweep_pb(pburn0, mask0, off, yb, x, H, W);
+        float2 pa0 = sweep_pb(pburn0, MASKED ? mask0 : nullptr, off, yb - 2, x, H, W);
+        float2 pb0 = sweep_pb(pburn0, MASKED ? mask0 : nullptr, off, yb - 1, x, H, W);
+        float2 pc0 = sweep_pb(pburn0, MASKED ? mask0 : nullptr, off, yb, x, H, W);
         int64_t v_is = off + (int64_t)yb * W + x;
         int64_t v = v_is;
         for (int k = 0; k < kSw2Depth - 1; ++k, v_is += W)
-            sweep2_issue(ring[warp][k], lane, r, pun0, pburn0, mask0, pun1, pburn1, mask1, gun_out, gburn_out, v_is,
+            sweep2_issue<MASKED>(ring[warp][k], lane, r, pun0, pburn0, mask0, pun1, pburn1, mask1, gun_out, gburn_out, v_is,
                          yb + k, col, col_o, xo - x, H, W);
         float h_prev = 0.f, h_cur = 0.f, h_next = 0.f;   // step t + 1 accumulators, rows y - 1, y, y + 1
         float g_prev = 0.f, g_cur = 0.f, g_next = 0.f;   // step t accumulators, rows y - 2, y - 1, y
@@ -825,18 +834,19 @@ k_relaxed_bwd_sweep2(const int4* __restrict__ items, int64_t n_items, const int3
         float rp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // rate row of y - 1
         for (int y = yb; y <= y1 + 1; ++y, v += W, v_is += W) {
             const int k = y - yb;
-            sweep2_issue(ring[warp][(k + kSw2Depth - 1) % kSw2Depth], lane, r, pun0, pburn0, mask0, pun1, pburn1,
+            sweep2_issue<MASKED>(ring[warp][(k + kSw2Depth - 1) % kSw2Depth], lane, r, pun0, pburn0, mask0, pun1, pburn1,
                          mask1, gun_out, gburn_out, v_is, y + kSw2Depth - 1, col, col_o, xo - x, H, W);
             cp_async_wait_n<kSw2Depth - 1>();
             const Sw2Slot& sl = ring[warp][k % kSw2Depth];
             const float4 ra4 = sl.ra[lane], rb4 = sl.rb[lane];
             const float pu1v = sl.pu1[lane], au2 = sl.au[lane], ab2 = sl.ab[lane];
-            const float pbn1 = sl.pbn1[lane], mn1 = sl.mn1[lane];
-            const float2 pn1 = make_float2(mask1 != nullptr ? pbn1 * (1.0f - mn1) : pbn1, mn1);
-            const float on = mask1 != nullptr ? sl.pbo1[lane] * (1.0f - sl.mo1[lane]) : sl.pbo1[lane];
+            const bool mk1 = MASKED && mask1 != nullptr, mk0 = MASKED && mask0 != nullptr;
+            const float pbn1 = sl.pbn1[lane], mn1 = mk1 ? sl.mn1[lane] : 0.f;
+            const float2 pn1 = make_float2(mk1 ? pbn1 * (1.0f - mn1) : pbn1, mn1);
+            const float on = mk1 ? sl.pbo1[lane] * (1.0f - sl.mo1[lane]) : sl.pbo1[lane];
             const float pu0v = sl.pu0[lane];
-            const float pbn0 = sl.pbn0[lane], mn0 = sl.mn0[lane];
-            const float2 pn0 = make_float2(mask0 != nullptr ? pbn0 * (1.0f - mn0) : pbn0, mn0);
+            const float pbn0 = sl.pbn0[lane], mn0 = mk0 ? sl.mn0[lane] : 0.f;
+            const float2 pn0 = make_float2(mk0 ? pbn0 * (1.0f - mn0) : pbn0, mn0);
             const float rv[8] = {ra4.x, ra4.y, ra4.z, ra4.w, rb4.x, rb4.y, rb4.z, rb4.w};
             // ---- step t + 1, target row y ----
             float h1;
@@ -893,7 +903,7 @@ k_relaxed_bwd_sweep2(const int4* __restrict__ items, int64_t n_items, const int3
             }
             // step t + 1's dL/dp_burn of row y - 1 is complete
             float ab1 = p_continue != 0.f ? p_continue * ab2_prev + h_prev : h_prev;
-            if (mask1 != nullptr) {
+            if (mk1) {
                 const float keep = 1.0f - m1_prev;
                 ab1 = keep != 0.f ? ab1 * keep : 0.f;
             }
@@ -941,7 +951,7 @@ k_relaxed_bwd_sweep2(const int4* __restrict__ items, int64_t n_items, const int3
                 // step t's dL/dp_burn of row y - 2 is complete
                 if (out_col && yy - 1 >= y0 && yy - 1 < y1) {
                     float gb = p_continue != 0.f ? p_continue * ab1_prev + g_prev : g_prev;
-                    if (mask0 != nullptr) {
+                    if (mk0) {
                         const float keep = 1.0f - pa0.y;
                         gb = keep != 0.f ? gb * keep : 0.f;
                     }
@@ -1110,21 +1120,30 @@ cudaError_t jwf_launch_relaxed_bwd2(jwf_ctx* c, const float* pun0, const float* 
                                     const float* pun1, const float* pburn1, const float* mask1,
                                     const float* gun_out, const float* gburn_out, float* gun, float* gburn,
                                     float* glam0, float* glam1, double* gpc, cudaStream_t s) {
-    static int per_sm[64] = {};
+    const bool masked = mask0 != nullptr || mask1 != nullptr;
+    static int per_sm[2][64] = {};
     if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
-    if (per_sm[c->device] == 0) {
+    int& ps = per_sm[masked ? 1 : 0][c->device];
+    if (ps == 0) {
         int b = 0;
         const cudaError_t err =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_bwd_sweep2, kSweepWarps * 32, 0);
+            masked ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_bwd_sweep2<true>, kSweepWarps * 32, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_bwd_sweep2<false>, kSweepWarps * 32,
+                                                                   0);
         if (err != cudaSuccess) return err;
-        per_sm[c->device] = b > 0 ? b : 1;
+        ps = b > 0 ? b : 1;
     }
     int64_t grid = (c->n_s2tiles + kSweepWarps - 1) / kSweepWarps;
-    if (grid > (int64_t)c->num_sms * per_sm[c->device]) grid = (int64_t)c->num_sms * per_sm[c->device];
+    if (grid > (int64_t)c->num_sms * ps) grid = (int64_t)c->num_sms * ps;
     if (grid > c->partial_cap) grid = c->partial_cap;
     if (grid < 1) grid = 1;
-    k_relaxed_bwd_sweep2<<<(unsigned)grid, kSweepWarps * 32, 0, s>>>(
-        c->d_s2tiles, c->n_s2tiles, c->d_H, c->d_W, c->d_off, c->d_r, pun0, pburn0, mask0, pun1, pburn1, mask1,
-        gun_out, gburn_out, c->P.p_continue, gun, gburn, glam0, glam1, c->d_partials, c->d_red_counter, gpc);
+    if (masked)
+        k_relaxed_bwd_sweep2<true><<<(unsigned)grid, kSweepWarps * 32, 0, s>>>(
+            c->d_s2tiles, c->n_s2tiles, c->d_H, c->d_W, c->d_off, c->d_r, pun0, pburn0, mask0, pun1, pburn1, mask1,
+            gun_out, gburn_out, c->P.p_continue, gun, gburn, glam0, glam1, c->d_partials, c->d_red_counter, gpc);
+    else
+        k_relaxed_bwd_sweep2<false><<<(unsigned)grid, kSweepWarps * 32, 0, s>>>(
+            c->d_s2tiles, c->n_s2tiles, c->d_H, c->d_W, c->d_off, c->d_r, pun0, pburn0, mask0, pun1, pburn1, mask1,
+            gun_out, gburn_out, c->P.p_continue, gun, gburn, glam0, glam1, c->d_partials, c->d_red_counter, gpc);
     return cudaGetLastError();
 }
