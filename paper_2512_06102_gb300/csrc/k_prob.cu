@@ -213,8 +213,15 @@ constexpr int kAccRows = JWF_RT_ROWS, kAccCols = JWF_RT_COLS;
 constexpr int kAccW = kAccCols + 2, kAccN = (kAccRows + 2) * kAccW;
 constexpr int kAccCPT = kAccRows * kAccCols / kAccT;       // cells a thread
 constexpr int kAccRowStep = kAccT / kAccCols;              // rows between a thread's cells
+// a step's staged planes; the mask's only when the accumulation has masks
+template <bool MASKED>
 struct AccStage {
     float pb[kAccN], m[kAccN];
+    float gl[kAccRows * kAccCols];
+};
+template <>
+struct AccStage<false> {
+    float pb[kAccN];
     float gl[kAccRows * kAccCols];
 };
 
@@ -245,7 +252,8 @@ __device__ __forceinline__ void acc_plan(AccPlan& pl, int y0, int x0, int H, int
 }
 
 // copies of one step: t0 = the global index of the tile's first cell in that step's planes
-__device__ __forceinline__ void acc_stage(AccStage& b, const AccPlan& pl, int64_t t0,
+template <bool MASKED>
+__device__ __forceinline__ void acc_stage(AccStage<MASKED>& b, const AccPlan& pl, int64_t t0,
                                           const float* __restrict__ glam, const float* __restrict__ pburn,
                                           const float* __restrict__ mask) {
 #pragma unroll
@@ -254,27 +262,30 @@ __device__ __forceinline__ void acc_stage(AccStage& b, const AccPlan& pl, int64_
         if (i >= kAccN) break;
         if (pl.pb[k] == kAccOut) {
             b.pb[i] = 0.f;
-            b.m[i] = 0.f;
+            if constexpr (MASKED) b.m[i] = 0.f;
             continue;
         }
         const int64_t u = t0 + pl.pb[k];
         jwf_cp_async4(&b.pb[i], pburn + u);
-        if (mask != nullptr)
-            jwf_cp_async4(&b.m[i], mask + u);
-        else
-            b.m[i] = 0.f;
+        if constexpr (MASKED) {
+            if (mask != nullptr)
+                jwf_cp_async4(&b.m[i], mask + u);
+            else
+                b.m[i] = 0.f;
+        }
     }
 #pragma unroll
     for (int k = 0; k < kAccCPT; ++k)
         if (pl.gl[k] != kAccOut) jwf_cp_async4(&b.gl[(int)threadIdx.x + k * kAccT], glam + t0 + pl.gl[k]);
 }
 
+template <bool MASKED>
 __global__ void __launch_bounds__(kAccT)
 k_rates_accumulate(const int4* __restrict__ tiles, const int32_t* __restrict__ Hs, const int32_t* __restrict__ Ws,
                    const int64_t* __restrict__ offs, int64_t cells, int32_t n_steps,
                    const float* __restrict__ glam, const float* __restrict__ pburn,
                    const float* __restrict__ mask, float* __restrict__ gr) {
-    __shared__ __align__(16) AccStage st[2];
+    __shared__ __align__(16) AccStage<MASKED> st[2];
     const int4 tl = tiles[blockIdx.x];
     const int e = tl.x, y0 = tl.y, x0 = tl.z;
     const int H = Hs[e], W = Ws[e];
@@ -296,7 +307,7 @@ k_rates_accumulate(const int4* __restrict__ tiles, const int32_t* __restrict__ H
         jwf_cp_async_commit();
         jwf_cp_async_wait_prev();
         __syncthreads();
-        AccStage& b = st[t & 1];
+        AccStage<MASKED>& b = st[t & 1];
 #pragma unroll
         for (int k = 0; k < kAccCPT; ++k) {
             const int ly = ty + k * kAccRowStep;
@@ -306,7 +317,9 @@ k_rates_accumulate(const int4* __restrict__ tiles, const int32_t* __restrict__ H
             for (int d = 0; d < 8; ++d) {
                 const int li = (ly + 1 - jwf_dr(d)) * kAccW + (tx + 1 - jwf_dx(d));
                 float pb = b.pb[li];
-                if (mask != nullptr) pb *= 1.0f - b.m[li];
+                if constexpr (MASKED) {
+                    if (mask != nullptr) pb *= 1.0f - b.m[li];
+                }
                 w[k][d] += g * pb;
             }
         }
@@ -562,8 +575,12 @@ cudaError_t jwf_launch_prob_table(const jwf_ctx* c, const uint8_t* cls, const fl
 
 cudaError_t jwf_launch_rates_accumulate(const jwf_ctx* c, int32_t n_steps, const float* glam,
                                         const float* pburn, const float* mask, float* gr, cudaStream_t s) {
-    k_rates_accumulate<<<(unsigned)c->n_rtiles, kAccT, 0, s>>>(c->d_rtiles, c->d_H, c->d_W, c->d_off, c->cells,
-                                                                n_steps, glam, pburn, mask, gr);
+    if (mask != nullptr)
+        k_rates_accumulate<true><<<(unsigned)c->n_rtiles, kAccT, 0, s>>>(c->d_rtiles, c->d_H, c->d_W, c->d_off,
+                                                                      c->cells, n_steps, glam, pburn, mask, gr);
+    else
+        k_rates_accumulate<false><<<(unsigned)c->n_rtiles, kAccT, 0, s>>>(c->d_rtiles, c->d_H, c->d_W, c->d_off,
+                                                                       c->cells, n_steps, glam, pburn, mask, gr);
     return cudaGetLastError();
 }
 

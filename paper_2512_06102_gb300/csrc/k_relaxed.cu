@@ -489,6 +489,7 @@ struct __align__(16) SwSlot {
 // (y, x) (only used when the cell exists), col / col_o whether this lane's
 // column and (halo lanes) its outer column lie in the grid, dxo = outer
 // column - x.
+template <bool MASKED>
 __device__ __forceinline__ void sweep_issue(SwSlot& sl, int lane, const float* __restrict__ r,
                                             const float* __restrict__ pun, const float* __restrict__ pburn,
                                             const float* __restrict__ mask, const float* __restrict__ gun_out,
@@ -509,21 +510,26 @@ __device__ __forceinline__ void sweep_issue(SwSlot& sl, int lane, const float* _
     }
     const bool row2 = (unsigned)(y + 2) < (unsigned)H;
     const int64_t v2 = v + 2 * (int64_t)W;
+    // (the mask fields are written, and read, only by the variant with masks)
     if (col && row2) {
         jwf_cp_async4(&sl.pbn[lane], pburn + v2);
-        if (mask != nullptr) jwf_cp_async4(&sl.mn[lane], mask + v2);
-        else sl.mn[lane] = 0.f;
+        if constexpr (MASKED) {
+            if (mask != nullptr) jwf_cp_async4(&sl.mn[lane], mask + v2);
+            else sl.mn[lane] = 0.f;
+        }
     } else {
         sl.pbn[lane] = 0.f;
-        sl.mn[lane] = 0.f;
+        if constexpr (MASKED) sl.mn[lane] = 0.f;
     }
     if (col_o && row2) {
         jwf_cp_async4(&sl.pbo[lane], pburn + v2 + dxo);
-        if (mask != nullptr) jwf_cp_async4(&sl.mo[lane], mask + v2 + dxo);
-        else sl.mo[lane] = 0.f;
+        if constexpr (MASKED) {
+            if (mask != nullptr) jwf_cp_async4(&sl.mo[lane], mask + v2 + dxo);
+            else sl.mo[lane] = 0.f;
+        }
     } else {
         sl.pbo[lane] = 0.f;
-        sl.mo[lane] = 0.f;
+        if constexpr (MASKED) sl.mo[lane] = 0.f;
     }
     jwf_cp_async_commit();
 }
@@ -531,6 +537,7 @@ __device__ __forceinline__ void sweep_issue(SwSlot& sl, int lane, const float* _
 template <int N>
 __device__ __forceinline__ void cp_async_wait_n() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+template <bool MASKED>
 __global__ void __launch_bounds__(kSweepWarps * 32)
 k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32_t* __restrict__ Hs,
                     const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs,
@@ -558,14 +565,14 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
         const int xo = lane == 0 ? x - 1 : x + 1;
         const bool edge = lane == 0 || lane == 31;
         // p_burn windows: rows y - 1, y, y + 1 of the target row y
-        float2 pa = sweep_pb(pburn, mask, off, y0 - 2, x, H, W);
-        float2 pb = sweep_pb(pburn, mask, off, y0 - 1, x, H, W);
-        float2 pc = sweep_pb(pburn, mask, off, y0, x, H, W);
+        float2 pa = sweep_pb(pburn, MASKED ? mask : nullptr, off, y0 - 2, x, H, W);
+        float2 pb = sweep_pb(pburn, MASKED ? mask : nullptr, off, y0 - 1, x, H, W);
+        float2 pc = sweep_pb(pburn, MASKED ? mask : nullptr, off, y0, x, H, W);
         float oa = 0.f, ob = 0.f, oc = 0.f;
         if (edge) {
-            oa = sweep_pb(pburn, mask, off, y0 - 2, xo, H, W).x;
-            ob = sweep_pb(pburn, mask, off, y0 - 1, xo, H, W).x;
-            oc = sweep_pb(pburn, mask, off, y0, xo, H, W).x;
+            oa = sweep_pb(pburn, MASKED ? mask : nullptr, off, y0 - 2, xo, H, W).x;
+            ob = sweep_pb(pburn, MASKED ? mask : nullptr, off, y0 - 1, xo, H, W).x;
+            oc = sweep_pb(pburn, MASKED ? mask : nullptr, off, y0, xo, H, W).x;
         }
         const int yb = y0 - 1;                            // first target row
         const bool col = x >= 0 && x < W, col_o = edge && xo >= 0 && xo < W;
@@ -574,13 +581,13 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
         int64_t v_is = off + (int64_t)yb * W + x;
         int64_t v = v_is;
         for (int k = 0; k < kSwDepth - 1; ++k, v_is += W)
-            sweep_issue(ring[warp][k], lane, r, pun, pburn, mask, gun_out, gburn_out, v_is, yb + k, col, col_o,
+            sweep_issue<MASKED>(ring[warp][k], lane, r, pun, pburn, mask, gun_out, gburn_out, v_is, yb + k, col, col_o,
                         xo - x, H, W);
         float g_prev = 0.f, g_cur = 0.f, g_next = 0.f;   // accumulators of rows y - 1, y, y + 1
         float ab_prev = 0.f, m_prev = 0.f;                // a_b and mask of row y - 1
         for (int y = yb; y <= y1; ++y, v += W, v_is += W) {
             const int k = y - yb;
-            sweep_issue(ring[warp][(k + kSwDepth - 1) % kSwDepth], lane, r, pun, pburn, mask, gun_out, gburn_out,
+            sweep_issue<MASKED>(ring[warp][(k + kSwDepth - 1) % kSwDepth], lane, r, pun, pburn, mask, gun_out, gburn_out,
                         v_is, y + kSwDepth - 1, col, col_o, xo - x, H, W);
             cp_async_wait_n<kSwDepth - 1>();
             const SwSlot& sl = ring[warp][k % kSwDepth];
@@ -588,9 +595,10 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
                 float4 ra, rb;
                 float pu, au, ab;
             } cur = {sl.ra[lane], sl.rb[lane], sl.pu[lane], sl.au[lane], sl.ab[lane]};
-            const float pbn = sl.pbn[lane], mn = sl.mn[lane];
-            const float2 pn = make_float2(mask != nullptr ? pbn * (1.0f - mn) : pbn, mn);
-            const float on = mask != nullptr ? sl.pbo[lane] * (1.0f - sl.mo[lane]) : sl.pbo[lane];
+            const bool mk = MASKED && mask != nullptr;
+            const float pbn = sl.pbn[lane], mn = mk ? sl.mn[lane] : 0.f;
+            const float2 pn = make_float2(mk ? pbn * (1.0f - mn) : pbn, mn);
+            const float on = mk ? sl.pbo[lane] * (1.0f - sl.mo[lane]) : sl.pbo[lane];
             // neighbour columns of the window
             float la = __shfl_up_sync(FULL, pa.x, 1), lb = __shfl_up_sync(FULL, pb.x, 1),
                   lc = __shfl_up_sync(FULL, pc.x, 1);
@@ -648,7 +656,7 @@ k_relaxed_bwd_sweep(const int4* __restrict__ items, int64_t n_items, const int32
             // row y - 1 is complete
             if (out_col && y - 1 >= y0 && y - 1 < y1) {
                 float gb = p_continue != 0.f ? p_continue * ab_prev + g_prev : g_prev;
-                if (mask != nullptr) {
+                if (mk) {
                     const float keep = 1.0f - m_prev;
                     gb = keep != 0.f ? gb * keep : 0.f;
                 }
@@ -1096,22 +1104,32 @@ cudaError_t jwf_launch_relaxed_bwd(jwf_ctx* c, const float* pun, const float* pb
         // column sweeps, grid-stride over the strips with as many CTAs as fit
         // the GPU at once (a fixed grid also keeps the per-CTA partial sums of
         // dL/dp_continue deterministic)
-        static int per_sm[64] = {};
+        const bool masked = mask != nullptr;
+        static int per_sm[2][64] = {};
         if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
-        if (per_sm[c->device] == 0) {
+        int& ps = per_sm[masked ? 1 : 0][c->device];
+        if (ps == 0) {
             int b = 0;
             const cudaError_t err =
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_bwd_sweep, kSweepWarps * 32, 0);
+                masked
+                    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_bwd_sweep<true>, kSweepWarps * 32, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_relaxed_bwd_sweep<false>, kSweepWarps * 32,
+                                                                    0);
             if (err != cudaSuccess) return err;
-            per_sm[c->device] = b > 0 ? b : 1;
+            ps = b > 0 ? b : 1;
         }
         int64_t grid = (c->n_stiles + kSweepWarps - 1) / kSweepWarps;
-        if (grid > (int64_t)c->num_sms * per_sm[c->device]) grid = (int64_t)c->num_sms * per_sm[c->device];
+        if (grid > (int64_t)c->num_sms * ps) grid = (int64_t)c->num_sms * ps;
         if (grid > c->partial_cap) grid = c->partial_cap;
         if (grid < 1) grid = 1;
-        k_relaxed_bwd_sweep<<<(unsigned)grid, kSweepWarps * 32, 0, s>>>(
-            c->d_stiles, c->n_stiles, c->d_H, c->d_W, c->d_off, c->d_r, pun, pburn, mask, gun_out, gburn_out,
-            c->P.p_continue, gun, gburn, glam, c->d_partials, c->d_red_counter, gpc);
+        if (masked)
+            k_relaxed_bwd_sweep<true><<<(unsigned)grid, kSweepWarps * 32, 0, s>>>(
+                c->d_stiles, c->n_stiles, c->d_H, c->d_W, c->d_off, c->d_r, pun, pburn, mask, gun_out, gburn_out,
+                c->P.p_continue, gun, gburn, glam, c->d_partials, c->d_red_counter, gpc);
+        else
+            k_relaxed_bwd_sweep<false><<<(unsigned)grid, kSweepWarps * 32, 0, s>>>(
+                c->d_stiles, c->n_stiles, c->d_H, c->d_W, c->d_off, c->d_r, pun, pburn, mask, gun_out, gburn_out,
+                c->P.p_continue, gun, gburn, glam, c->d_partials, c->d_red_counter, gpc);
     }
     return cudaGetLastError();
 }
