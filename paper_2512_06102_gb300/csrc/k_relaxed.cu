@@ -785,8 +785,9 @@ __device__ __forceinline__ void sweep2_issue(Sw2Slot& sl, int lane, const float*
     jwf_cp_async_commit();
 }
 
+// Without masks the sweep fits 80 registers: six CTAs an SM instead of five.
 template <bool MASKED>
-__global__ void __launch_bounds__(kSweepWarps * 32)
+__global__ void __launch_bounds__(kSweepWarps * 32, MASKED ? 5 : 6)
 k_relaxed_bwd_sweep2(const int4* __restrict__ items, int64_t n_items, const int32_t* __restrict__ Hs,
                      const int32_t* __restrict__ Ws, const int64_t* __restrict__ offs, const float* __restrict__ r,
                      const float* __restrict__ pun0, const float* __restrict__ pburn0,
