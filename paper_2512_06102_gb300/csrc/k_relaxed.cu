@@ -841,12 +841,15 @@ k_relaxed_bwd_sweep2(const int4* __restrict__ items, int64_t n_items, const int3
         float au1_prev = 0.f;                             // step t + 1's dL/dp_un of row y - 1
         float ab1_prev = 0.f;                             // step t + 1's dL/dp_burn of row y - 2
         float rp[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // rate row of y - 1
+        // ring slots: the row being read and the row being fetched (kSw2Depth - 1 ahead)
+        int s_use = 0, s_fetch = kSw2Depth - 1;
         for (int y = yb; y <= y1 + 1; ++y, v += W, v_is += W) {
-            const int k = y - yb;
-            sweep2_issue<MASKED>(ring[warp][(k + kSw2Depth - 1) % kSw2Depth], lane, r, pun0, pburn0, mask0, pun1, pburn1,
-                         mask1, gun_out, gburn_out, v_is, y + kSw2Depth - 1, col, col_o, xo - x, H, W);
+            sweep2_issue<MASKED>(ring[warp][s_fetch], lane, r, pun0, pburn0, mask0, pun1, pburn1, mask1, gun_out,
+                                 gburn_out, v_is, y + kSw2Depth - 1, col, col_o, xo - x, H, W);
             cp_async_wait_n<kSw2Depth - 1>();
-            const Sw2Slot& sl = ring[warp][k % kSw2Depth];
+            const Sw2Slot& sl = ring[warp][s_use];
+            s_use = s_use + 1 == kSw2Depth ? 0 : s_use + 1;
+            s_fetch = s_fetch + 1 == kSw2Depth ? 0 : s_fetch + 1;
             const float4 ra4 = sl.ra[lane], rb4 = sl.rb[lane];
             const float pu1v = sl.pu1[lane], au2 = sl.au[lane], ab2 = sl.ab[lane];
             const bool mk1 = MASKED && mask1 != nullptr, mk0 = MASKED && mask0 != nullptr;
