@@ -10,9 +10,12 @@
 //      word a lane, the can-burn cells with a burning neighbour and the
 //      burning cells (eight shifted ORs of the burning plane); the work items
 //      (remain-burning draws, compared (target, source) pairs) go to a
-//      block-wide queue in shared memory;
-//   B. all threads of the CTA evaluate the queued items (Philox draws, the
-//      ignition probability) and set ignition and burn-out bits;
+//      block-wide queue in shared memory (one atomicAdd reservation per
+//      chunk), and the candidates' terrain rows are prefetched for B;
+//   B. all threads of the CTA evaluate the queued items (one Philox block an
+//      item; a pair's ignition probability in plain float with a proven
+//      error bound, the double-float rate only for draws within it) and set
+//      ignition and burn-out bits;
 //   C. the dealt chunks are written back (new burning plane, the next
 //      step's tanker drop, counts).
 // A launch may be split after a few steps (k_reorder between the parts) so
