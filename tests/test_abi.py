@@ -64,5 +64,13 @@ def test_host_side_errors_without_gpu(libjwf):
     # every context call rejects a null context
     for name, args in [("jwf_set_reorder_steps", (None, 8)), ("jwf_set_tile_copy", (None, 1)),
                        ("jwf_set_tile_copy_wait", (None, 1000, 0)), ("jwf_set_env_priority", (None, None)),
-                       ("jwf_load_state_packed", (None, None, None)), ("jwf_get_state_packed", (None, None, None))]:
+                       ("jwf_load_state_packed", (None, None, None)), ("jwf_get_state_packed", (None, None, None)),
+                       ("jwf_check_prob_bound", (None, 0, None, None, None, None, None, None, None, None)),
+                       ("jwf_step_masked", (None, 1, None, None, None, None, None))]:
         assert getattr(libjwf, name)(*args) == 1, name
+    # context-free mask packing: sizes and argument checks
+    assert libjwf.jwf_mask_words(0) == 0
+    assert libjwf.jwf_mask_words(1) == 1
+    assert libjwf.jwf_mask_words(64) == 2
+    assert libjwf.jwf_mask_words(65) == 3
+    assert libjwf.jwf_pack_masks(-1, 10, None, None, None) == 1
