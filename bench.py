@@ -993,7 +993,7 @@ def bench_rollout(args, D, dev, rank):
     sim.set_kernel(jwf.KERNEL_FUSED)
     sim.set_terrain(*terrain)
     choice = autotune.tune(sim, F0, dr, kernel=jwf.KERNEL_FUSED, probe_steps=16, use_cache=False)
-    k_best = autotune.tune_steps_per_launch(sim, F0, dr, 64, candidates=(1, 8, 32, 64))
+    k_best = autotune.tune_steps_per_launch(sim, F0, dr, RAG_T, candidates=(64, 125, 250, None))
 
     def timed(fn, reps=1):
         best = None
