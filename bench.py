@@ -153,6 +153,9 @@ class _Nvml:
         v = self.c.c_ulonglong()
         return v.value if self.reasons_fn(self.h, self.c.byref(v)) == 0 else 0
 
+    def close(self):
+        self.lib.nvmlShutdown()
+
 
 class Clocks:
     """SM clock and clock event reasons sampled every millisecond (NVML) while
@@ -210,8 +213,10 @@ class Clocks:
             rows = [r for r in self.rows if (t0 is None or r[0] >= t0) and (t1 is None or r[0] <= t1)]
             sm = [r[1] for r in rows if r[1] > 0]
             reasons = sorted({n for r in rows for bit, n in _Nvml.REASONS.items() if r[2] & bit})
-            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.nvml.sm_max(),
-                    "reasons": reasons, "samples": len(sm), "source": "NVML, 1 ms"}
+            rec = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.nvml.sm_max(),
+                   "reasons": reasons, "samples": len(sm), "source": "NVML, 1 ms"}
+            self.nvml.close()
+            return rec
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
